@@ -1,0 +1,305 @@
+"""CPU oracle of the Camelot query pipeline -- TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 C++ restatement of what the pipeline computes (``camelot_oracle.cpp``)
+wrapped with ctypes.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product library
+(``paper_2005_02088_b300``) never does, and the two share no code.
+
+Every function carries the paper passage it restates in the C++ source.  The
+pins that tie it to something other than itself live in
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "camelot_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
+POLICY_MAX_PEAK, POLICY_MIN_SM = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with g++ (OpenMP) if it is missing or stale."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC",
+                    "-o", tmp, _SRC], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _declare(C.CDLL(build()))
+        return _lib
+
+
+P = C.c_void_p
+I64 = C.c_int64
+
+
+def _declare(L):
+    sig = {
+        "orc_normalize_u8": (None, [P, I64, P]),
+        "orc_norm_pool2": (None, [P, I64, C.c_int, C.c_int, C.c_int, P]),
+        "orc_gelu": (C.c_double, [C.c_double]),
+        "orc_linear": (None, [P, I64, C.c_int, P, C.c_int, C.c_int, P, P]),
+        "orc_argmax": (None, [P, I64, C.c_int, P]),
+        "orc_topk": (None, [P, I64, C.c_int, C.c_int, P, P]),
+        "orc_round_f32": (None, [P, I64, P]),
+        "orc_round_bf16": (None, [P, I64, P]),
+        "orc_bf16_bits": (None, [P, I64, P]),
+        "orc_round_e4m3": (None, [P, I64, P]),
+        "orc_pipeline_mlp": (None, [P, I64, P, P, P, P, P, P, C.c_int]),
+        "orc_pipeline_gemm3": (None, [P, I64, C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_int,
+                                      P, P, C.c_int]),
+        "orc_simulate": (I64, [P, I64, C.c_int, C.c_double, C.c_int, P, P, P, P, I64, P, P]),
+        "orc_allocate_exhaustive": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
+                                    + [C.c_int] + [P] * 5),
+        "orc_allocate_anneal": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
+                                + [C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64]
+                                + [P] * 5),
+        "orc_min_gpus": (C.c_double, [P, P, C.c_int, C.c_double, C.c_double]),
+        "orc_pred_nparams": (I64, []),
+        "orc_pred_forward": (None, [P, P, I64, P]),
+        "orc_pred_grad": (C.c_double, [P, P, P, I64, P]),
+        "orc_adam_step": (None, [P, P, P, P, I64, C.c_int, C.c_double, C.c_double,
+                                 C.c_double, C.c_double]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# stage math
+# ---------------------------------------------------------------------------
+def normalize_u8(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    y = np.empty(x.shape, np.float64)
+    lib().orc_normalize_u8(_p(x), x.size, _p(y))
+    return y.reshape(x.shape[0], -1) if x.ndim > 1 else y
+
+
+def norm_pool2(x: np.ndarray) -> np.ndarray:
+    """x [n, H, W, C] u8 -> [n, H/2 * W/2 * C] float64."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    n, H, W, Cc = x.shape
+    y = np.empty((n, (H // 2) * (W // 2) * Cc), np.float64)
+    lib().orc_norm_pool2(_p(x), n, H, W, Cc, _p(y))
+    return y
+
+
+def gelu(v: float) -> float:
+    return lib().orc_gelu(float(v))
+
+
+def linear(x: np.ndarray, w: np.ndarray, act: int = ACT_NONE, want_absdot: bool = False):
+    """y = act(x @ w.T) with x [n, K], w [N, K]; optionally sum |w x| per output."""
+    x = _f64(x)
+    w = _f64(w)
+    n, K = x.shape
+    N = w.shape[0]
+    y = np.empty((n, N), np.float64)
+    a = np.empty((n, N), np.float64) if want_absdot else None
+    lib().orc_linear(_p(x), n, K, _p(w), N, act, _p(y), _p(a) if a is not None else None)
+    return (y, a) if want_absdot else y
+
+
+def argmax(z: np.ndarray) -> np.ndarray:
+    z = _f64(z)
+    idx = np.empty(z.shape[0], np.int32)
+    lib().orc_argmax(_p(z), z.shape[0], z.shape[1], _p(idx))
+    return idx
+
+
+def topk(z: np.ndarray, k: int):
+    z = _f64(z)
+    idx = np.empty((z.shape[0], k), np.int32)
+    val = np.empty((z.shape[0], k), np.float64)
+    lib().orc_topk(_p(z), z.shape[0], z.shape[1], k, _p(idx), _p(val))
+    return idx, val
+
+
+def round_f32(v) -> np.ndarray:
+    v = _f64(v)
+    out = np.empty_like(v)
+    lib().orc_round_f32(_p(v), v.size, _p(out))
+    return out
+
+
+def round_bf16(v) -> np.ndarray:
+    v = _f64(v)
+    out = np.empty_like(v)
+    lib().orc_round_bf16(_p(v), v.size, _p(out))
+    return out
+
+
+def bf16_bits(v) -> np.ndarray:
+    v = _f64(v)
+    out = np.empty(v.shape, np.uint16)
+    lib().orc_bf16_bits(_p(v), v.size, _p(out))
+    return out
+
+
+def round_e4m3(v) -> np.ndarray:
+    v = _f64(v)
+    out = np.empty_like(v)
+    lib().orc_round_e4m3(_p(v), v.size, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# whole pipelines
+# ---------------------------------------------------------------------------
+def pipeline_mlp(x_u8: np.ndarray, ws, nthreads: int = 0):
+    """Plain 2-stage pipeline: normalise, 3-layer ReLU MLP, argmax.
+    Returns (logits [n, N3] float64, idx [n] int32)."""
+    x = np.ascontiguousarray(x_u8, dtype=np.uint8).reshape(x_u8.shape[0], -1)
+    w1, w2, w3 = (_f64(w) for w in ws)
+    dims = np.array([w1.shape[1], w1.shape[0], w2.shape[0], w3.shape[0]], np.int32)
+    n = x.shape[0]
+    logits = np.empty((n, dims[3]), np.float64)
+    idx = np.empty(n, np.int32)
+    lib().orc_pipeline_mlp(_p(x), n, _p(dims), _p(w1), _p(w2), _p(w3), _p(logits), _p(idx),
+                           int(nthreads))
+    return logits, idx
+
+
+def pipeline_gemm3(x_u8: np.ndarray, ws, top_k: int = 5, emulate_bf16: bool = False,
+                   nthreads: int = 0):
+    """3-stage pipeline: pool+normalise, gelu(Wb gelu(Wa y)), logits Wc h, top-k.
+    Returns (logits [n, N3], idx [n, k])."""
+    x = np.ascontiguousarray(x_u8, dtype=np.uint8)
+    n, H, W, _ = x.shape
+    wa, wb, wc = (_f64(w) for w in ws)
+    dims = np.array([wa.shape[1], wa.shape[0], wb.shape[0], wc.shape[0]], np.int32)
+    logits = np.empty((n, dims[3]), np.float64)
+    idx = np.empty((n, top_k), np.int32)
+    lib().orc_pipeline_gemm3(_p(x), n, H, W, _p(dims), _p(wa), _p(wb), _p(wc), top_k,
+                             int(bool(emulate_bf16)), _p(logits), _p(idx), int(nthreads))
+    return logits, idx
+
+
+# ---------------------------------------------------------------------------
+# event-driven simulator
+# ---------------------------------------------------------------------------
+def simulate(arrivals_s, B: int, t_wait: float, instances, tau, caps=None, mult=None):
+    """Completion time of every query (seconds) and the issued batch sizes.
+
+    ``tau[s][b-1]`` = service time of a b-query batch at stage s; ``mult`` an
+    optional ``[stages, m]`` array of per-batch service-time multipliers."""
+    arr = _f64(arrivals_s)
+    ns = len(instances)
+    inst = np.ascontiguousarray(instances, dtype=np.int32)
+    tau = _f64(tau).reshape(ns, B)
+    caps = np.ascontiguousarray(caps if caps is not None else [1 << 30] * ns, dtype=np.int32)
+    if mult is not None:
+        mult = _f64(mult).reshape(ns, -1)
+        mlen = mult.shape[1]
+    else:
+        mlen = 0
+    done = np.empty(arr.size, np.float64)
+    bs = np.empty(arr.size, np.int32)
+    nb = lib().orc_simulate(_p(arr), arr.size, int(B), float(t_wait), ns, _p(inst), _p(tau),
+                            _p(caps), _p(mult) if mult is not None else None, mlen, _p(done),
+                            _p(bs))
+    return done, bs[:nb]
+
+
+# ---------------------------------------------------------------------------
+# allocator
+# ---------------------------------------------------------------------------
+def _alloc_args(prob):
+    f = _f64(prob["f"])      # [nb, n, L]
+    bw = _f64(prob["bw"])
+    d = _f64(prob["d"])
+    mem = _f64(prob["mem"])  # [nb, n]
+    nb, n, L = f.shape
+    return f, bw, d, mem, nb, n, L
+
+
+def allocate(prob: dict, policy: int, solver: str = "exhaustive", iters: int = 5000,
+             T0: float = 1.0, alpha: float = 0.995, seed: int = 0):
+    """Solve Eq. 1 (policy 0) or Eq. 3 (policy 1) on a profile table.
+
+    ``prob`` keys: f, bw, d ([nb, n, L]), mem ([nb, n]), unit, S, I, BW, F, qos,
+    load.  Returns None if infeasible, else dict(bi, N, l, p, thr, sms)."""
+    f, bw, d, mem, nb, n, L = _alloc_args(prob)
+    bi = C.c_int(0)
+    N = np.zeros(n, np.int32)
+    lv = np.zeros(n, np.int32)
+    thr = C.c_double(0)
+    sms = C.c_int(0)
+    common = (n, L, nb, int(prob["unit"]), int(prob["S"]), int(prob["I"]), _p(f), _p(bw),
+              _p(d), _p(mem), float(prob["BW"]), float(prob["F"]), float(prob["qos"]),
+              float(prob.get("load", 0.0)), int(policy))
+    outs = (C.byref(bi), _p(N), _p(lv), C.byref(thr), C.byref(sms))
+    if solver == "exhaustive":
+        ok = lib().orc_allocate_exhaustive(*common, *outs)
+    else:
+        ok = lib().orc_allocate_anneal(*common, int(iters), float(T0), float(alpha),
+                                       int(seed), *outs)
+    if not ok:
+        return None
+    return dict(bi=bi.value, N=N.tolist(), l=lv.tolist(),
+                p=[(x + 1) * int(prob["unit"]) for x in lv.tolist()], thr=thr.value,
+                sms=sms.value)
+
+
+def min_gpus(Cs, Ms, G: float, F: float) -> float:
+    Cs, Ms = _f64(Cs), _f64(Ms)
+    return lib().orc_min_gpus(_p(Cs), _p(Ms), Cs.size, float(G), float(F))
+
+
+# ---------------------------------------------------------------------------
+# predictor MLP
+# ---------------------------------------------------------------------------
+def pred_nparams() -> int:
+    return int(lib().orc_pred_nparams())
+
+
+def pred_forward(theta, X) -> np.ndarray:
+    theta, X = _f64(theta), _f64(X)
+    y = np.empty(X.shape[0], np.float64)
+    lib().orc_pred_forward(_p(theta), _p(X), X.shape[0], _p(y))
+    return y
+
+
+def pred_grad(theta, X, t):
+    theta, X, t = _f64(theta), _f64(X), _f64(t)
+    g = np.empty_like(theta)
+    loss = lib().orc_pred_grad(_p(theta), _p(X), _p(t), X.shape[0], _p(g))
+    return loss, g
+
+
+def adam_step(theta, g, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam update of float64 arrays theta, m, v."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib().orc_adam_step(_p(theta), _p(g), _p(m), _p(v), theta.size, int(t), lr, b1, b2, eps)
