@@ -1,0 +1,297 @@
+/*
+ * camelot.h -- C ABI of libcamelot.so, a B300-native (sm_103a) runtime for
+ * multi-stage GPU microservice query pipelines in the manner of Camelot
+ * (Zhang et al., "Towards QoS-Aware and Resource-Efficient GPU Microservices
+ * Based on Spatial Multitasking GPUs In Datacenters").
+ *
+ * What the library does, in the paper's terms:
+ *   - Each microservice stage runs as instances that own a fixed number of SMs
+ *     (the SM quota p_i of Table 2; instances N_i), all inside ONE persistent
+ *     cooperative kernel whose CTAs are partitioned into stage instances, one
+ *     CTA per SM.  This replaces the MPS quotas of Sec. 5.2 step 5.
+ *   - Stage i hands a batch to stage i+1 through device global memory: a ring
+ *     slot plus an acquire/release sequence flag; the consumer reads the slot
+ *     in place (the global-memory-based communication of Sec. 6.2).  The
+ *     comparison arm copies every handoff device -> pinned host -> device (the
+ *     default main-memory mechanism of Sec. 4.2 and Sec. 6.1).
+ *   - Queries wait in a queue and are batched when B of them wait or when the
+ *     oldest has waited a bound (Sec. 5.2 steps 1-2).
+ *   - camelot_allocate solves the peak-load policy (Eq. 1) and the low-load
+ *     resource policy (Eq. 3) over instance counts and SM quotas.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a camelot_status; nothing throws across the ABI.  On
+ *     error no partial effect is left behind unless stated, and
+ *     camelot_last_error() returns a thread-local message.
+ *   - Pointers documented as "device" must be device (or managed) memory of the
+ *     current CUDA device; "host" pointers are ordinary host memory.  The
+ *     library never takes ownership of caller memory.
+ *   - A pipeline is driven by one submitting thread and one polling thread at
+ *     most (they may be the same thread).
+ *   - The library prints nothing; it allocates device memory only inside
+ *     camelot_stage_prepare and camelot_pipeline_create.
+ */
+#ifndef CAMELOT_H_
+#define CAMELOT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    CAMELOT_OK = 0,
+    CAMELOT_EINVAL = 1,      /* bad argument (message says which)                        */
+    CAMELOT_ENOMEM = 2,      /* device or pinned host allocation failed                  */
+    CAMELOT_EAGAIN = 3,      /* back-pressure: the query ring is full; nothing was queued */
+    CAMELOT_ETIMEDOUT = 4,   /* a bounded wait (device or host) gave up                  */
+    CAMELOT_ECUDA = 5,       /* a CUDA runtime/driver call failed                         */
+    CAMELOT_ESTATE = 6,      /* the pipeline is in an error state or the call is out of order */
+    CAMELOT_EINFEASIBLE = 7  /* camelot_allocate: no allocation satisfies the constraints */
+} camelot_status;
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* camelot_last_error(void);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int camelot_version(void);
+
+/* ------------------------------------------------------------- stages */
+/* Stage kinds.  The synthetic microservices stand in for the suite of
+ * Sec. 3 (Table 1); their definitions are the workload configurations:
+ *   NORMALIZE_U8   : u8 image [H][W][C] (HWC) -> f32 [H*W*C], y = (x - 127.5) / 64.
+ *   NORM_POOL2_BF16: u8 image [H][W][C] -> bf16 [H/2][W/2][C], y = rne_bf16(
+ *                    (mean of the 2x2 block - 127.5) / 64).  H, W even.
+ *   MLP_FP32       : f32 rows -> chain of FP32 dense layers y = act(W x) (no
+ *                    bias), then, if top_k > 0, the top-k indices/values of the
+ *                    last layer (top_k = 1 is argmax; ties -> lowest index).
+ *                    FP32 FFMA arithmetic, no TF32.
+ *   GEMM_BF16      : bf16 rows -> chain of dense layers on the tensor cores
+ *                    (bf16 operands, f32 accumulation in TMEM), each layer's
+ *                    output rounded to bf16 after its activation, except the
+ *                    last layer of a final (top_k > 0) stage, whose f32 output
+ *                    feeds the top-k. */
+typedef enum {
+    CAMELOT_STAGE_NORMALIZE_U8 = 1,
+    CAMELOT_STAGE_NORM_POOL2_BF16 = 2,
+    CAMELOT_STAGE_MLP_FP32 = 3,
+    CAMELOT_STAGE_GEMM_BF16 = 4
+} camelot_stage_kind;
+
+typedef enum { CAMELOT_ACT_NONE = 0, CAMELOT_ACT_RELU = 1, CAMELOT_ACT_GELU = 2 } camelot_act;
+
+#define CAMELOT_MAX_LAYERS 4
+#define CAMELOT_MAX_STAGES 8
+#define CAMELOT_MAX_TOPK 5
+
+typedef struct {
+    int32_t kind;                       /* camelot_stage_kind                              */
+    int32_t n_layers;                   /* dense kinds: 1..CAMELOT_MAX_LAYERS; else 0       */
+    int32_t dims[CAMELOT_MAX_LAYERS + 1]; /* dense: dims[0] = input width, dims[l+1] = width
+                                           after layer l.  Image kinds: {H, W, C, 0, 0}.   */
+    int32_t act[CAMELOT_MAX_LAYERS];    /* dense: camelot_act per layer                     */
+    int32_t top_k;                      /* 0: the stage's output rows go to the next stage;
+                                           1..CAMELOT_MAX_TOPK: final stage, emits top-k   */
+    int32_t max_batch;                  /* largest batch the stage must accept (1..256)    */
+    const void* weights[CAMELOT_MAX_LAYERS]; /* dense: device pointers, row-major
+                                           [dims[l+1]][dims[l]], f32 for MLP_FP32, bf16 for
+                                           GEMM_BF16.  Read once by camelot_stage_prepare. */
+} camelot_stage_desc;
+
+/* A prepared stage: validated descriptor plus the library's own copy of its
+ * weights in the layout its kernels read (one copy per stage, shared by every
+ * instance of the stage, as in Sec. 7.4's weight sharing). */
+typedef struct camelot_stage camelot_stage;
+
+/* Validate `desc` and copy its weights into kernel layout (device memory owned
+ * by the returned object).  The caller's weight buffers may be freed after the
+ * call returns.  Errors: EINVAL (shape/kind), ENOMEM, ECUDA. */
+camelot_status camelot_stage_prepare(const camelot_stage_desc* desc, camelot_stage** out);
+camelot_status camelot_stage_release(camelot_stage* st);
+
+/* Row sizes in bytes of one query's input and output for the stage (output
+ * bytes are 0 for a final stage), and the device scratch bytes a direct launch
+ * of `n` rows needs. */
+camelot_status camelot_stage_info(const camelot_stage* st, size_t* in_row_bytes,
+                                  size_t* out_row_bytes, uint32_t n, size_t* scratch_bytes);
+
+/* Direct, non-persistent launch of one stage on `n_ctas` CTAs (one per SM; the
+ * SM quota) over a batch of n rows -- the same device code the pipeline runs
+ * per batch.  Asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ * stream).
+ *   in      device, n * in_row_bytes, rows contiguous.
+ *   out     device, n * out_row_bytes (intermediate stages), else may be NULL.
+ *   out_idx device int32 [n][top_k] (final stages), else NULL.
+ *   out_val device f32   [n][top_k] (final stages), else NULL.
+ *   out_logits device f32 [n][dims[n_layers]] or NULL: the final layer's
+ *           output before top-k (dense kinds only).
+ *   scratch device, >= camelot_stage_info(...) bytes, 256-byte aligned; the
+ *           call clears what must start at zero.
+ * Errors: EINVAL (n = 0 or > max_batch, n_ctas outside 1..SM count, missing
+ * buffer), ECUDA (launch failure). */
+camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const void* in,
+                                    uint32_t n, void* out, int32_t* out_idx, float* out_val,
+                                    float* out_logits, void* scratch, size_t scratch_bytes,
+                                    void* stream);
+
+/* ----------------------------------------------------------- pipelines */
+typedef enum {
+    CAMELOT_HANDOFF_GLOBAL = 0,      /* pointer + flag in device memory, no copy (Sec. 6.2) */
+    CAMELOT_HANDOFF_HOST_STAGED = 1  /* D2H to pinned host, then H2D (Sec. 4.2 / 6.1)      */
+} camelot_handoff;
+
+/* Instances and SM quotas per stage: the allocation vector V of Sec. 7.3
+ * ([N_1..N_n, p_1..p_n]) plus the batch size s. */
+typedef struct {
+    int32_t n_stages;
+    int32_t instances[CAMELOT_MAX_STAGES]; /* N_i >= 1                                     */
+    int32_t sm_quota[CAMELOT_MAX_STAGES];  /* p_i: SMs (= CTAs) per instance, >= 1          */
+    int32_t batch;                         /* B: largest batch the trigger forms            */
+} camelot_alloc;
+
+typedef struct {
+    uint32_t query_slots;   /* capacity of the query ring and of the completion ring
+                               (power of two, default 65536)                          */
+    uint32_t batch_slots;   /* capacity of each inter-stage batch ring (default 8)       */
+    int64_t max_wait_ns;    /* batch trigger: a partial batch leaves once its oldest query
+                               has waited this long (default 200000)                   */
+    int64_t idle_exit_ns;   /* the persistent kernel ends after this long without work;
+                               the next submit or poll relaunches it (default 500 ms)  */
+    int64_t wait_limit_ns;  /* every other device wait gives up after this and puts the
+                               pipeline in the error state (default 2 s)               */
+    float* logits_sink;     /* optional device f32 [query_slots][final width]: the final
+                               layer's output of query q lands in row q % query_slots  */
+} camelot_options;
+
+/* Fill `o` with the defaults above. */
+void camelot_options_default(camelot_options* o);
+
+typedef struct camelot_pipeline camelot_pipeline;
+
+/* Build a pipeline of n_stages prepared stages (stage i's output row must be
+ * stage i+1's input row; the last stage must have top_k > 0) with allocation
+ * `alloc` (sum_i N_i * p_i must not exceed the SM count; each stage's
+ * max_batch >= alloc->batch), the given handoff mode and options (NULL =
+ * defaults).  Allocates the rings (device memory; the query and completion
+ * rings in pinned, mapped host memory) and launches the persistent kernel.
+ * The stages must outlive the pipeline.  Errors: EINVAL, ENOMEM, ECUDA. */
+camelot_status camelot_pipeline_create(camelot_stage* const* stages, int n_stages,
+                                       const camelot_alloc* alloc, camelot_handoff mode,
+                                       const camelot_options* opts, camelot_pipeline** out);
+
+/* Queue n queries from host memory (n * stage-0 input row bytes, rows
+ * contiguous); the bytes are copied before return.  Query IDs are assigned
+ * consecutively from *first_query_id (a per-pipeline counter starting at 0).
+ * arrival_ns (host, nullable) gives each query's arrival stamp on the host
+ * CLOCK_MONOTONIC scale; NULL stamps them with the time of the call.  All or
+ * nothing: EAGAIN if fewer than n slots are free (poll to free them), ESTATE
+ * if the pipeline is in the error state or a trace is running. */
+camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id, const void* queries,
+                              uint32_t n, const int64_t* arrival_ns, uint64_t* first_query_id);
+
+/* Replay an arrival trace whose queries already reside in device memory:
+ * query i (bytes at queries + i * row bytes, device) arrives arrival_off_ns[i]
+ * nanoseconds (device int64 array, non-decreasing) after the device starts the
+ * trace; the batch trigger waits for each arrival on the device clock, so the
+ * host is out of the loop.  Requires no outstanding queries and n <=
+ * query_slots.  Completion stamps of trace queries are on the device clock.
+ * The device buffers must stay valid until the trace's completions are polled.
+ * Errors: EINVAL, ESTATE (outstanding queries / error state). */
+camelot_status camelot_submit_trace(camelot_pipeline* p, uint32_t stream_id, const void* queries,
+                                    uint32_t n, const int64_t* arrival_off_ns,
+                                    uint64_t* first_query_id);
+
+typedef struct {
+    uint64_t query_id;
+    uint32_t stream_id;
+    int32_t status;                 /* 0 = ok                                            */
+    int32_t idx[CAMELOT_MAX_TOPK];  /* top-k indices of the final stage (k = its top_k)   */
+    float val[CAMELOT_MAX_TOPK];    /* and their values                                   */
+    int32_t batch_size;             /* size of the batch the query travelled in           */
+    int32_t pad_;
+    int64_t t_arrival_ns;           /* submit: host clock; trace: device clock            */
+    int64_t t_batch_ns;             /* device clock: batch formed by the trigger           */
+    int64_t t_done_ns;              /* device clock: final stage finished                  */
+    int64_t t_poll_ns;              /* host clock: when camelot_poll returned it           */
+} camelot_completion;
+
+/* Copy up to max completions, strictly in query-ID order, into out; *n_out
+ * receives the count.  Waits up to timeout_us (0 = do not wait, < 0 = wait
+ * without a bound) for the first completion.  Returns ETIMEDOUT only if
+ * timeout_us > 0 elapsed with nothing to return; ESTATE (with the completions
+ * delivered so far) if the device reported an error. */
+camelot_status camelot_poll(camelot_pipeline* p, camelot_completion* out, uint32_t max,
+                            uint32_t* n_out, int64_t timeout_us);
+
+typedef struct {
+    uint64_t submitted, completed;          /* query counters                            */
+    uint64_t batches[CAMELOT_MAX_STAGES];   /* batches finished per stage                */
+    uint64_t kernel_launches;               /* persistent-kernel launches so far          */
+    uint64_t relayed_bytes;                 /* host-staged mode: bytes copied D2H + H2D   */
+    uint64_t device_bytes_per_batch_slot;   /* device bytes of one inter-stage slot       */
+    uint64_t device_ring_bytes;             /* device bytes held by all inter-stage rings */
+    int32_t device_status, device_where;    /* first device error (0 = none)              */
+} camelot_stats;
+
+camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);
+
+/* Stop the persistent kernel (it exits at its next check), wait for it and
+ * free every resource.  Completions not yet polled are dropped. */
+camelot_status camelot_pipeline_destroy(camelot_pipeline* p);
+
+/* ------------------------------------------------------------ allocator */
+typedef enum {
+    CAMELOT_POLICY_MAX_PEAK = 0,  /* Eq. 1: maximise min_i N_i f_i(p_i)                   */
+    CAMELOT_POLICY_MIN_SM = 1     /* Eq. 3: minimise sum_i N_i p_i at the given load      */
+} camelot_policy;
+
+typedef enum {
+    CAMELOT_SOLVER_EXHAUSTIVE = 0, /* enumerate every (batch, N, p): exact                */
+    CAMELOT_SOLVER_ANNEAL = 1      /* simulated annealing over V (end of Sec. 7.3)        */
+} camelot_solver;
+
+/* Per-instance performance table (the predicted f, g/bandwidth, duration and
+ * memory of Table 2), for n_stages stages, n_levels SM-quota levels (level l
+ * means (l + 1) * unit SMs) and n_batches candidate batch sizes.  Arrays are
+ * row-major [n_batches][n_stages][n_levels] (mem: [n_batches][n_stages]). */
+typedef struct {
+    int32_t n_stages, n_levels, n_batches, unit;
+    const int32_t* batch_sizes;  /* [n_batches]                                          */
+    const double* thr_qps;       /* f_i(p): queries/s of ONE instance                    */
+    const double* bw_gbs;        /* its global-memory bandwidth demand, GB/s            */
+    const double* dur_s;         /* its duration for one batch, s                        */
+    const double* mem_bytes;     /* its global-memory footprint, bytes                   */
+} camelot_profile;
+
+typedef struct {
+    int32_t total_sms;      /* S (C * R with C = 1 GPU)                                   */
+    int32_t max_instances;  /* I: most instances in total                                 */
+    double bw_gbs;          /* BW: bandwidth budget (Constraint-3)                        */
+    double mem_bytes;       /* F: memory budget (Constraint-4)                            */
+    double qos_s;           /* QoS bound on the sum of stage durations (Constraint-5)     */
+    double load_qps;        /* MIN_SM only: throughput the allocation must sustain        */
+    int32_t solver;         /* camelot_solver                                              */
+    int32_t anneal_iters;   /* annealing: iterations per batch size (default 5000 if 0)   */
+    double anneal_t0;       /* initial temperature (relative; default 1.0 if 0)           */
+    double anneal_alpha;    /* geometric cooling factor (default 0.995 if 0)              */
+    uint64_t seed;          /* annealing random stream (SplitMix64)                        */
+} camelot_constraints;
+
+/* Solve the chosen policy.  On success fills out (n_stages, instances,
+ * sm_quota, batch = batch_sizes[chosen]) and *objective (the min-throughput for
+ * MAX_PEAK, the SM count for MIN_SM).  Constraints: sum N_i p_i <= S, sum N_i <=
+ * I, N_i >= 1, sum N_i bw_i <= BW, sum N_i mem_i <= F, sum_i dur_i <= QoS, and for
+ * MIN_SM min_i N_i f_i >= load.  Ties: better objective, then fewer SMs (MAX_PEAK)
+ * or higher throughput (MIN_SM), then the lexicographically smallest
+ * (batch index, N, level).  Errors: EINVAL, EINFEASIBLE.  Host-only; no GPU use. */
+camelot_status camelot_allocate(const camelot_profile* prof, camelot_policy policy,
+                                const camelot_constraints* c, camelot_alloc* out,
+                                double* objective);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAMELOT_H_ */

@@ -1,0 +1,224 @@
+"""ctypes binding of ``libcamelot.so`` (declared in ``include/camelot.h``).
+
+Argument marshalling only: every step of the query path runs in the library's
+CUDA kernels and C++ runtime.  Functions keep the C names; errors raise
+``CamelotError`` carrying the status code and ``camelot_last_error()``.
+There is no fallback: if the library cannot be loaded, importing fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+MAX_LAYERS, MAX_STAGES, MAX_TOPK = 4, 8, 5
+
+OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, ECUDA, ESTATE, EINFEASIBLE = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EAGAIN", "ETIMEDOUT", "ECUDA", "ESTATE", "EINFEASIBLE"]
+
+STAGE_NORMALIZE_U8, STAGE_NORM_POOL2_BF16, STAGE_MLP_FP32, STAGE_GEMM_BF16 = 1, 2, 3, 4
+ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
+HANDOFF_GLOBAL, HANDOFF_HOST_STAGED = 0, 1
+POLICY_MAX_PEAK, POLICY_MIN_SM = 0, 1
+SOLVER_EXHAUSTIVE, SOLVER_ANNEAL = 0, 1
+
+
+class CamelotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class StageDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
+                ("act", C.c_int32 * MAX_LAYERS), ("top_k", C.c_int32), ("max_batch", C.c_int32),
+                ("weights", C.c_void_p * MAX_LAYERS)]
+
+
+class Alloc(C.Structure):
+    _fields_ = [("n_stages", C.c_int32), ("instances", C.c_int32 * MAX_STAGES),
+                ("sm_quota", C.c_int32 * MAX_STAGES), ("batch", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("query_slots", C.c_uint32), ("batch_slots", C.c_uint32), ("max_wait_ns", C.c_int64),
+                ("idle_exit_ns", C.c_int64), ("wait_limit_ns", C.c_int64),
+                ("logits_sink", C.c_void_p)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("query_id", C.c_uint64), ("stream_id", C.c_uint32), ("status", C.c_int32),
+                ("idx", C.c_int32 * MAX_TOPK), ("val", C.c_float * MAX_TOPK),
+                ("batch_size", C.c_int32), ("pad_", C.c_int32), ("t_arrival_ns", C.c_int64),
+                ("t_batch_ns", C.c_int64), ("t_done_ns", C.c_int64), ("t_poll_ns", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64),
+                ("batches", C.c_uint64 * MAX_STAGES), ("kernel_launches", C.c_uint64),
+                ("relayed_bytes", C.c_uint64), ("device_bytes_per_batch_slot", C.c_uint64),
+                ("device_ring_bytes", C.c_uint64), ("device_status", C.c_int32),
+                ("device_where", C.c_int32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("n_stages", C.c_int32), ("n_levels", C.c_int32), ("n_batches", C.c_int32),
+                ("unit", C.c_int32), ("batch_sizes", C.c_void_p), ("thr_qps", C.c_void_p),
+                ("bw_gbs", C.c_void_p), ("dur_s", C.c_void_p), ("mem_bytes", C.c_void_p)]
+
+
+class Constraints(C.Structure):
+    _fields_ = [("total_sms", C.c_int32), ("max_instances", C.c_int32), ("bw_gbs", C.c_double),
+                ("mem_bytes", C.c_double), ("qos_s", C.c_double), ("load_qps", C.c_double),
+                ("solver", C.c_int32), ("anneal_iters", C.c_int32), ("anneal_t0", C.c_double),
+                ("anneal_alpha", C.c_double), ("seed", C.c_uint64)]
+
+
+# Every symbol include/camelot.h declares, with its ctypes signature.
+P = C.c_void_p
+_SIGS = {
+    "camelot_last_error": (C.c_char_p, []),
+    "camelot_version": (C.c_int, []),
+    "camelot_stage_prepare": (C.c_int, [P, P]),
+    "camelot_stage_release": (C.c_int, [P]),
+    "camelot_stage_info": (C.c_int, [P, P, P, C.c_uint32, P]),
+    "camelot_stage_launch": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P]),
+    "camelot_options_default": (None, [P]),
+    "camelot_pipeline_create": (C.c_int, [P, C.c_int, P, C.c_int, P, P]),
+    "camelot_submit": (C.c_int, [P, C.c_uint32, P, C.c_uint32, P, P]),
+    "camelot_submit_trace": (C.c_int, [P, C.c_uint32, P, C.c_uint32, P, P]),
+    "camelot_poll": (C.c_int, [P, P, C.c_uint32, P, C.c_int64]),
+    "camelot_pipeline_stats": (C.c_int, [P, P]),
+    "camelot_pipeline_destroy": (C.c_int, [P]),
+    "camelot_allocate": (C.c_int, [P, C.c_int, P, P, P]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcamelot.so (building it first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libcamelot.so not found at {path}")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, allow=()):
+    if st != OK and st not in allow:
+        raise CamelotError(st, load().camelot_last_error().decode())
+    return st
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+# ---------------------------------------------------------------------------
+# same-named wrappers
+# ---------------------------------------------------------------------------
+def camelot_version() -> int:
+    return load().camelot_version()
+
+
+def camelot_last_error() -> str:
+    return load().camelot_last_error().decode()
+
+
+def camelot_stage_prepare(desc: StageDesc) -> int:
+    h = C.c_void_p()
+    _check(load().camelot_stage_prepare(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def camelot_stage_release(st: int) -> None:
+    _check(load().camelot_stage_release(st))
+
+
+def camelot_stage_info(st: int, n: int = 1):
+    a, b, s = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _check(load().camelot_stage_info(st, C.byref(a), C.byref(b), n, C.byref(s)))
+    return a.value, b.value, s.value
+
+
+def camelot_stage_launch(st: int, n_ctas: int, inp, n: int, out=None, out_idx=None, out_val=None,
+                         out_logits=None, scratch=None, scratch_bytes: int = 0, stream=None) -> None:
+    _check(load().camelot_stage_launch(st, n_ctas, _ptr(inp), n, _ptr(out), _ptr(out_idx),
+                                       _ptr(out_val), _ptr(out_logits), _ptr(scratch),
+                                       scratch_bytes, _ptr(stream)))
+
+
+def camelot_options_default() -> Options:
+    o = Options()
+    load().camelot_options_default(C.byref(o))
+    return o
+
+
+def camelot_pipeline_create(stages, alloc: Alloc, mode: int, opts: Options | None = None) -> int:
+    arr = (C.c_void_p * len(stages))(*stages)
+    h = C.c_void_p()
+    _check(load().camelot_pipeline_create(arr, len(stages), C.byref(alloc), mode,
+                                          C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h.value
+
+
+def camelot_submit(p: int, stream_id: int, queries, n: int, arrival_ns=None, allow_eagain=False):
+    """Returns the first query ID, or None on EAGAIN when ``allow_eagain``."""
+    first = C.c_uint64()
+    st = _check(load().camelot_submit(p, stream_id, _ptr(queries), n, _ptr(arrival_ns),
+                                      C.byref(first)), allow=(EAGAIN,) if allow_eagain else ())
+    return None if st == EAGAIN else first.value
+
+
+def camelot_submit_trace(p: int, stream_id: int, queries, n: int, arrival_off_ns) -> int:
+    first = C.c_uint64()
+    _check(load().camelot_submit_trace(p, stream_id, _ptr(queries), n, _ptr(arrival_off_ns),
+                                       C.byref(first)))
+    return first.value
+
+
+def camelot_poll(p: int, buf, timeout_us: int = 0, allow_timeout: bool = True) -> int:
+    """Fill ``buf`` (a ctypes array of Completion) and return the count."""
+    n = C.c_uint32()
+    _check(load().camelot_poll(p, buf, len(buf), C.byref(n), timeout_us),
+           allow=(ETIMEDOUT,) if allow_timeout else ())
+    return n.value
+
+
+def camelot_pipeline_stats(p: int) -> Stats:
+    s = Stats()
+    _check(load().camelot_pipeline_stats(p, C.byref(s)))
+    return s
+
+
+def camelot_pipeline_destroy(p: int) -> None:
+    _check(load().camelot_pipeline_destroy(p))
+
+
+def camelot_allocate(prof: Profile, policy: int, cons: Constraints):
+    a = Alloc()
+    obj = C.c_double()
+    _check(load().camelot_allocate(C.byref(prof), policy, C.byref(cons), C.byref(a), C.byref(obj)))
+    return a, obj.value

@@ -1,0 +1,231 @@
+// camelot_allocate: the two contention-aware allocation policies.
+//
+// Peak-load policy (Eq. 1) and low-load resource policy (Eq. 3) over the
+// allocation vector V = [N_1..N_n, p_1..p_n] (end of Sec. 7.3) and a candidate
+// batch size (Eq. 3 makes the batch a variable).  The exhaustive solver walks
+// every stage's (instances, quota level) pairs depth first, pruning a branch
+// as soon as a partial sum already breaks a budget (every table entry is
+// non-negative, so partial sums only grow).  The annealing solver is the
+// paper's: random one-step moves of V, infeasible moves dropped, worse moves
+// accepted with a probability that decays with a geometric temperature,
+// from several starting states.  Host code only.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/camelot.h"
+
+void camelot_internal_set_error(const char* msg);   // runtime.cpp: camelot_last_error's slot
+
+namespace {
+
+camelot_status set_err(camelot_status s, const char* msg) {
+    camelot_internal_set_error(msg);
+    return s;
+}
+
+struct Problem {
+    int n, L, nb, unit, S, I, policy, maxN;
+    const double *f, *bw, *d, *mem;
+    double BW, F, qos, load;
+    size_t k(int b, int i, int l) const { return ((size_t)b * n + i) * L + l; }
+};
+
+// A candidate and its ordering key.
+struct Cand {
+    bool ok = false;
+    int b = 0;
+    std::vector<int> N, l;
+    double thr = 0.0;
+    int sms = 0;
+};
+
+// Is (thr, sms, b, N, l) strictly better than `best`?
+bool better(const Problem& P, double thr, int sms, int b, const int* N, const int* l,
+            const Cand& best) {
+    if (!best.ok) return true;
+    if (P.policy == CAMELOT_POLICY_MAX_PEAK) {
+        if (thr != best.thr) return thr > best.thr;
+        if (sms != best.sms) return sms < best.sms;
+    } else {
+        if (sms != best.sms) return sms < best.sms;
+        if (thr != best.thr) return thr > best.thr;
+    }
+    if (b != best.b) return b < best.b;
+    for (int i = 0; i < P.n; ++i)
+        if (N[i] != best.N[i]) return N[i] < best.N[i];
+    for (int i = 0; i < P.n; ++i)
+        if (l[i] != best.l[i]) return l[i] < best.l[i];
+    return false;
+}
+
+// Full evaluation of one state, summing in stage order.
+bool feasible(const Problem& P, int b, const int* N, const int* l, double* thr, int* sms) {
+    long long sm = 0, inst = 0;
+    double bws = 0.0, mems = 0.0, dur = 0.0, tmin = INFINITY;
+    for (int i = 0; i < P.n; ++i) {
+        if (N[i] < 1 || N[i] > P.maxN || l[i] < 0 || l[i] >= P.L) return false;
+        const size_t k = P.k(b, i, l[i]);
+        sm += (long long)N[i] * (l[i] + 1) * P.unit;
+        inst += N[i];
+        bws += N[i] * P.bw[k];
+        mems += N[i] * P.mem[(size_t)b * P.n + i];
+        dur += P.d[k];
+        tmin = std::min(tmin, N[i] * P.f[k]);
+    }
+    if (sm > P.S || inst > P.I || bws > P.BW || mems > P.F || dur > P.qos) return false;
+    if (P.policy == CAMELOT_POLICY_MIN_SM && tmin < P.load) return false;
+    *thr = tmin;
+    *sms = (int)sm;
+    return true;
+}
+
+struct Dfs {
+    const Problem& P;
+    int b;
+    std::vector<int> N, l;
+    Cand& best;
+    void run(int i, long long sm, long long inst, double bws, double mems, double dur) {
+        if (i == P.n) {
+            double thr;
+            int sms;
+            if (feasible(P, b, N.data(), l.data(), &thr, &sms) &&
+                better(P, thr, sms, b, N.data(), l.data(), best)) {
+                best.ok = true;
+                best.b = b;
+                best.N = N;
+                best.l = l;
+                best.thr = thr;
+                best.sms = sms;
+            }
+            return;
+        }
+        for (int n = 1; n <= P.maxN; ++n) {
+            if (inst + n > P.I) break;
+            const double m2 = mems + n * P.mem[(size_t)b * P.n + i];
+            if (m2 > P.F) break;
+            for (int lv = 0; lv < P.L; ++lv) {
+                const long long sm2 = sm + (long long)n * (lv + 1) * P.unit;
+                if (sm2 > P.S) break;
+                const size_t k = P.k(b, i, lv);
+                const double bw2 = bws + n * P.bw[k];
+                const double d2 = dur + P.d[k];
+                if (bw2 > P.BW || d2 > P.qos) continue;
+                N[i] = n;
+                l[i] = lv;
+                run(i + 1, sm2, inst + n, bw2, m2, d2);
+            }
+        }
+    }
+};
+
+uint64_t sm64(uint64_t* s) {   // SplitMix64 (Steele, Lea & Flood 2014)
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void anneal(const Problem& P, int iters, double T0, double alpha, uint64_t seed, Cand& best) {
+    uint64_t rs = seed ^ 0x5851F42D4C957F2Dull;
+    std::vector<int> N(P.n), l(P.n), N2, l2;
+    // Four walks per batch size: the first from N_i = 1 at the lowest level, the
+    // others from random feasible states, since single-step moves cannot cross
+    // an infeasible gap in V.
+    for (int walk = 0; walk < 4 * P.nb; ++walk) {
+        const int b = walk / 4;
+        std::fill(N.begin(), N.end(), 1);
+        std::fill(l.begin(), l.end(), 0);
+        double thr = 0;
+        int sms = 0;
+        bool have = (walk % 4 == 0) && feasible(P, b, N.data(), l.data(), &thr, &sms);
+        for (int t = 0; t < 20000 && !have; ++t) {
+            for (int i = 0; i < P.n; ++i) {
+                N[i] = 1 + (int)(sm64(&rs) % (uint64_t)P.maxN);
+                l[i] = (int)(sm64(&rs) % (uint64_t)P.L);
+            }
+            have = feasible(P, b, N.data(), l.data(), &thr, &sms);
+        }
+        if (!have) continue;
+        if (better(P, thr, sms, b, N.data(), l.data(), best))
+            best = Cand{true, b, N, l, thr, sms};
+        const double scale = P.policy == CAMELOT_POLICY_MAX_PEAK ? std::max(thr, 1e-300) : (double)P.S;
+        double T = T0;
+        for (int it = 0; it < iters; ++it, T *= alpha) {
+            N2 = N;
+            l2 = l;
+            const uint64_t r = sm64(&rs);
+            const int coord = (int)((r >> 1) % (uint64_t)(2 * P.n));
+            const int step = (r & 1) ? 1 : -1;
+            if (coord < P.n) N2[coord] += step; else l2[coord - P.n] += step;
+            double thr2;
+            int sms2;
+            if (!feasible(P, b, N2.data(), l2.data(), &thr2, &sms2)) continue;
+            const double gain = P.policy == CAMELOT_POLICY_MAX_PEAK ? (thr2 - thr) / scale
+                                                                     : (double)(sms - sms2) / scale;
+            const double u = (sm64(&rs) >> 11) * 0x1.0p-53;
+            if (gain > 0 || (T > 0 && u < std::exp(gain / T))) {
+                N.swap(N2);
+                l.swap(l2);
+                thr = thr2;
+                sms = sms2;
+                if (better(P, thr, sms, b, N.data(), l.data(), best))
+                    best = Cand{true, b, N, l, thr, sms};
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" camelot_status camelot_allocate(const camelot_profile* prof, camelot_policy policy,
+                                           const camelot_constraints* c, camelot_alloc* out,
+                                           double* objective) {
+    if (!prof || !c || !out) return set_err(CAMELOT_EINVAL, "null argument");
+    if (policy != CAMELOT_POLICY_MAX_PEAK && policy != CAMELOT_POLICY_MIN_SM)
+        return set_err(CAMELOT_EINVAL, "unknown policy");
+    if (prof->n_stages < 1 || prof->n_stages > CAMELOT_MAX_STAGES || prof->n_levels < 1 ||
+        prof->n_batches < 1 || prof->unit < 1)
+        return set_err(CAMELOT_EINVAL, "bad profile sizes");
+    if (!prof->thr_qps || !prof->bw_gbs || !prof->dur_s || !prof->mem_bytes || !prof->batch_sizes)
+        return set_err(CAMELOT_EINVAL, "profile table missing");
+    if (c->total_sms < 1 || c->max_instances < 1) return set_err(CAMELOT_EINVAL, "bad constraints");
+    const size_t cells = (size_t)prof->n_batches * prof->n_stages * prof->n_levels;
+    for (size_t i = 0; i < cells; ++i)
+        if (!(prof->thr_qps[i] >= 0) || !(prof->bw_gbs[i] >= 0) || !(prof->dur_s[i] >= 0))
+            return set_err(CAMELOT_EINVAL, "profile entries must be finite and >= 0");
+    for (size_t i = 0; i < (size_t)prof->n_batches * prof->n_stages; ++i)
+        if (!(prof->mem_bytes[i] >= 0)) return set_err(CAMELOT_EINVAL, "memory entries must be >= 0");
+    Problem P{prof->n_stages, prof->n_levels, prof->n_batches, prof->unit, c->total_sms,
+              c->max_instances, (int)policy,
+              std::max(1, std::min(c->max_instances, c->total_sms / prof->unit)),
+              prof->thr_qps, prof->bw_gbs, prof->dur_s, prof->mem_bytes,
+              c->bw_gbs, c->mem_bytes, c->qos_s, c->load_qps};
+    Cand best;
+    if (c->solver == CAMELOT_SOLVER_EXHAUSTIVE) {
+        for (int b = 0; b < P.nb; ++b) {
+            Dfs dfs{P, b, std::vector<int>(P.n, 1), std::vector<int>(P.n, 0), best};
+            dfs.run(0, 0, 0, 0.0, 0.0, 0.0);
+        }
+    } else if (c->solver == CAMELOT_SOLVER_ANNEAL) {
+        anneal(P, c->anneal_iters > 0 ? c->anneal_iters : 5000,
+               c->anneal_t0 > 0 ? c->anneal_t0 : 1.0, c->anneal_alpha > 0 ? c->anneal_alpha : 0.995,
+               c->seed, best);
+    } else {
+        return set_err(CAMELOT_EINVAL, "unknown solver");
+    }
+    if (!best.ok) return set_err(CAMELOT_EINFEASIBLE, "no allocation satisfies the constraints");
+    memset(out, 0, sizeof *out);
+    out->n_stages = P.n;
+    for (int i = 0; i < P.n; ++i) {
+        out->instances[i] = best.N[i];
+        out->sm_quota[i] = (best.l[i] + 1) * P.unit;
+    }
+    out->batch = prof->batch_sizes[best.b];
+    if (objective) *objective = policy == CAMELOT_POLICY_MAX_PEAK ? best.thr : (double)best.sms;
+    return CAMELOT_OK;
+}

@@ -1,0 +1,363 @@
+// Device entry points: the persistent pipeline kernel (all stage instances of
+// a pipeline as CTA groups of one cooperative launch) and the direct launch of
+// a single stage.
+#include <cuda_runtime.h>
+
+#include "pipeline_params.h"
+#include "stages.cuh"
+
+namespace camelot {
+
+// ---------------------------------------------------------------------------
+// Leader side of the per-batch protocol (warp 0 of the instance's CTA 0).
+// ---------------------------------------------------------------------------
+struct LeaderState {
+    unsigned long long seen_h;   // oldest waiting ticket the trigger has seen ...
+    uint64_t seen_t;             // ... and since when (device clock)
+    uint64_t idle_since;
+};
+
+__device__ __forceinline__ bool stop_requested(const PipeParams& P) {
+    return *P.host_stop != 0ull || has_error(P.ctl);
+}
+
+// Claim a free slot of `r` for a new ticket (producer side).  Returns false on
+// timeout (error recorded) or stop.
+__device__ bool reserve_out(const PipeParams& P, const RingDev& r, uint32_t where,
+                            unsigned long long* ticket) {
+    Backoff bo(P.limit_ns);
+    for (;;) {
+        const unsigned long long t = *(volatile unsigned long long*)r.tail;
+        const unsigned long long sq = ld_acquire_gpu(&r.seq[t % r.slots]);
+        if (sq == t) {
+            if (atomicCAS(r.tail, t, t + 1) == t) { *ticket = t; return true; }
+            continue;
+        }
+        if (sq > t) continue;   // stale cursor
+        if (stop_requested(P)) return false;
+        if (!bo.step()) { record_error(P.ctl, DEV_ERR_OUT_SLOT, where); return false; }
+    }
+}
+
+// Stage 0: the wait queue and batch trigger (Sec. 5.2 steps 1-2).  A batch of
+// the oldest waiting tickets leaves when B of them are ready, or when the
+// oldest has waited max_wait_ns.  Executed by warp 0 of the leader CTA; lane 0
+// returns the command.  Writes the per-query metadata of the claimed tickets
+// into their completion slots.
+__device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
+                                       unsigned long long* first, unsigned int* n_out,
+                                       bool* from_trace, long long* t_batch) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        // every decision below is taken on lane 0's view, so the warp stays converged
+        const int stop = __shfl_sync(0xffffffffu, lane == 0 ? (int)stop_requested(P) : 0, 0);
+        if (stop) return CMD_EXIT;
+        const unsigned long long h =
+            __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&P.ctl->in_head.v, 0);
+        const uint64_t now = __shfl_sync(0xffffffffu, gtime(), 0);
+        const TraceDev* tr = P.trace;
+        const unsigned int armed = __shfl_sync(0xffffffffu, *(volatile unsigned int*)&tr->armed, 0);
+        const unsigned long long tb =
+            __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&tr->base, 0);
+        const unsigned long long tn =
+            __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&tr->n, 0);
+        bool trace = armed && h >= tb && h < tb + tn;
+        int avail;
+        bool ready = false;
+        long long arr = 0, oldest = 0;
+        unsigned int sid = 0;
+        if (trace) {
+            unsigned long long t0 = 0;
+            if (lane == 0) {
+                t0 = *(volatile unsigned long long*)&P.ctl->trace_t0.v;
+                if (t0 == 0ull) {
+                    const unsigned long long prev = atomicCAS(&P.ctl->trace_t0.v, 0ull, now);
+                    t0 = prev == 0ull ? now : prev;
+                }
+            }
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            avail = (int)min((unsigned long long)P.B, tb + tn - h);
+            if (lane < avail) {
+                arr = (long long)t0 + tr->off[h - tb + lane];
+                ready = (uint64_t)arr <= now;
+            }
+            oldest = (long long)t0 + tr->off[h - tb];
+            sid = tr->stream_id;
+        } else {
+            avail = P.B;
+            if (lane < avail) {
+                const QDesc& d = P.qring[(h + lane) & P.qmask];
+                ready = ld_acquire_sys(&d.seq) == h + lane + 1;
+                if (ready) { arr = d.t_arrival; sid = d.stream_id; }
+            }
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, ready);
+        const int k = __ffs(~bal) - 1 < 0 ? 32 : __ffs(~bal) - 1;   // ready prefix length
+        const int kk = min(k, avail);
+        if (kk == 0) {
+            const int idle_out = __shfl_sync(
+                0xffffffffu, (!trace && now - ls.idle_since > (uint64_t)P.idle_ns) ? 1 : 0, 0);
+            if (idle_out) return CMD_EXIT;
+            __nanosleep(trace ? 200 : 500);
+            continue;
+        }
+        if (!trace && ls.seen_h != h) { ls.seen_h = h; ls.seen_t = now; }
+        const uint64_t waited = trace ? (now - (uint64_t)oldest) : (now - ls.seen_t);
+        if (kk < P.B && waited < (uint64_t)P.max_wait_ns) { __nanosleep(200); continue; }
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicCAS(&P.ctl->in_head.v, h, h + kk);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got != h) continue;
+        // the tickets [h, h + kk) are ours: record their metadata
+        if (lane < kk) {
+            camelot_completion& c = P.comp[(h + lane) & P.cmask].c;
+            c.query_id = h + lane;
+            c.stream_id = sid;
+            c.status = 0;
+            c.batch_size = kk;
+            c.t_arrival_ns = arr;
+            c.t_batch_ns = (long long)now;
+        }
+        *first = h;
+        *n_out = (unsigned)kk;
+        *from_trace = trace;
+        *t_batch = (long long)now;
+        ls.idle_since = now;
+        return CMD_WORK;
+    }
+}
+
+// Stage s >= 1: take the oldest published batch of the input ring.
+__device__ unsigned int stageN_acquire(const PipeParams& P, int s, LeaderState& ls,
+                                       unsigned long long* slot_ticket, unsigned long long* first,
+                                       unsigned int* n_out, long long* t_batch) {
+    const RingDev& r = P.in_ring[s];
+    const unsigned long long* up_tail = P.out_ring[s - 1].tail;
+    const uint64_t bound = (uint64_t)P.idle_ns * (uint64_t)(s + 2) + (uint64_t)P.limit_ns;
+    for (;;) {
+        if (stop_requested(P)) return CMD_EXIT;
+        const unsigned long long h = *(volatile unsigned long long*)r.head;
+        const unsigned long long sq = ld_acquire_gpu(&r.seq[h % r.slots]);
+        if (sq == h + 1) {
+            if (atomicCAS(r.head, h, h + 1) != h) continue;
+            const volatile BatchHdr* vh = &r.hdr[h % r.slots];
+            const unsigned int hn = vh->n;
+            if (hn == 0 || hn > (unsigned)P.B) {
+                record_error(P.ctl, DEV_ERR_BAD_BATCH, s);
+                return CMD_EXIT;
+            }
+            *slot_ticket = h;
+            *first = vh->first;
+            *n_out = hn;
+            *t_batch = vh->t_batch;
+            ls.idle_since = gtime();
+            return CMD_WORK;
+        }
+        // empty: done once the upstream stage has exited and everything it
+        // produced has been taken
+        const unsigned long long ex = *(volatile unsigned long long*)&P.ctl->exited[s - 1].v;
+        if (ex >= (unsigned long long)P.inst[s - 1] &&
+            h >= *(volatile unsigned long long*)up_tail)
+            return CMD_EXIT;
+        if (gtime() - ls.idle_since > bound) {
+            record_error(P.ctl, DEV_ERR_MAILBOX, 100 + s);
+            return CMD_EXIT;
+        }
+        __nanosleep(300);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams* __restrict__ pp) {
+    extern __shared__ float4 smem4[];
+    const PipeParams& P = *pp;
+    const int b = blockIdx.x;
+    int s = 0;
+    while (s + 1 < P.n_stages && b >= P.cta_begin[s + 1]) ++s;
+    const int local = b - P.cta_begin[s];
+    const int inst = local / P.quota[s];
+    const int rank = local - inst * P.quota[s];
+    GroupSync* gs = P.groups + P.inst_begin[s] + inst;
+    StageCtx cx{rank, P.quota[s], gs, P.ctl, (uint64_t)P.limit_ns, (uint32_t)s,
+                P.scratch + P.scratch_off[s] + (size_t)inst * P.inst_scratch[s],
+                reinterpret_cast<float*>(smem4)};
+    const StageParams& SP = P.st[s];
+    const bool final_stage = (s == P.n_stages - 1);
+    const bool leader = (rank == 0);
+
+    __shared__ unsigned int sh_cmd, sh_n, sh_trace;
+    __shared__ unsigned long long sh_in, sh_first, sh_out;
+    __shared__ long long sh_tb;
+    LeaderState ls{~0ull, 0, gtime()};
+
+    for (;;) {
+        // ---- the leader finds work and posts it in the instance's mailbox
+        if (leader && threadIdx.x < 32) {
+            unsigned int cmd, n = 0;
+            unsigned long long in_t = 0, first = 0, out_t = 0;
+            bool tr = false;
+            long long tb = 0;
+            if (s == 0) {
+                cmd = stage0_acquire(P, ls, &first, &n, &tr, &tb);
+                in_t = first;
+            } else {
+                if (threadIdx.x == 0) cmd = stageN_acquire(P, s, ls, &in_t, &first, &n, &tb);
+                cmd = __shfl_sync(0xffffffffu, cmd, 0);
+            }
+            if (threadIdx.x == 0) {
+                if (cmd == CMD_WORK && !final_stage && !reserve_out(P, P.out_ring[s], s, &out_t))
+                    cmd = CMD_EXIT;
+                gs->cmd = cmd;
+                gs->n = n;
+                gs->in_ticket = in_t;
+                gs->out_ticket = out_t;
+                gs->t_batch = tb;
+                gs->from_trace = tr ? 1u : 0u;
+                gs->first = first;
+            }
+        }
+        // ---- broadcast (a group barrier whose wait covers the leader's idle time)
+        if (!group_barrier(gs, cx.nctas, P.ctl, (uint64_t)P.idle_ns * (uint64_t)(P.n_stages + 2) +
+                                                     2ull * (uint64_t)P.limit_ns,
+                           200 + s, DEV_ERR_MAILBOX))
+            break;
+        if (threadIdx.x == 0) {
+            volatile GroupSync* vg = gs;
+            sh_cmd = vg->cmd;
+            sh_n = vg->n;
+            sh_in = vg->in_ticket;
+            sh_out = vg->out_ticket;
+            sh_tb = vg->t_batch;
+            sh_trace = vg->from_trace;
+            sh_first = vg->first;
+        }
+        __syncthreads();
+        if (sh_cmd != CMD_WORK) break;
+        const int n = (int)sh_n;
+        const unsigned long long first = sh_first;
+
+        // ---- inputs and outputs of this batch
+        RowRef in;
+        if (s == 0) {
+            if (sh_trace) {
+                const TraceDev* tr = P.trace;
+                in = RowRef{const_cast<char*>(tr->data) + (first - tr->base) * P.q_row, 0, ~0ull,
+                            P.q_row};
+            } else {
+                in = RowRef{P.qdata, first, P.qmask, P.q_row};
+            }
+        } else {
+            const RingDev& r = P.in_ring[s];
+            in = RowRef{r.data + (sh_in % r.slots) * r.slot_bytes, 0, ~0ull, SP.in_row_bytes};
+        }
+        RowRef out{nullptr, 0, ~0ull, 0};
+        if (!final_stage) {
+            const RingDev& r = P.out_ring[s];
+            out = RowRef{r.data + (sh_out % r.slots) * r.slot_bytes, 0, ~0ull, SP.out_row_bytes};
+        }
+        FinalOut fo{reinterpret_cast<int32_t*>(cx.scratch + SP.res_off),
+                    reinterpret_cast<float*>(cx.scratch + SP.res_off) + (size_t)P.B * kMaxTopK,
+                    RowRef{reinterpret_cast<char*>(P.sink), first, P.cmask, P.sink_ld * sizeof(float)}};
+        if (P.sink == nullptr) fo.logits.base = nullptr;
+
+        if (!stage_body(cx, SP, in, n, out, fo)) break;
+        if (!group_barrier(gs, cx.nctas, P.ctl, P.limit_ns, 300 + s)) break;
+
+        // ---- the leader publishes the result and releases the input
+        if (leader) {
+            if (final_stage) {
+                __shared__ long long sh_done;
+                if (threadIdx.x == 0) sh_done = (long long)gtime();
+                __syncthreads();
+                const int k = SP.top_k;
+                for (int q = threadIdx.x; q < n; q += kThreads) {
+                    CompSlot& cs = P.comp[(first + q) & P.cmask];
+                    for (int r = 0; r < kMaxTopK; ++r) {
+                        cs.c.idx[r] = r < k ? fo.idx[(size_t)q * k + r] : -1;
+                        cs.c.val[r] = r < k ? fo.val[(size_t)q * k + r] : 0.f;
+                    }
+                    cs.c.t_done_ns = sh_done;
+                    __threadfence_system();
+                    st_release_sys(&cs.seq, first + q + 1);
+                }
+            } else if (threadIdx.x == 0) {
+                const RingDev& r = P.out_ring[s];
+                const unsigned int slot = (unsigned int)(sh_out % r.slots);
+                BatchHdr& hd = r.hdr[slot];
+                hd.first = first;
+                hd.n = (unsigned)n;
+                hd.t_batch = sh_tb;
+                __threadfence();
+                st_release_gpu(&r.seq[slot], sh_out + 1);
+                if (r.note_pub != nullptr) {
+                    r.note_n[slot] = (unsigned)n;
+                    __threadfence_system();
+                    st_release_sys(&r.note_pub[slot], sh_out + 1);
+                }
+            }
+            if (s == 0) {
+                if (!sh_trace) {
+                    const unsigned long long R = P.qmask + 1;
+                    for (int q = threadIdx.x; q < n; q += kThreads)
+                        st_release_sys(&P.qring[(first + q) & P.qmask].seq, first + q + R);
+                }
+            } else if (threadIdx.x == 0) {
+                const RingDev& r = P.in_ring[s];
+                const unsigned int slot = (unsigned int)(sh_in % r.slots);
+                st_release_gpu(&r.seq[slot], sh_in + r.slots);
+                if (r.note_free != nullptr) st_release_sys(&r.note_free[slot], sh_in + r.slots);
+            }
+            if (threadIdx.x == 0) atomicAdd(&P.ctl->batches[s].v, 1ull);
+        }
+    }
+    __syncthreads();
+    if (leader && threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&P.ctl->exited[s].v, 1ull);
+        const unsigned long long st = ld_relaxed_gpu(&P.ctl->status.v);
+        if (st != 0ull) *P.host_status = st;
+    }
+}
+
+// Direct launch of one stage over one batch: the whole grid is one instance.
+__global__ void __launch_bounds__(kThreads, 1)
+    stage_direct_kernel(const StageParams* __restrict__ sp, RowRef in, int n, RowRef out,
+                        int32_t* idx, float* val, RowRef logits, char* scratch, GroupSync* gs,
+                        Ctl* ctl, long long limit_ns) {
+    extern __shared__ float4 smem4[];
+    StageCtx cx{(int)blockIdx.x, (int)gridDim.x, gs, ctl, (uint64_t)limit_ns, 0u, scratch,
+                reinterpret_cast<float*>(smem4)};
+    FinalOut fo{idx, val, logits};
+    stage_body(cx, *sp, in, n, out, fo);
+}
+
+}  // namespace camelot
+
+// Host-callable launch helpers (used by the runtime in runtime.cpp).
+namespace camelot {
+cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream) {
+    void* args[] = {(void*)&dparams};
+    return cudaLaunchCooperativeKernel((const void*)pipeline_kernel, dim3(grid), dim3(kThreads),
+                                       args, kSmemBytes, stream);
+}
+
+cudaError_t launch_stage_direct(const StageParams* dsp, RowRef in, int n, RowRef out, int32_t* idx,
+                                float* val, RowRef logits, char* scratch, GroupSync* gs, Ctl* ctl,
+                                long long limit_ns, int grid, cudaStream_t stream) {
+    void* args[] = {(void*)&dsp, &in, &n, &out, &idx, &val, &logits, &scratch, &gs, &ctl, &limit_ns};
+    return cudaLaunchCooperativeKernel((const void*)stage_direct_kernel, dim3(grid), dim3(kThreads),
+                                       args, kSmemBytes, stream);
+}
+
+cudaError_t configure_kernels() {
+    cudaError_t e = cudaFuncSetAttribute((const void*)pipeline_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)stage_direct_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
+cudaError_t max_coresident_ctas(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)pipeline_kernel,
+                                                         kThreads, kSmemBytes);
+}
+}  // namespace camelot

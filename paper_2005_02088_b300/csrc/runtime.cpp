@@ -1,0 +1,854 @@
+// Host runtime of libcamelot: stage preparation, pipeline rings and lifecycle,
+// submission, completion polling, trace replay and the host-staged relay.
+#include <cuda_runtime.h>
+#include <time.h>
+#include <immintrin.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/camelot.h"
+#include "pipeline_params.h"
+
+namespace camelot {
+cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream);
+cudaError_t launch_stage_direct(const StageParams* dsp, RowRef in, int n, RowRef out, int32_t* idx,
+                                float* val, RowRef logits, char* scratch, GroupSync* gs, Ctl* ctl,
+                                long long limit_ns, int grid, cudaStream_t stream);
+cudaError_t configure_kernels();
+cudaError_t max_coresident_ctas(int* per_sm);
+}  // namespace camelot
+
+using namespace camelot;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static camelot_status fail(camelot_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? CAMELOT_ENOMEM : CAMELOT_ECUDA,   \
+                        "%s failed: %s", #expr, cudaGetErrorString(e_));                   \
+    } while (0)
+
+extern "C" const char* camelot_last_error(void) { return g_err.c_str(); }
+void camelot_internal_set_error(const char* msg) { g_err = msg; }
+extern "C" int camelot_version(void) { return 100; }
+
+static int64_t host_now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static camelot_status ensure_configured() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] { err = configure_kernels(); });
+    if (err != cudaSuccess) return fail(CAMELOT_ECUDA, "kernel configuration failed: %s",
+                                        cudaGetErrorString(err));
+    return CAMELOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------
+struct camelot_stage {
+    camelot_stage_desc desc;
+    StageParams sp;            // host copy (device pointers inside)
+    StageParams* d_sp = nullptr;
+    std::vector<void*> allocs; // device buffers owned by the stage
+    int device = 0;
+};
+
+static void stage_free(camelot_stage* st) {
+    for (void* p : st->allocs) cudaFree(p);
+    if (st->d_sp) cudaFree(st->d_sp);
+    delete st;
+}
+
+// K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, 128].
+static int choose_kc(int K) {
+    int kc = (K + 127) / 128;
+    kc = (kc + 3) / 4 * 4;
+    kc = std::max(32, std::min(kMaxKC, kc));
+    return std::min(kc, K);
+}
+
+// Scratch layout of one instance for batches of up to B rows.
+static size_t layout_scratch(StageParams& sp, int B) {
+    size_t p_bytes = 0, h_bytes = 0;
+    for (int l = 0; l < sp.n_layers; ++l) {
+        LayerParams& L = sp.layer[l];
+        if (!L.head) p_bytes = std::max(p_bytes, (size_t)L.C * B * L.Npad * sizeof(float));
+        h_bytes = std::max(h_bytes, (size_t)B * L.N * sizeof(float));
+    }
+    size_t off = 0;
+    const size_t p_off = off;
+    off = align_up(off + p_bytes, 256);
+    const size_t h0 = off;
+    off = align_up(off + h_bytes, 256);
+    const size_t h1 = off;
+    off = align_up(off + h_bytes, 256);
+    for (int l = 0; l < sp.n_layers; ++l) {
+        sp.layer[l].p_off = p_off;
+        sp.layer[l].h_off = (l % 2 == 0) ? h0 : h1;
+    }
+    sp.res_off = off;
+    off = align_up(off + (size_t)B * kMaxTopK * 8, 256);
+    return off;
+}
+
+extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, camelot_stage** out) {
+    if (!d || !out) return fail(CAMELOT_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->max_batch < 1 || d->max_batch > 256)
+        return fail(CAMELOT_EINVAL, "max_batch %d outside 1..256", d->max_batch);
+    if (d->top_k < 0 || d->top_k > kMaxTopK)
+        return fail(CAMELOT_EINVAL, "top_k %d outside 0..%d", d->top_k, kMaxTopK);
+    camelot_status cs = ensure_configured();
+    if (cs != CAMELOT_OK) return cs;
+    StageParams sp{};
+    sp.kind = d->kind;
+    sp.top_k = d->top_k;
+    sp.max_batch = d->max_batch;
+    auto* st = new camelot_stage();
+    st->desc = *d;
+    cudaGetDevice(&st->device);
+    auto bail = [&](camelot_status s) { stage_free(st); return s; };
+
+    switch (d->kind) {
+        case CAMELOT_STAGE_NORMALIZE_U8:
+        case CAMELOT_STAGE_NORM_POOL2_BF16: {
+            const int H = d->dims[0], W = d->dims[1], C = d->dims[2];
+            if (H <= 0 || W <= 0 || C <= 0) return bail(fail(CAMELOT_EINVAL, "image dims must be > 0"));
+            if (d->top_k != 0) return bail(fail(CAMELOT_EINVAL, "image stages cannot be final"));
+            sp.H = H; sp.W = W; sp.C = C;
+            sp.in_row_bytes = (size_t)H * W * C;
+            if (d->kind == CAMELOT_STAGE_NORMALIZE_U8) {
+                if (sp.in_row_bytes % 16)
+                    return bail(fail(CAMELOT_EINVAL, "H*W*C must be a multiple of 16"));
+                sp.out_row_bytes = sp.in_row_bytes * 4;
+            } else {
+                if (H % 2 || W % 2) return bail(fail(CAMELOT_EINVAL, "H and W must be even"));
+                if ((2 * W * C) % 16 || 2 * W * C > 8192)
+                    return bail(fail(CAMELOT_EINVAL, "2*W*C must be a multiple of 16 and <= 8192"));
+                sp.out_row_bytes = (size_t)(H / 2) * (W / 2) * C * 2;
+            }
+            sp.scratch_bytes = 0;
+            break;
+        }
+        case CAMELOT_STAGE_MLP_FP32: {
+            const int L = d->n_layers;
+            if (L < 1 || L > kMaxLayers) return bail(fail(CAMELOT_EINVAL, "n_layers %d outside 1..4", L));
+            for (int l = 0; l <= L; ++l)
+                if (d->dims[l] <= 0) return bail(fail(CAMELOT_EINVAL, "dims[%d] must be > 0", l));
+            for (int l = 0; l < L; ++l) {
+                if (d->dims[l] % 4) return bail(fail(CAMELOT_EINVAL, "layer input width dims[%d]=%d must be a multiple of 4", l, d->dims[l]));
+                if (!d->weights[l]) return bail(fail(CAMELOT_EINVAL, "weights[%d] is null", l));
+                if (d->act[l] < 0 || d->act[l] > 2) return bail(fail(CAMELOT_EINVAL, "act[%d] invalid", l));
+            }
+            if (d->top_k > d->dims[L]) return bail(fail(CAMELOT_EINVAL, "top_k exceeds the final width"));
+            sp.n_layers = L;
+            sp.in_row_bytes = (size_t)d->dims[0] * 4;
+            sp.out_row_bytes = d->top_k ? 0 : (size_t)d->dims[L] * 4;
+            if (!d->top_k && d->dims[L] % 4)
+                return bail(fail(CAMELOT_EINVAL, "an intermediate stage's output width must be a multiple of 4"));
+            sp.out_width = d->dims[L];
+            for (int l = 0; l < L; ++l) {
+                LayerParams& Lp = sp.layer[l];
+                const int K = d->dims[l], N = d->dims[l + 1];
+                Lp.K = K; Lp.N = N; Lp.act = d->act[l];
+                Lp.head = (l == L - 1 && d->top_k > 0 && N <= 32) ? 1 : 0;
+                std::vector<float> w((size_t)N * K);
+                if (cudaMemcpy(w.data(), d->weights[l], w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return bail(fail(CAMELOT_EINVAL, "weights[%d] is not readable device memory", l));
+                std::vector<float> packed;
+                if (Lp.head) {
+                    Lp.Npad = N; Lp.KC = K; Lp.C = 1;
+                    packed = std::move(w);
+                } else {
+                    Lp.Npad = (N + kNBlock - 1) / kNBlock * kNBlock;
+                    Lp.KC = choose_kc(K);
+                    Lp.C = (K + Lp.KC - 1) / Lp.KC;
+                    packed.assign((size_t)(K / 4) * Lp.Npad * 4, 0.f);
+                    for (int kq = 0; kq < K / 4; ++kq)
+                        for (int n = 0; n < N; ++n)
+                            for (int j = 0; j < 4; ++j)
+                                packed[((size_t)kq * Lp.Npad + n) * 4 + j] = w[(size_t)n * K + 4 * kq + j];
+                }
+                void* dp = nullptr;
+                if (cudaMalloc(&dp, packed.size() * 4) != cudaSuccess)
+                    return bail(fail(CAMELOT_ENOMEM, "weight copy allocation failed"));
+                st->allocs.push_back(dp);
+                if (cudaMemcpy(dp, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                    return bail(fail(CAMELOT_ECUDA, "weight upload failed"));
+                Lp.w = (const float*)dp;
+            }
+            sp.scratch_bytes = layout_scratch(sp, d->max_batch);
+            break;
+        }
+        case CAMELOT_STAGE_GEMM_BF16:
+            return bail(fail(CAMELOT_EINVAL, "GEMM_BF16 stages are not available in this build"));
+        default:
+            return bail(fail(CAMELOT_EINVAL, "unknown stage kind %d", d->kind));
+    }
+    st->sp = sp;
+    if (cudaMalloc(&st->d_sp, sizeof(StageParams)) != cudaSuccess)
+        return bail(fail(CAMELOT_ENOMEM, "allocation failed"));
+    if (cudaMemcpy(st->d_sp, &st->sp, sizeof(StageParams), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(CAMELOT_ECUDA, "upload failed"));
+    *out = st;
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_stage_release(camelot_stage* st) {
+    if (!st) return fail(CAMELOT_EINVAL, "null stage");
+    stage_free(st);
+    return CAMELOT_OK;
+}
+
+static const size_t kDirectHeader = align_up(sizeof(Ctl), 256) + align_up(sizeof(GroupSync), 256);
+
+extern "C" camelot_status camelot_stage_info(const camelot_stage* st, size_t* in_row,
+                                             size_t* out_row, uint32_t n, size_t* scratch) {
+    if (!st) return fail(CAMELOT_EINVAL, "null stage");
+    if (in_row) *in_row = st->sp.in_row_bytes;
+    if (out_row) *out_row = st->sp.out_row_bytes;
+    if (scratch) *scratch = kDirectHeader + st->sp.scratch_bytes;   // laid out for max_batch
+    (void)n;
+    return CAMELOT_OK;
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+extern "C" camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const void* in,
+                                               uint32_t n, void* out, int32_t* out_idx,
+                                               float* out_val, float* out_logits, void* scratch,
+                                               size_t scratch_bytes, void* stream) {
+    if (!st) return fail(CAMELOT_EINVAL, "null stage");
+    const StageParams& sp = st->sp;
+    if (n == 0 || (int)n > sp.max_batch)
+        return fail(CAMELOT_EINVAL, "n=%u outside 1..max_batch=%d", n, sp.max_batch);
+    if (n_ctas < 1 || n_ctas > sm_count())
+        return fail(CAMELOT_EINVAL, "n_ctas=%d outside 1..%d", n_ctas, sm_count());
+    if (!in) return fail(CAMELOT_EINVAL, "null input");
+    if (sp.top_k == 0 && !out) return fail(CAMELOT_EINVAL, "intermediate stage needs `out`");
+    if (sp.top_k > 0 && (!out_idx || !out_val)) return fail(CAMELOT_EINVAL, "final stage needs out_idx and out_val");
+    size_t need = 0;
+    camelot_stage_info(st, nullptr, nullptr, n, &need);
+    if (!scratch || scratch_bytes < need)
+        return fail(CAMELOT_EINVAL, "scratch of %zu bytes needed, %zu given", need, scratch_bytes);
+    if (((uintptr_t)scratch) % 256) return fail(CAMELOT_EINVAL, "scratch must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)scratch;
+    Ctl* ctl = (Ctl*)base;
+    GroupSync* gs = (GroupSync*)(base + align_up(sizeof(Ctl), 256));
+    CUDA_TRY(cudaMemsetAsync(base, 0, kDirectHeader, s));
+    RowRef rin{(char*)in, 0, ~0ull, sp.in_row_bytes};
+    RowRef rout{(char*)out, 0, ~0ull, sp.out_row_bytes};
+    RowRef rlog{(char*)out_logits, 0, ~0ull, sp.out_width * sizeof(float)};
+    CUDA_TRY(launch_stage_direct(st->d_sp, rin, (int)n, rout, out_idx, out_val, rlog,
+                                 base + kDirectHeader, gs, ctl, 2000000000ll, n_ctas, s));
+    return CAMELOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pipelines
+// ---------------------------------------------------------------------------
+extern "C" void camelot_options_default(camelot_options* o) {
+    if (!o) return;
+    o->query_slots = 65536;
+    o->batch_slots = 8;
+    o->max_wait_ns = 200000;
+    o->idle_exit_ns = 500000000;
+    o->wait_limit_ns = 2000000000;
+    o->logits_sink = nullptr;
+}
+
+struct HostRing {   // one batch ring's allocations
+    unsigned long long* seq = nullptr;
+    BatchHdr* hdr = nullptr;
+    char* data = nullptr;
+    unsigned long long* cursors = nullptr;   // [head line, tail line]
+    unsigned int slots = 0;
+    size_t slot_bytes = 0;
+    // host-staged
+    unsigned long long* note_pub = nullptr;
+    unsigned int* note_n = nullptr;
+    unsigned long long* note_free = nullptr;
+};
+
+struct camelot_pipeline {
+    int device = 0;
+    int n_stages = 0;
+    camelot_stage* stages[kMaxStages] = {};
+    camelot_alloc alloc{};
+    camelot_handoff mode = CAMELOT_HANDOFF_GLOBAL;
+    camelot_options opt{};
+    int grid = 0;
+    PipeParams hp{};
+    PipeParams* dp = nullptr;
+    Ctl* ctl = nullptr;
+    HostFlags* hflags = nullptr;       // pinned
+    unsigned long long* hstatus = nullptr;  // pinned (inside hflags' page)
+    GroupSync* groups = nullptr;
+    char* scratch = nullptr;
+    HostRing out_rings[kMaxStages], in_rings[kMaxStages];
+    QDesc* qring = nullptr;            // pinned
+    char* qdata = nullptr;             // pinned
+    CompSlot* comp = nullptr;          // pinned
+    TraceDev* trace = nullptr;         // device
+    cudaStream_t kstream = nullptr, side = nullptr;
+    cudaEvent_t kdone = nullptr;
+    bool launched = false;
+    std::mutex launch_mu;
+    std::atomic<uint64_t> next_ticket{0};
+    std::atomic<uint64_t> next_poll{0};
+    uint64_t launches = 0;
+    bool trace_active = false;
+    uint64_t trace_end = 0;
+    std::atomic<bool> failed{false};
+    std::string fail_msg;
+    // relay (host-staged)
+    std::thread relay;
+    std::atomic<bool> relay_stop{false};
+    std::atomic<uint64_t> relayed_bytes{0};
+    cudaStream_t r_d2h[kMaxStages] = {}, r_h2d[kMaxStages] = {};
+    std::vector<cudaEvent_t> r_ev[kMaxStages];
+    char* r_stage[kMaxStages] = {};          // pinned staging [slots][slot_bytes]
+    BatchHdr* r_hdr[kMaxStages] = {};        // pinned
+    unsigned long long* r_valA[kMaxStages] = {};
+    unsigned long long* r_valB[kMaxStages] = {};
+    std::atomic<int> relay_err{0};
+};
+
+static void free_ring(HostRing& r) {
+    if (r.seq) cudaFree(r.seq);
+    if (r.hdr) cudaFree(r.hdr);
+    if (r.data) cudaFree(r.data);
+    if (r.cursors) cudaFree(r.cursors);
+    if (r.note_pub) cudaFreeHost(r.note_pub);
+    if (r.note_n) cudaFreeHost(r.note_n);
+    if (r.note_free) cudaFreeHost(r.note_free);
+    r = HostRing{};
+}
+
+static camelot_status alloc_ring(HostRing& r, unsigned slots, size_t slot_bytes, bool notes) {
+    r.slots = slots;
+    r.slot_bytes = slot_bytes;
+    CUDA_TRY(cudaMalloc(&r.seq, slots * sizeof(unsigned long long)));
+    CUDA_TRY(cudaMalloc(&r.hdr, slots * sizeof(BatchHdr)));
+    CUDA_TRY(cudaMalloc(&r.data, slots * slot_bytes));
+    CUDA_TRY(cudaMalloc(&r.cursors, 2 * sizeof(Line64)));
+    CUDA_TRY(cudaMemset(r.cursors, 0, 2 * sizeof(Line64)));
+    CUDA_TRY(cudaMemset(r.hdr, 0, slots * sizeof(BatchHdr)));
+    std::vector<unsigned long long> iota(slots);
+    for (unsigned i = 0; i < slots; ++i) iota[i] = i;
+    CUDA_TRY(cudaMemcpy(r.seq, iota.data(), slots * 8, cudaMemcpyHostToDevice));
+    if (notes) {
+        CUDA_TRY(cudaHostAlloc((void**)&r.note_pub, slots * 8, cudaHostAllocMapped | cudaHostAllocPortable));
+        CUDA_TRY(cudaHostAlloc((void**)&r.note_n, slots * 4, cudaHostAllocMapped | cudaHostAllocPortable));
+        CUDA_TRY(cudaHostAlloc((void**)&r.note_free, slots * 8, cudaHostAllocMapped | cudaHostAllocPortable));
+        for (unsigned i = 0; i < slots; ++i) {
+            r.note_pub[i] = 0;
+            r.note_n[i] = 0;
+            r.note_free[i] = i;
+        }
+    }
+    return CAMELOT_OK;
+}
+
+static RingDev ring_view(const HostRing& r) {
+    RingDev v{};
+    v.seq = r.seq;
+    v.hdr = r.hdr;
+    v.data = r.data;
+    v.head = r.cursors;
+    v.tail = (unsigned long long*)((char*)r.cursors + sizeof(Line64));
+    v.slots = r.slots;
+    v.slot_bytes = r.slot_bytes;
+    v.note_pub = r.note_pub;
+    v.note_n = r.note_n;
+    v.note_free = r.note_free;
+    return v;
+}
+
+static void pipeline_free(camelot_pipeline* p) {
+    if (p->relay.joinable()) {
+        p->relay_stop = true;
+        p->relay.join();
+    }
+    if (p->kstream) cudaStreamSynchronize(p->kstream);
+    for (int s = 0; s < kMaxStages; ++s) {
+        free_ring(p->out_rings[s]);
+        free_ring(p->in_rings[s]);
+        if (p->r_d2h[s]) cudaStreamDestroy(p->r_d2h[s]);
+        if (p->r_h2d[s]) cudaStreamDestroy(p->r_h2d[s]);
+        for (auto e : p->r_ev[s]) cudaEventDestroy(e);
+        if (p->r_stage[s]) cudaFreeHost(p->r_stage[s]);
+        if (p->r_hdr[s]) cudaFreeHost(p->r_hdr[s]);
+        if (p->r_valA[s]) cudaFreeHost(p->r_valA[s]);
+        if (p->r_valB[s]) cudaFreeHost(p->r_valB[s]);
+    }
+    if (p->dp) cudaFree(p->dp);
+    if (p->ctl) cudaFree(p->ctl);
+    if (p->groups) cudaFree(p->groups);
+    if (p->scratch) cudaFree(p->scratch);
+    if (p->trace) cudaFree(p->trace);
+    if (p->hflags) cudaFreeHost(p->hflags);
+    if (p->qring) cudaFreeHost(p->qring);
+    if (p->qdata) cudaFreeHost(p->qdata);
+    if (p->comp) cudaFreeHost(p->comp);
+    if (p->kdone) cudaEventDestroy(p->kdone);
+    if (p->kstream) cudaStreamDestroy(p->kstream);
+    if (p->side) cudaStreamDestroy(p->side);
+    delete p;
+}
+
+static camelot_status set_failed(camelot_pipeline* p, const char* why) {
+    p->failed = true;
+    p->fail_msg = why;
+    return fail(CAMELOT_ESTATE, "pipeline failed: %s", why);
+}
+
+// Checks the device error word and the state of the last launch; relaunches
+// the persistent kernel if it has ended (idle exit) and `want_running`.
+static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
+    std::lock_guard<std::mutex> g(p->launch_mu);
+    if (p->failed) return fail(CAMELOT_ESTATE, "pipeline failed: %s", p->fail_msg.c_str());
+    const unsigned long long st = *(volatile unsigned long long*)p->hstatus;
+    if (st != 0ull) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device error %u at %u", (unsigned)(st & 0xffffffffu),
+                 (unsigned)(st >> 32));
+        return set_failed(p, buf);
+    }
+    if (p->relay_err.load()) return set_failed(p, "host-staged relay copy failed");
+    bool running = false;
+    if (p->launched) {
+        cudaError_t e = cudaEventQuery(p->kdone);
+        if (e == cudaErrorNotReady) running = true;
+        else if (e != cudaSuccess) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "persistent kernel failed: %s", cudaGetErrorString(e));
+            return set_failed(p, buf);
+        }
+    }
+    if (running || !want_running) return CAMELOT_OK;
+    // (re)launch: clear the per-launch exit counters and the group barriers
+    cudaError_t e = cudaMemsetAsync(&p->ctl->exited[0], 0, sizeof(p->ctl->exited), p->kstream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->groups, 0, sizeof(GroupSync) *
+                                              (size_t)p->hp.inst_begin[p->n_stages - 1] +
+                                              sizeof(GroupSync) * p->hp.inst[p->n_stages - 1],
+                                              p->kstream);
+    if (e == cudaSuccess) e = launch_pipeline_kernel(p->dp, p->grid, p->kstream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->kdone, p->kstream);
+    if (e != cudaSuccess) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "launch failed: %s", cudaGetErrorString(e));
+        return set_failed(p, buf);
+    }
+    p->launched = true;
+    p->launches++;
+    return CAMELOT_OK;
+}
+
+// Host-staged handoff (Sec. 4.2 / 6.1): every published batch is copied from
+// the producer's device slot to pinned host memory and from there into the
+// consumer's device slot; the copies run on one D2H and one H2D stream per
+// stage boundary, so consecutive batches overlap.
+static void relay_main(camelot_pipeline* p) {
+    cudaSetDevice(p->device);
+    std::vector<uint64_t> cur(p->n_stages, 0);
+    int idle = 0;
+    while (!p->relay_stop.load(std::memory_order_relaxed)) {
+        bool progress = false;
+        for (int s = 0; s + 1 < p->n_stages; ++s) {
+            HostRing& A = p->out_rings[s];
+            HostRing& Bq = p->in_rings[s + 1];
+            const uint64_t t = cur[s];
+            const unsigned a = (unsigned)(t % A.slots), b = (unsigned)(t % Bq.slots);
+            if (((volatile unsigned long long*)A.note_pub)[a] != t + 1) continue;
+            if (((volatile unsigned long long*)Bq.note_free)[b] != t) continue;
+            std::atomic_thread_fence(std::memory_order_acquire);
+            const unsigned n = ((volatile unsigned int*)A.note_n)[a];
+            const size_t bytes = (size_t)n * p->stages[s]->sp.out_row_bytes;
+            char* stg = p->r_stage[s] + (size_t)b * A.slot_bytes;
+            cudaError_t e = cudaMemcpyAsync(&p->r_hdr[s][b], &A.hdr[a], sizeof(BatchHdr),
+                                            cudaMemcpyDeviceToHost, p->r_d2h[s]);
+            if (!e) e = cudaMemcpyAsync(stg, A.data + (size_t)a * A.slot_bytes, bytes,
+                                        cudaMemcpyDeviceToHost, p->r_d2h[s]);
+            p->r_valA[s][a] = t + A.slots;
+            if (!e) e = cudaMemcpyAsync(&A.seq[a], &p->r_valA[s][a], 8, cudaMemcpyHostToDevice,
+                                        p->r_d2h[s]);
+            if (!e) e = cudaEventRecord(p->r_ev[s][b], p->r_d2h[s]);
+            if (!e) e = cudaStreamWaitEvent(p->r_h2d[s], p->r_ev[s][b], 0);
+            if (!e) e = cudaMemcpyAsync(&Bq.hdr[b], &p->r_hdr[s][b], sizeof(BatchHdr),
+                                        cudaMemcpyHostToDevice, p->r_h2d[s]);
+            if (!e) e = cudaMemcpyAsync(Bq.data + (size_t)b * Bq.slot_bytes, stg, bytes,
+                                        cudaMemcpyHostToDevice, p->r_h2d[s]);
+            p->r_valB[s][b] = t + 1;
+            if (!e) e = cudaMemcpyAsync(&Bq.seq[b], &p->r_valB[s][b], 8, cudaMemcpyHostToDevice,
+                                        p->r_h2d[s]);
+            if (e) { p->relay_err = 1; return; }
+            p->relayed_bytes += 2 * bytes;
+            cur[s] = t + 1;
+            progress = true;
+        }
+        if (progress) { idle = 0; continue; }
+        if (++idle < 2000) _mm_pause();
+        else std::this_thread::yield();
+    }
+}
+
+extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, int n_stages,
+                                                  const camelot_alloc* alloc, camelot_handoff mode,
+                                                  const camelot_options* opts,
+                                                  camelot_pipeline** out) {
+    if (!stages || !alloc || !out) return fail(CAMELOT_EINVAL, "null argument");
+    *out = nullptr;
+    if (n_stages < 1 || n_stages > kMaxStages)
+        return fail(CAMELOT_EINVAL, "n_stages %d outside 1..%d", n_stages, kMaxStages);
+    if (alloc->n_stages != n_stages) return fail(CAMELOT_EINVAL, "alloc.n_stages != n_stages");
+    if (mode != CAMELOT_HANDOFF_GLOBAL && mode != CAMELOT_HANDOFF_HOST_STAGED)
+        return fail(CAMELOT_EINVAL, "unknown handoff mode");
+    camelot_options o;
+    camelot_options_default(&o);
+    if (opts) o = *opts;
+    if (o.query_slots < 64 || (o.query_slots & (o.query_slots - 1)))
+        return fail(CAMELOT_EINVAL, "query_slots must be a power of two >= 64");
+    if (o.batch_slots < 2 || o.batch_slots > 4096) return fail(CAMELOT_EINVAL, "batch_slots outside 2..4096");
+    if (o.max_wait_ns < 0 || o.idle_exit_ns < 1000000 || o.wait_limit_ns < 1000000)
+        return fail(CAMELOT_EINVAL, "max_wait_ns >= 0, idle_exit_ns and wait_limit_ns >= 1 ms required");
+    const int B = alloc->batch;
+    if (B < 1 || B > 32) return fail(CAMELOT_EINVAL, "batch %d outside 1..32", B);
+    int total = 0;
+    for (int s = 0; s < n_stages; ++s) {
+        const camelot_stage* st = stages[s];
+        if (!st) return fail(CAMELOT_EINVAL, "stage %d is null", s);
+        if (alloc->instances[s] < 1 || alloc->sm_quota[s] < 1)
+            return fail(CAMELOT_EINVAL, "stage %d: instances and sm_quota must be >= 1", s);
+        if (st->sp.max_batch < B) return fail(CAMELOT_EINVAL, "stage %d: max_batch < batch", s);
+        const bool last = (s == n_stages - 1);
+        if (last != (st->sp.top_k > 0))
+            return fail(CAMELOT_EINVAL, "stage %d: only the last stage may (and must) have top_k > 0", s);
+        if (!last && st->sp.out_row_bytes != stages[s + 1]->sp.in_row_bytes)
+            return fail(CAMELOT_EINVAL, "stage %d output row (%zu B) != stage %d input row (%zu B)", s,
+                        st->sp.out_row_bytes, s + 1, stages[s + 1]->sp.in_row_bytes);
+        total += alloc->instances[s] * alloc->sm_quota[s];
+    }
+    camelot_status cs = ensure_configured();
+    if (cs != CAMELOT_OK) return cs;
+    int per_sm = 0;
+    CUDA_TRY(max_coresident_ctas(&per_sm));
+    const int sms = sm_count();
+    if (per_sm < 1 || total > per_sm * sms)
+        return fail(CAMELOT_EINVAL, "allocation needs %d SMs, the device offers %d", total, sms * per_sm);
+    if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32)
+        return fail(CAMELOT_EINVAL, "logits_sink needs a dense final stage");
+
+    auto* p = new camelot_pipeline();
+    auto bail = [&](camelot_status s) { pipeline_free(p); return s; };
+#define P_TRY(expr)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? CAMELOT_ENOMEM : CAMELOT_ECUDA, \
+                             "%s failed: %s", #expr, cudaGetErrorString(e_)));              \
+    } while (0)
+    cudaGetDevice(&p->device);
+    p->n_stages = n_stages;
+    for (int s = 0; s < n_stages; ++s) p->stages[s] = stages[s];
+    p->alloc = *alloc;
+    p->mode = mode;
+    p->opt = o;
+    p->grid = total;
+    P_TRY(cudaStreamCreateWithFlags(&p->kstream, cudaStreamNonBlocking));
+    P_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    P_TRY(cudaEventCreateWithFlags(&p->kdone, cudaEventDisableTiming));
+
+    PipeParams& hp = p->hp;
+    hp.n_stages = n_stages;
+    hp.B = B;
+    hp.handoff = mode;
+    hp.total_ctas = total;
+    int cta = 0, inst = 0;
+    size_t scr = 0;
+    for (int s = 0; s < n_stages; ++s) {
+        hp.cta_begin[s] = cta;
+        hp.inst[s] = alloc->instances[s];
+        hp.quota[s] = alloc->sm_quota[s];
+        hp.inst_begin[s] = inst;
+        hp.st[s] = stages[s]->sp;
+        StageParams tmp = stages[s]->sp;
+        const size_t per = tmp.kind == KIND_MLP_FP32 ? align_up(layout_scratch(tmp, B), 256) : 0;
+        hp.st[s] = tmp;   // scratch offsets laid out for batch B
+        hp.inst_scratch[s] = per;
+        hp.scratch_off[s] = scr;
+        scr += per * alloc->instances[s];
+        cta += alloc->instances[s] * alloc->sm_quota[s];
+        inst += alloc->instances[s];
+    }
+    hp.cta_begin[n_stages] = cta;
+    P_TRY(cudaMalloc(&p->ctl, sizeof(Ctl)));
+    P_TRY(cudaMemset(p->ctl, 0, sizeof(Ctl)));
+    P_TRY(cudaMalloc(&p->groups, sizeof(GroupSync) * inst));
+    P_TRY(cudaMemset(p->groups, 0, sizeof(GroupSync) * inst));
+    if (scr) P_TRY(cudaMalloc(&p->scratch, scr));
+    P_TRY(cudaHostAlloc((void**)&p->hflags, 2 * sizeof(HostFlags), cudaHostAllocMapped | cudaHostAllocPortable));
+    memset((void*)p->hflags, 0, 2 * sizeof(HostFlags));
+    p->hstatus = (unsigned long long*)&p->hflags[1].stop;
+    hp.ctl = p->ctl;
+    hp.host_stop = &p->hflags[0].stop;
+    hp.host_status = (volatile unsigned long long*)p->hstatus;
+    hp.groups = p->groups;
+    hp.scratch = p->scratch;
+    // batch rings
+    for (int s = 0; s + 1 < n_stages; ++s) {
+        const size_t slot_bytes = align_up((size_t)B * stages[s]->sp.out_row_bytes, 256);
+        const bool staged = (mode == CAMELOT_HANDOFF_HOST_STAGED);
+        cs = alloc_ring(p->out_rings[s], o.batch_slots, slot_bytes, staged);
+        if (cs != CAMELOT_OK) return bail(cs);
+        hp.out_ring[s] = ring_view(p->out_rings[s]);
+        if (staged) {
+            cs = alloc_ring(p->in_rings[s + 1], o.batch_slots, slot_bytes, true);
+            if (cs != CAMELOT_OK) return bail(cs);
+            // the producer side publishes notes, the consumer side frees them
+            hp.out_ring[s].note_free = nullptr;
+            hp.in_ring[s + 1] = ring_view(p->in_rings[s + 1]);
+            hp.in_ring[s + 1].note_pub = nullptr;
+            hp.in_ring[s + 1].note_n = nullptr;
+            P_TRY(cudaStreamCreateWithFlags(&p->r_d2h[s], cudaStreamNonBlocking));
+            P_TRY(cudaStreamCreateWithFlags(&p->r_h2d[s], cudaStreamNonBlocking));
+            p->r_ev[s].resize(o.batch_slots);
+            for (auto& e : p->r_ev[s]) P_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            P_TRY(cudaHostAlloc((void**)&p->r_stage[s], (size_t)o.batch_slots * slot_bytes, cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_hdr[s], o.batch_slots * sizeof(BatchHdr), cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_valA[s], o.batch_slots * 8, cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_valB[s], o.batch_slots * 8, cudaHostAllocPortable));
+        } else {
+            hp.out_ring[s].note_pub = nullptr;
+            hp.out_ring[s].note_n = nullptr;
+            hp.out_ring[s].note_free = nullptr;
+            hp.in_ring[s + 1] = hp.out_ring[s];
+        }
+    }
+    // query ring and completion ring (pinned, mapped)
+    const size_t R = o.query_slots;
+    const size_t q_row = stages[0]->sp.in_row_bytes;
+    P_TRY(cudaHostAlloc((void**)&p->qring, R * sizeof(QDesc), cudaHostAllocMapped | cudaHostAllocPortable));
+    P_TRY(cudaHostAlloc((void**)&p->qdata, R * q_row, cudaHostAllocMapped | cudaHostAllocPortable));
+    P_TRY(cudaHostAlloc((void**)&p->comp, R * sizeof(CompSlot), cudaHostAllocMapped | cudaHostAllocPortable));
+    memset((void*)p->qring, 0, R * sizeof(QDesc));
+    memset((void*)p->comp, 0, R * sizeof(CompSlot));
+    for (size_t i = 0; i < R; ++i) p->qring[i].seq = i;
+    hp.qring = p->qring;
+    hp.qdata = p->qdata;
+    hp.qmask = R - 1;
+    hp.q_row = q_row;
+    hp.comp = p->comp;
+    hp.cmask = R - 1;
+    hp.sink = o.logits_sink;
+    hp.sink_ld = stages[n_stages - 1]->sp.out_width;
+    P_TRY(cudaMalloc(&p->trace, sizeof(TraceDev)));
+    P_TRY(cudaMemset(p->trace, 0, sizeof(TraceDev)));
+    hp.trace = p->trace;
+    hp.max_wait_ns = o.max_wait_ns;
+    hp.idle_ns = o.idle_exit_ns;
+    hp.limit_ns = o.wait_limit_ns;
+    P_TRY(cudaMalloc(&p->dp, sizeof(PipeParams)));
+    P_TRY(cudaMemcpy(p->dp, &hp, sizeof(PipeParams), cudaMemcpyHostToDevice));
+    cs = check_and_run(p, true);
+    if (cs != CAMELOT_OK) return bail(cs);
+    if (mode == CAMELOT_HANDOFF_HOST_STAGED) p->relay = std::thread(relay_main, p);
+#undef P_TRY
+    *out = p;
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id, const void* queries,
+                                         uint32_t n, const int64_t* arrival_ns,
+                                         uint64_t* first_query_id) {
+    if (!p) return fail(CAMELOT_EINVAL, "null pipeline");
+    if (n == 0) { if (first_query_id) *first_query_id = p->next_ticket; return CAMELOT_OK; }
+    if (!queries) return fail(CAMELOT_EINVAL, "null queries");
+    if (p->failed) return fail(CAMELOT_ESTATE, "pipeline failed: %s", p->fail_msg.c_str());
+    const uint64_t polled = p->next_poll.load(std::memory_order_acquire);
+    if (p->trace_active) {
+        if (polled < p->trace_end) return fail(CAMELOT_ESTATE, "a trace is running");
+        p->trace_active = false;
+    }
+    const uint64_t R = p->opt.query_slots, mask = R - 1;
+    const uint64_t t0 = p->next_ticket.load(std::memory_order_relaxed);
+    if (t0 + n - polled > R) return fail(CAMELOT_EAGAIN, "completion ring full (poll first)");
+    for (uint32_t i = 0; i < n; ++i)
+        if (p->qring[(t0 + i) & mask].seq != t0 + i)
+            return fail(CAMELOT_EAGAIN, "query ring full");
+    const size_t row = p->hp.q_row;
+    const int64_t now = host_now_ns();
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t t = t0 + i;
+        memcpy(p->qdata + (t & mask) * row, (const char*)queries + (size_t)i * row, row);
+        QDesc& d = p->qring[t & mask];
+        d.t_arrival = arrival_ns ? arrival_ns[i] : now;
+        d.stream_id = stream_id;
+    }
+    std::atomic_thread_fence(std::memory_order_release);
+    for (uint32_t i = 0; i < n; ++i) p->qring[(t0 + i) & mask].seq = t0 + i + 1;
+    p->next_ticket.store(t0 + n, std::memory_order_release);
+    if (first_query_id) *first_query_id = t0;
+    return check_and_run(p, true);
+}
+
+extern "C" camelot_status camelot_submit_trace(camelot_pipeline* p, uint32_t stream_id,
+                                               const void* queries, uint32_t n,
+                                               const int64_t* arrival_off_ns,
+                                               uint64_t* first_query_id) {
+    if (!p) return fail(CAMELOT_EINVAL, "null pipeline");
+    if (!queries || !arrival_off_ns || n == 0) return fail(CAMELOT_EINVAL, "empty trace");
+    if (p->failed) return fail(CAMELOT_ESTATE, "pipeline failed: %s", p->fail_msg.c_str());
+    const uint64_t base = p->next_ticket.load();
+    if (p->next_poll.load() != base) return fail(CAMELOT_ESTATE, "queries are outstanding");
+    const uint64_t R = p->opt.query_slots;
+    if (n > R) return fail(CAMELOT_EINVAL, "trace longer than query_slots");
+    cudaSetDevice(p->device);
+    TraceDev td{};
+    td.data = (const char*)queries;
+    td.off = (const long long*)arrival_off_ns;
+    td.base = base;
+    td.n = n;
+    td.stream_id = stream_id;
+    td.armed = 0;
+    static const unsigned long long zero = 0;
+    static const unsigned int one = 1;
+    // disarm, reset the trace clock, write the fields, then arm
+    CUDA_TRY(cudaMemcpyAsync(&p->trace->armed, &td.armed, sizeof(unsigned), cudaMemcpyHostToDevice, p->side));
+    CUDA_TRY(cudaMemcpyAsync(&p->ctl->trace_t0.v, &zero, 8, cudaMemcpyHostToDevice, p->side));
+    CUDA_TRY(cudaMemcpyAsync(p->trace, &td, sizeof(TraceDev), cudaMemcpyHostToDevice, p->side));
+    CUDA_TRY(cudaMemcpyAsync(&p->trace->armed, &one, sizeof(unsigned), cudaMemcpyHostToDevice, p->side));
+    CUDA_TRY(cudaStreamSynchronize(p->side));
+    // tickets after the trace: each host ring slot now expects the first
+    // ticket >= base + n that maps to it
+    const uint64_t next = base + n, mask = R - 1;
+    for (uint64_t s = 0; s < R; ++s) {
+        uint64_t t = next + ((s - next) & mask);
+        p->qring[s].seq = t;
+    }
+    p->trace_active = true;
+    p->trace_end = next;
+    p->next_ticket.store(next, std::memory_order_release);
+    if (first_query_id) *first_query_id = base;
+    return check_and_run(p, true);
+}
+
+extern "C" camelot_status camelot_poll(camelot_pipeline* p, camelot_completion* out, uint32_t max,
+                                       uint32_t* n_out, int64_t timeout_us) {
+    if (!p || !n_out || (max && !out)) return fail(CAMELOT_EINVAL, "null argument");
+    *n_out = 0;
+    const uint64_t mask = p->opt.query_slots - 1;
+    const int64_t t_start = host_now_ns();
+    uint32_t got = 0;
+    int spins = 0;
+    for (;;) {
+        uint64_t t = p->next_poll.load(std::memory_order_relaxed);
+        while (got < max) {
+            CompSlot& cs = p->comp[t & mask];
+            if (cs.seq != t + 1) break;
+            std::atomic_thread_fence(std::memory_order_acquire);
+            out[got] = cs.c;
+            out[got].t_poll_ns = host_now_ns();
+            ++got;
+            ++t;
+        }
+        if (got) {
+            p->next_poll.store(t, std::memory_order_release);
+            *n_out = got;
+            return CAMELOT_OK;
+        }
+        if ((spins & 1023) == 0) {
+            const bool outstanding = t < p->next_ticket.load(std::memory_order_acquire);
+            camelot_status cs = check_and_run(p, outstanding);
+            if (cs != CAMELOT_OK) return cs;
+        }
+        if (max == 0 || timeout_us == 0) return CAMELOT_OK;
+        if (timeout_us > 0 && host_now_ns() - t_start > timeout_us * 1000)
+            return fail(CAMELOT_ETIMEDOUT, "no completion within %lld us", (long long)timeout_us);
+        if (++spins < 4000) _mm_pause();
+        else std::this_thread::yield();
+    }
+}
+
+extern "C" camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out) {
+    if (!p || !out) return fail(CAMELOT_EINVAL, "null argument");
+    memset(out, 0, sizeof *out);
+    out->submitted = p->next_ticket.load();
+    out->completed = p->next_poll.load();
+    Line64 b[kMaxStages];
+    CUDA_TRY(cudaMemcpyAsync(b, &p->ctl->batches[0], sizeof b, cudaMemcpyDeviceToHost, p->side));
+    CUDA_TRY(cudaStreamSynchronize(p->side));
+    for (int s = 0; s < kMaxStages; ++s) out->batches[s] = b[s].v;
+    out->kernel_launches = p->launches;
+    out->relayed_bytes = p->relayed_bytes.load();
+    size_t slot = 0, ring = 0;
+    for (int s = 0; s < kMaxStages; ++s) {
+        for (HostRing* r : {&p->out_rings[s], &p->in_rings[s]}) {
+            if (!r->data) continue;
+            slot = std::max(slot, r->slot_bytes);
+            ring += (size_t)r->slots * r->slot_bytes;
+        }
+    }
+    out->device_bytes_per_batch_slot = slot;
+    out->device_ring_bytes = ring;
+    const unsigned long long st = *(volatile unsigned long long*)p->hstatus;
+    out->device_status = (int32_t)(st & 0xffffffffu);
+    out->device_where = (int32_t)(st >> 32);
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_pipeline_destroy(camelot_pipeline* p) {
+    if (!p) return fail(CAMELOT_EINVAL, "null pipeline");
+    cudaSetDevice(p->device);
+    p->hflags[0].stop = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    if (p->relay.joinable()) {
+        p->relay_stop = true;
+        p->relay.join();
+    }
+    cudaError_t e = cudaStreamSynchronize(p->kstream);
+    for (int s = 0; s < kMaxStages; ++s) {
+        if (p->r_d2h[s]) cudaStreamSynchronize(p->r_d2h[s]);
+        if (p->r_h2d[s]) cudaStreamSynchronize(p->r_h2d[s]);
+    }
+    pipeline_free(p);
+    if (e != cudaSuccess) return fail(CAMELOT_ECUDA, "persistent kernel ended with: %s", cudaGetErrorString(e));
+    return CAMELOT_OK;
+}

@@ -1,0 +1,68 @@
+// Plain-data description of a prepared stage, shared by the host runtime and
+// the device code (passed by value in kernel parameters).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace camelot {
+
+constexpr int kMaxLayers = 4;
+constexpr int kMaxStages = 8;
+constexpr int kMaxTopK = 5;
+constexpr int kThreads = 512;          // threads per CTA (one CTA per SM)
+constexpr int kWarps = kThreads / 32;
+constexpr int kQGroup = 16;            // queries per register tile of the FP32 layers
+constexpr int kNBlock = 128;           // neurons per warp task (4 per lane)
+constexpr int kMaxKC = 128;            // largest K-chunk of a warp task
+constexpr size_t kSmemBytes = 160 * 1024;  // dynamic shared memory per CTA: > half an SM,
+                                           // so exactly one CTA fits on an SM
+
+enum StageKind : int32_t { KIND_NORMALIZE_U8 = 1, KIND_NORM_POOL2_BF16 = 2, KIND_MLP_FP32 = 3,
+                           KIND_GEMM_BF16 = 4 };
+enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
+
+// One dense layer in kernel layout.
+//  - "task" layers (N > 32 or not the last layer of a final stage): weights
+//    packed as quads of k, [K/4][Npad][4] f32, Npad = N rounded up to 128, rows
+//    >= N zero; computed as (query-group, 128-neuron block, K-chunk) warp tasks
+//    whose partial sums are reduced over chunks in chunk order.
+//  - "head" layer (last layer of a final stage with N <= 32): weights row-major
+//    [N][K]; one warp computes a whole query.
+struct LayerParams {
+    const float* w;     // device, kernel layout (see above)
+    int32_t K, N, Npad;
+    int32_t KC, C;      // K-chunk (multiple of 4) and number of chunks
+    int32_t act;
+    int32_t head;       // 1 = head layer
+    size_t p_off;       // scratch offset of this layer's partial sums (task layers)
+    size_t h_off;       // scratch offset of its output rows (hidden layers / logits)
+};
+
+struct StageParams {
+    int32_t kind;
+    int32_t n_layers;
+    int32_t top_k;          // 0 = intermediate stage
+    int32_t max_batch;
+    int32_t H, W, C;        // image kinds
+    int32_t pad_;
+    size_t in_row_bytes;
+    size_t out_row_bytes;   // 0 for final stages
+    size_t out_width;       // final stages: width of the last layer (logits per query)
+    size_t scratch_bytes;   // per instance (for max_batch)
+    size_t res_off;         // scratch offset of final results: idx [B][5] int32, val [B][5] f32
+    LayerParams layer[kMaxLayers];
+};
+
+// Row addressing: row q is at base + ((first + q) & mask) * stride.  Ring
+// slots wrap with mask = slots - 1; contiguous buffers use mask = ~0.
+struct RowRef {
+    char* base;
+    uint64_t first;
+    uint64_t mask;
+    size_t stride;
+    __host__ __device__ char* row(uint64_t q) const {
+        return base + ((first + q) & mask) * stride;
+    }
+};
+
+}  // namespace camelot

@@ -1,0 +1,355 @@
+// Stage bodies of the synthetic microservices (stand-ins for the Sec. 3 suite).
+//
+// A body runs on the p CTAs of one stage instance (the SM quota p_i of Table 2)
+// over one batch of n rows.  CTAs split the work by their rank in the instance
+// and meet at group barriers between dependent phases.  The decomposition of
+// every floating-point reduction is fixed by the stage (chunk sizes chosen when
+// the stage is prepared), never by p, so the result of a query is bit-identical
+// whatever the SM quota, the number of instances or the batch it travels in.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "device_sync.cuh"
+#include "stage_params.h"
+
+namespace camelot {
+
+struct StageCtx {
+    int rank;          // CTA rank inside the instance
+    int nctas;         // CTAs (SMs) of the instance
+    GroupSync* gs;
+    Ctl* ctl;
+    uint64_t limit_ns;
+    uint32_t where;    // stage index, for error reports
+    char* scratch;     // the instance's scratch memory
+    float* smem;       // dynamic shared memory of this CTA
+};
+
+struct FinalOut {
+    int32_t* idx;      // [n][top_k]
+    float* val;        // [n][top_k]
+    RowRef logits;     // final layer output rows (base == nullptr: not wanted)
+};
+
+__device__ __forceinline__ float apply_act(float v, int act) {
+    if (act == ACT_RELU) return v > 0.f ? v : 0.f;
+    if (act == ACT_GELU) return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// NORMALIZE_U8: y = (x - 127.5) / 64, u8 -> f32, row layout unchanged.  Exact in
+// FP32 (x - 127.5 is a half-integer below 256, and 1/64 is a power of two).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float norm_u8(uint32_t b) {
+    return (static_cast<float>(b) - 127.5f) * 0.015625f;
+}
+
+__device__ void normalize_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                               RowRef out) {
+    const uint64_t chunks = P.in_row_bytes / 16;     // 16 input bytes -> 64 output bytes
+    const uint64_t total = (uint64_t)n * chunks;
+    const uint64_t stride = (uint64_t)cx.nctas * kThreads;
+    constexpr int U = 4;                               // loads in flight per thread
+    for (uint64_t base = (uint64_t)cx.rank * kThreads + threadIdx.x; base < total;
+         base += stride * U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t e = base + u * stride;
+            if (e < total) {
+                const uint64_t q = e / chunks, c = e - q * chunks;
+                v[u] = __ldcg(reinterpret_cast<const uint4*>(in.row(q)) + c);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t e = base + u * stride;
+            if (e < total) {
+                const uint64_t q = e / chunks, c = e - q * chunks;
+                float4* o = reinterpret_cast<float4*>(out.row(q)) + 4 * c;
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    __stcg(o + j, make_float4(norm_u8(w[j] & 0xff), norm_u8((w[j] >> 8) & 0xff),
+                                              norm_u8((w[j] >> 16) & 0xff), norm_u8(w[j] >> 24)));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// NORM_POOL2_BF16: 2x2 mean, normalise, round to bf16.  One warp per (query,
+// output row): the two input rows (2 * W * C contiguous bytes) are staged in
+// the warp's shared memory with 16-byte loads, then each lane produces output
+// values m = lane, lane + 32, ... of the row.  The FP32 value is exact (an
+// integer sum <= 1020, times 1/4, minus 127.5, times 1/64), so the bf16 result
+// is the round-to-nearest-even of the exact value.
+// ---------------------------------------------------------------------------
+__device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                              RowRef out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int H = P.H, W = P.W, C = P.C, Ho = H / 2, Wo = W / 2;
+    const int pair_bytes = 2 * W * C;
+    const int out_vals = Wo * C;
+    uint8_t* sm = reinterpret_cast<uint8_t*>(cx.smem) + warp * 8192;
+    const int units = n * Ho;
+    for (int u = cx.rank * kWarps + warp; u < units; u += cx.nctas * kWarps) {
+        const int q = u / Ho, ho = u - q * Ho;
+        const uint4* src = reinterpret_cast<const uint4*>(in.row(q) + (size_t)2 * ho * W * C);
+        uint4* dst = reinterpret_cast<uint4*>(sm);
+        for (int i = lane; i < pair_bytes / 16; i += 32) dst[i] = __ldcg(src + i);
+        __syncwarp();
+        const uint8_t* r0 = sm;
+        const uint8_t* r1 = sm + W * C;
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out.row(q)) + (size_t)ho * out_vals;
+        for (int m = lane; m < out_vals; m += 32) {
+            const int w = m / C, c = m - w * C;
+            const int i0 = 2 * w * C + c;
+            const uint32_t s = (uint32_t)r0[i0] + r0[i0 + C] + r1[i0] + r1[i0 + C];
+            const float y = (static_cast<float>(s) * 0.25f - 127.5f) * 0.015625f;
+            o[m] = __float2bfloat16_rn(y);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 dense layers (MLP_FP32).
+// Task layer: y[q][j] = act(sum_k W[j][k] x[q][k]).  The K axis is cut into
+// fixed chunks of KC; warp task (query group of 16, 128-neuron block, chunk c)
+// accumulates, for each of its 16 x 128 outputs, the chunk's products in
+// ascending k with FMA, and stores the chunk partial P[c][q][j].  The reduce
+// phase sums P over c in ascending order.  Each lane owns neurons lane,
+// lane+32, lane+64, lane+96 of the block: the packed weights [K/4][Npad][4]
+// give one coalesced 512-byte load per neuron slot and k-quad, and the query
+// activations are broadcast from the warp's shared-memory copy of the chunk.
+// ---------------------------------------------------------------------------
+__device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
+                            float* Pbuf) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kQGroup * kMaxKC / 4);
+    const int QG = (n + kQGroup - 1) / kQGroup, NBLK = L.Npad / kNBlock;
+    const int ntask = QG * NBLK * L.C;
+    const float4* wp = reinterpret_cast<const float4*>(L.w);
+    for (int t = cx.rank * kWarps + warp; t < ntask; t += cx.nctas * kWarps) {
+        const int c = t % L.C;
+        const int r = t / L.C;
+        const int nb = r % NBLK, qg = r / NBLK;
+        const int k0 = c * L.KC;
+        const int kq_n = min(L.KC, L.K - k0) >> 2;
+        for (int e = lane; e < kQGroup * kq_n; e += 32) {
+            const int q = e / kq_n, kq = e - q * kq_n;
+            const int gq = qg * kQGroup + q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gq < n) v = __ldcg(reinterpret_cast<const float4*>(x.row(gq)) + (k0 >> 2) + kq);
+            xs[q * (kMaxKC / 4) + kq] = v;
+        }
+        __syncwarp();
+        float acc[kQGroup][4];
+#pragma unroll
+        for (int q = 0; q < kQGroup; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
+        const float4* wq = wp + (size_t)(k0 >> 2) * L.Npad + nb * kNBlock + lane;
+        float4 w0 = __ldg(wq), w1 = __ldg(wq + 32), w2 = __ldg(wq + 64), w3 = __ldg(wq + 96);
+        for (int kq = 0; kq < kq_n; ++kq) {
+            float4 n0 = w0, n1 = w1, n2 = w2, n3 = w3;
+            if (kq + 1 < kq_n) {
+                const float4* wn = wq + (size_t)(kq + 1) * L.Npad;
+                n0 = __ldg(wn); n1 = __ldg(wn + 32); n2 = __ldg(wn + 64); n3 = __ldg(wn + 96);
+            }
+#pragma unroll
+            for (int q = 0; q < kQGroup; ++q) {
+                const float4 xv = xs[q * (kMaxKC / 4) + kq];
+                acc[q][0] = fmaf(xv.x, w0.x, acc[q][0]); acc[q][0] = fmaf(xv.y, w0.y, acc[q][0]);
+                acc[q][0] = fmaf(xv.z, w0.z, acc[q][0]); acc[q][0] = fmaf(xv.w, w0.w, acc[q][0]);
+                acc[q][1] = fmaf(xv.x, w1.x, acc[q][1]); acc[q][1] = fmaf(xv.y, w1.y, acc[q][1]);
+                acc[q][1] = fmaf(xv.z, w1.z, acc[q][1]); acc[q][1] = fmaf(xv.w, w1.w, acc[q][1]);
+                acc[q][2] = fmaf(xv.x, w2.x, acc[q][2]); acc[q][2] = fmaf(xv.y, w2.y, acc[q][2]);
+                acc[q][2] = fmaf(xv.z, w2.z, acc[q][2]); acc[q][2] = fmaf(xv.w, w2.w, acc[q][2]);
+                acc[q][3] = fmaf(xv.x, w3.x, acc[q][3]); acc[q][3] = fmaf(xv.y, w3.y, acc[q][3]);
+                acc[q][3] = fmaf(xv.z, w3.z, acc[q][3]); acc[q][3] = fmaf(xv.w, w3.w, acc[q][3]);
+            }
+            w0 = n0; w1 = n1; w2 = n2; w3 = n3;
+        }
+#pragma unroll
+        for (int q = 0; q < kQGroup; ++q) {
+            const int gq = qg * kQGroup + q;
+            if (gq < n) {
+                float* prow = Pbuf + ((size_t)c * n + gq) * L.Npad + nb * kNBlock + lane;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) __stcg(prow + 32 * i, acc[q][i]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ void dense_reduce(const StageCtx& cx, const LayerParams& L, int n, const float* Pbuf,
+                             RowRef out) {
+    const int total = n * L.N;
+    const size_t cstride = (size_t)n * L.Npad;
+    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
+        const int q = e / L.N, j = e - q * L.N;
+        const float* p = Pbuf + (size_t)q * L.Npad + j;
+        float s = 0.f;
+        int c = 0;
+        for (; c + 4 <= L.C; c += 4) {
+            const float a0 = __ldcg(p + (size_t)c * cstride), a1 = __ldcg(p + (size_t)(c + 1) * cstride);
+            const float a2 = __ldcg(p + (size_t)(c + 2) * cstride), a3 = __ldcg(p + (size_t)(c + 3) * cstride);
+            s += a0; s += a1; s += a2; s += a3;
+        }
+        for (; c < L.C; ++c) s += __ldcg(p + (size_t)c * cstride);
+        __stcg(reinterpret_cast<float*>(out.row(q)) + j, apply_act(s, L.act));
+    }
+}
+
+// Warp-wide best of (value, index) under "larger value, then smaller index".
+__device__ __forceinline__ void warp_best(float& v, int& i) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, off);
+        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+}
+
+// Head layer (last layer of a final stage, N <= 32): one warp per query.  Lane
+// l accumulates k-quads l, l+32, ... in ascending order for all N outputs;
+// the 32 lane partials of each output are then summed by an xor butterfly,
+// which builds the same addition tree in every lane.  Lane j keeps output j;
+// the top-k follows by repeated warp-wide best.
+__device__ void dense_head(const StageCtx& cx, const LayerParams& L, RowRef x, int n, int top_k,
+                           const FinalOut& fo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KQ = L.K >> 2;
+    for (int q = cx.rank * kWarps + warp; q < n; q += cx.nctas * kWarps) {
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        const float4* xr = reinterpret_cast<const float4*>(x.row(q));
+        for (int kq = lane; kq < KQ; kq += 32) {
+            const float4 xv = __ldcg(xr + kq);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < L.N) {
+                    const float4 wv = __ldg(reinterpret_cast<const float4*>(L.w + (size_t)j * L.K) + kq);
+                    acc[j] = fmaf(xv.x, wv.x, acc[j]);
+                    acc[j] = fmaf(xv.y, wv.y, acc[j]);
+                    acc[j] = fmaf(xv.z, wv.z, acc[j]);
+                    acc[j] = fmaf(xv.w, wv.w, acc[j]);
+                }
+            }
+        }
+        float mine = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < L.N) {
+                float v = acc[j];
+#pragma unroll
+                for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == j) mine = v;
+            }
+        }
+        mine = apply_act(mine, L.act);
+        if (fo.logits.base != nullptr && lane < L.N)
+            reinterpret_cast<float*>(fo.logits.row(q))[lane] = mine;
+        float cand = lane < L.N ? mine : -INFINITY;
+        for (int r = 0; r < top_k; ++r) {
+            float bv = cand;
+            int bi = lane < L.N ? lane : 0x7fffffff;
+            warp_best(bv, bi);
+            if (lane == 0) {
+                fo.idx[(size_t)q * top_k + r] = bi;
+                fo.val[(size_t)q * top_k + r] = bv;
+            }
+            if (lane == bi) cand = -INFINITY;
+        }
+    }
+}
+
+// Top-k of rows z (f32, width N) by one warp per query: every lane keeps its
+// own k best (value desc, index asc) over j = lane, lane+32, ...; k rounds of
+// warp-wide best then pop the winners.
+__device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int k, const FinalOut& fo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = cx.rank * kWarps + warp; q < n; q += cx.nctas * kWarps) {
+        float bv[kMaxTopK];
+        int bi[kMaxTopK];
+#pragma unroll
+        for (int r = 0; r < kMaxTopK; ++r) { bv[r] = -INFINITY; bi[r] = 0x7fffffff; }
+        const float* zr = reinterpret_cast<const float*>(z.row(q));
+        for (int j = lane; j < N; j += 32) {
+            const float v = __ldcg(zr + j);
+            if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
+            // insert (v, j): j grows along the scan, so ties keep the earlier index first
+            if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
+                float cv = v;
+                int ci = j;
+#pragma unroll
+                for (int r = 0; r < kMaxTopK; ++r) {
+                    if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
+                        const float tv = bv[r];
+                        const int ti = bi[r];
+                        bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+                    }
+                }
+            }
+        }
+        for (int r = 0; r < k; ++r) {
+            float v = bv[0];
+            int i = bi[0];
+            warp_best(v, i);
+            if (lane == 0) {
+                fo.idx[(size_t)q * k + r] = i;
+                fo.val[(size_t)q * k + r] = v;
+            }
+            if (bi[0] == i) {   // the winning lane pops its head
+#pragma unroll
+                for (int s = 0; s + 1 < kMaxTopK; ++s) { bv[s] = bv[s + 1]; bi[s] = bi[s + 1]; }
+                bv[kMaxTopK - 1] = -INFINITY;
+                bi[kMaxTopK - 1] = 0x7fffffff;
+            }
+        }
+    }
+}
+
+// The whole FP32 MLP stage.  Returns false if a group barrier failed.
+__device__ bool mlp_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
+                         const FinalOut& fo) {
+    RowRef x = in;
+    for (int l = 0; l < P.n_layers; ++l) {
+        const LayerParams& L = P.layer[l];
+        const bool last = (l == P.n_layers - 1);
+        if (L.head) {
+            dense_head(cx, L, x, n, P.top_k, fo);
+            return true;
+        }
+        float* Pbuf = reinterpret_cast<float*>(cx.scratch + L.p_off);
+        dense_tasks(cx, L, x, n, Pbuf);
+        if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+        RowRef dst = (last && P.top_k == 0)
+                         ? out
+                         : RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * sizeof(float)};
+        dense_reduce(cx, L, n, Pbuf, dst);
+        if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+        x = dst;
+        if (last && P.top_k > 0) topk_rows(cx, x, n, L.N, P.top_k, fo);
+    }
+    return true;
+}
+
+// Dispatch on the stage kind.
+__device__ bool stage_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
+                           const FinalOut& fo) {
+    switch (P.kind) {
+        case KIND_NORMALIZE_U8: normalize_body(cx, P, in, n, out); return true;
+        case KIND_NORM_POOL2_BF16: normpool_body(cx, P, in, n, out); return true;
+        case KIND_MLP_FP32: return mlp_body(cx, P, in, n, out, fo);
+        default: return false;
+    }
+}
+
+}  // namespace camelot
