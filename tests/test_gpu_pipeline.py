@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import argmax_margin_ok, cfg1_data, chain_bound
+from gpu_common import argmax_margin_ok, cfg1_data, chain_bound, first_argmax
 
 pytestmark = pytest.mark.gpu
 
@@ -61,9 +61,12 @@ def _check_against_oracle(orc, comps, logits, n=N_Q):
     z64, bound = chain_bound(orc, x[:n], ws, [1, 1, 0])
     assert np.all(np.abs(logits - z64) <= bound + 1e-30)
     idx = np.array([c.idx[0] for c in comps])
-    ok = argmax_margin_ok(z64, bound)
-    assert ok.mean() > 0.97
+    assert np.array_equal(idx, first_argmax(logits))          # integer result: exact
+    assert np.array_equal(np.array([c.val[0] for c in comps], np.float32),
+                          logits[np.arange(n), idx])
+    ok = argmax_margin_ok(z64, np.abs(logits - z64))
     assert np.array_equal(idx[ok], np.argmax(z64, axis=1)[ok])
+    assert np.mean(idx == np.argmax(z64, axis=1)) >= 0.99
     assert all(c.idx[1] == -1 for c in comps)
     for c in comps:
         assert c.t_batch_ns <= c.t_done_ns and 1 <= c.batch_size <= 16
