@@ -164,6 +164,10 @@ typedef struct {
                                pipeline in the error state (default 2 s)               */
     float* logits_sink;     /* optional device f32 [query_slots][final width]: the final
                                layer's output of query q lands in row q % query_slots  */
+    int32_t exit_after_trace; /* 1: the persistent kernel ends as soon as a trace has been
+                               fully taken and drained (one launch per trace, which makes
+                               the launch's CUDA-event time the trace's device time)  */
+    int32_t pad_;
 } camelot_options;
 
 /* Fill `o` with the defaults above. */
@@ -176,7 +180,9 @@ typedef struct camelot_pipeline camelot_pipeline;
  * `alloc` (sum_i N_i * p_i must not exceed the SM count; each stage's
  * max_batch >= alloc->batch), the given handoff mode and options (NULL =
  * defaults).  Allocates the rings (device memory; the query and completion
- * rings in pinned, mapped host memory) and launches the persistent kernel.
+ * rings in pinned, mapped host memory).  The persistent kernel is launched by
+ * the first submit (and relaunched by any later submit or poll that finds it
+ * ended).
  * The stages must outlive the pipeline.  Errors: EINVAL, ENOMEM, ECUDA. */
 camelot_status camelot_pipeline_create(camelot_stage* const* stages, int n_stages,
                                        const camelot_alloc* alloc, camelot_handoff mode,
@@ -234,6 +240,8 @@ typedef struct {
     uint64_t device_bytes_per_batch_slot;   /* device bytes of one inter-stage slot       */
     uint64_t device_ring_bytes;             /* device bytes held by all inter-stage rings */
     int32_t device_status, device_where;    /* first device error (0 = none)              */
+    double last_launch_ms;                  /* CUDA-event duration of the last finished launch */
+    double total_launch_ms;                 /* sum over finished launches                  */
 } camelot_stats;
 
 camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);

@@ -44,7 +44,7 @@ class Alloc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("query_slots", C.c_uint32), ("batch_slots", C.c_uint32), ("max_wait_ns", C.c_int64),
                 ("idle_exit_ns", C.c_int64), ("wait_limit_ns", C.c_int64),
-                ("logits_sink", C.c_void_p)]
+                ("logits_sink", C.c_void_p), ("exit_after_trace", C.c_int32), ("pad_", C.c_int32)]
 
 
 class Completion(C.Structure):
@@ -59,7 +59,8 @@ class Stats(C.Structure):
                 ("batches", C.c_uint64 * MAX_STAGES), ("kernel_launches", C.c_uint64),
                 ("relayed_bytes", C.c_uint64), ("device_bytes_per_batch_slot", C.c_uint64),
                 ("device_ring_bytes", C.c_uint64), ("device_status", C.c_int32),
-                ("device_where", C.c_int32)]
+                ("device_where", C.c_int32), ("last_launch_ms", C.c_double),
+                ("total_launch_ms", C.c_double)]
 
 
 class Profile(C.Structure):

@@ -61,6 +61,7 @@ __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
             __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&tr->base, 0);
         const unsigned long long tn =
             __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&tr->n, 0);
+        if (P.exit_after_trace && armed && h >= tb + tn) return CMD_EXIT;   // trace taken
         bool trace = armed && h >= tb && h < tb + tn;
         int avail;
         bool ready = false;

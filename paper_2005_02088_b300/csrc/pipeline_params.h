@@ -97,6 +97,7 @@ struct PipeParams {
     size_t sink_ld;             // floats per sink row
     TraceDev* trace;
     long long max_wait_ns, idle_ns, limit_ns;
+    int exit_after_trace;
 };
 
 }  // namespace camelot

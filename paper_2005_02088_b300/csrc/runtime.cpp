@@ -292,6 +292,8 @@ extern "C" void camelot_options_default(camelot_options* o) {
     o->idle_exit_ns = 500000000;
     o->wait_limit_ns = 2000000000;
     o->logits_sink = nullptr;
+    o->exit_after_trace = 0;
+    o->pad_ = 0;
 }
 
 struct HostRing {   // one batch ring's allocations
@@ -328,8 +330,10 @@ struct camelot_pipeline {
     CompSlot* comp = nullptr;          // pinned
     TraceDev* trace = nullptr;         // device
     cudaStream_t kstream = nullptr, side = nullptr;
-    cudaEvent_t kdone = nullptr;
+    cudaEvent_t kdone = nullptr, kstart = nullptr;
     bool launched = false;
+    bool timed = false;          // the last launch's duration has been added
+    double last_launch_ms = 0.0, total_launch_ms = 0.0;
     std::mutex launch_mu;
     std::atomic<uint64_t> next_ticket{0};
     std::atomic<uint64_t> next_poll{0};
@@ -429,6 +433,7 @@ static void pipeline_free(camelot_pipeline* p) {
     if (p->qdata) cudaFreeHost(p->qdata);
     if (p->comp) cudaFreeHost(p->comp);
     if (p->kdone) cudaEventDestroy(p->kdone);
+    if (p->kstart) cudaEventDestroy(p->kstart);
     if (p->kstream) cudaStreamDestroy(p->kstream);
     if (p->side) cudaStreamDestroy(p->side);
     delete p;
@@ -463,6 +468,14 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
             return set_failed(p, buf);
         }
     }
+    if (p->launched && !running && !p->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->kstart, p->kdone) == cudaSuccess) {
+            p->last_launch_ms = ms;
+            p->total_launch_ms += ms;
+        }
+        p->timed = true;
+    }
     if (running || !want_running) return CAMELOT_OK;
     // (re)launch: clear the per-launch exit counters and the group barriers
     cudaError_t e = cudaMemsetAsync(&p->ctl->exited[0], 0, sizeof(p->ctl->exited), p->kstream);
@@ -470,6 +483,7 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
                                               (size_t)p->hp.inst_begin[p->n_stages - 1] +
                                               sizeof(GroupSync) * p->hp.inst[p->n_stages - 1],
                                               p->kstream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->kstart, p->kstream);
     if (e == cudaSuccess) e = launch_pipeline_kernel(p->dp, p->grid, p->kstream);
     if (e == cudaSuccess) e = cudaEventRecord(p->kdone, p->kstream);
     if (e != cudaSuccess) {
@@ -478,6 +492,7 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
         return set_failed(p, buf);
     }
     p->launched = true;
+    p->timed = false;
     p->launches++;
     return CAMELOT_OK;
 }
@@ -594,7 +609,8 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     p->grid = total;
     P_TRY(cudaStreamCreateWithFlags(&p->kstream, cudaStreamNonBlocking));
     P_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
-    P_TRY(cudaEventCreateWithFlags(&p->kdone, cudaEventDisableTiming));
+    P_TRY(cudaEventCreate(&p->kdone));
+    P_TRY(cudaEventCreate(&p->kstart));
 
     PipeParams& hp = p->hp;
     hp.n_stages = n_stages;
@@ -685,10 +701,9 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     hp.max_wait_ns = o.max_wait_ns;
     hp.idle_ns = o.idle_exit_ns;
     hp.limit_ns = o.wait_limit_ns;
+    hp.exit_after_trace = o.exit_after_trace ? 1 : 0;
     P_TRY(cudaMalloc(&p->dp, sizeof(PipeParams)));
     P_TRY(cudaMemcpy(p->dp, &hp, sizeof(PipeParams), cudaMemcpyHostToDevice));
-    cs = check_and_run(p, true);
-    if (cs != CAMELOT_OK) return bail(cs);
     if (mode == CAMELOT_HANDOFF_HOST_STAGED) p->relay = std::thread(relay_main, p);
 #undef P_TRY
     *out = p;
@@ -831,6 +846,9 @@ extern "C" camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_st
     const unsigned long long st = *(volatile unsigned long long*)p->hstatus;
     out->device_status = (int32_t)(st & 0xffffffffu);
     out->device_where = (int32_t)(st >> 32);
+    check_and_run(p, false);   // folds in the duration of a launch that has ended
+    out->last_launch_ms = p->last_launch_ms;
+    out->total_launch_ms = p->total_launch_ms;
     return CAMELOT_OK;
 }
 
