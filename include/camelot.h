@@ -137,6 +137,29 @@ camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const v
                                     float* out_logits, void* scratch, size_t scratch_bytes,
                                     void* stream);
 
+/* Allocation-free form of camelot_stage_launch (the paper has no counterpart;
+ * it serves callers of this library that cannot allocate device memory at the
+ * point where they run a stage: an application whose memory manager owns the
+ * whole device pool, a serving loop that cannot afford the latency or the
+ * device-wide synchronisation of cudaMalloc/cudaFree mid-request, or a
+ * plug-in that is only handed its input and output buffers).  Same arguments
+ * and results as camelot_stage_launch, minus the scratch: the stage's scratch
+ * lives in a static 16 MiB device array that every GPU loading the library
+ * holds until the process exits.  Nothing is allocated by this call.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address and sets the kernel's shared-memory limit; make
+ *     that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the call clears the part that must start at zero.  Calls whose
+ *     kernels overlap on the GPU (other streams, other host threads) race on
+ *     the array and give wrong results: order them on one stream.
+ *   - Errors: EINVAL when the batch needs more than the 16 MiB (for the plain
+ *     2-stage MLP stage: batches above 62 queries), plus those of
+ *     camelot_stage_launch. */
+camelot_status camelot_stage_launch_noalloc(const camelot_stage* st, int n_ctas, const void* in,
+                                            uint32_t n, void* out, int32_t* out_idx,
+                                            float* out_val, float* out_logits, void* stream);
+
 /* ----------------------------------------------------------- pipelines */
 typedef enum {
     CAMELOT_HANDOFF_GLOBAL = 0,      /* pointer + flag in device memory, no copy (Sec. 6.2) */

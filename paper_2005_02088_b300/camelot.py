@@ -85,6 +85,7 @@ _SIGS = {
     "camelot_stage_release": (C.c_int, [P]),
     "camelot_stage_info": (C.c_int, [P, P, P, C.c_uint32, P]),
     "camelot_stage_launch": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P]),
+    "camelot_stage_launch_noalloc": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P]),
     "camelot_options_default": (None, [P]),
     "camelot_pipeline_create": (C.c_int, [P, C.c_int, P, C.c_int, P, P]),
     "camelot_submit": (C.c_int, [P, C.c_uint32, P, C.c_uint32, P, P]),
@@ -169,6 +170,13 @@ def camelot_stage_launch(st: int, n_ctas: int, inp, n: int, out=None, out_idx=No
     _check(load().camelot_stage_launch(st, n_ctas, _ptr(inp), n, _ptr(out), _ptr(out_idx),
                                        _ptr(out_val), _ptr(out_logits), _ptr(scratch),
                                        scratch_bytes, _ptr(stream)))
+
+
+def camelot_stage_launch_noalloc(st: int, n_ctas: int, inp, n: int, out=None, out_idx=None,
+                                 out_val=None, out_logits=None, stream=None) -> None:
+    """Stage launch whose scratch is the library's static device buffer."""
+    _check(load().camelot_stage_launch_noalloc(st, n_ctas, _ptr(inp), n, _ptr(out), _ptr(out_idx),
+                                               _ptr(out_val), _ptr(out_logits), _ptr(stream)))
 
 
 def camelot_options_default() -> Options:

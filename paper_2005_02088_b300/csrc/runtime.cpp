@@ -64,6 +64,13 @@ static int64_t host_now_ns() {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
 static camelot_status ensure_configured() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
@@ -233,6 +240,14 @@ extern "C" camelot_status camelot_stage_release(camelot_stage* st) {
 
 static const size_t kDirectHeader = align_up(sizeof(Ctl), 256) + align_up(sizeof(GroupSync), 256);
 
+// Internal helpers shared with noalloc.cu (not part of the C ABI).
+const StageParams* camelot_internal_stage_params(const camelot_stage* st) { return &st->sp; }
+size_t camelot_internal_layout_scratch(StageParams& sp, int B) {
+    return sp.kind == KIND_MLP_FP32 ? layout_scratch(sp, B) : 0;
+}
+int camelot_internal_sm_count() { return sm_count(); }
+camelot_status camelot_internal_fail(camelot_status st, const char* msg) { return fail(st, "%s", msg); }
+
 extern "C" camelot_status camelot_stage_info(const camelot_stage* st, size_t* in_row,
                                              size_t* out_row, uint32_t n, size_t* scratch) {
     if (!st) return fail(CAMELOT_EINVAL, "null stage");
@@ -243,12 +258,6 @@ extern "C" camelot_status camelot_stage_info(const camelot_stage* st, size_t* in
     return CAMELOT_OK;
 }
 
-static int sm_count() {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n;
-}
 
 extern "C" camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const void* in,
                                                uint32_t n, void* out, int32_t* out_idx,

@@ -46,7 +46,7 @@ __device__ __forceinline__ float norm_u8(uint32_t b) {
     return (static_cast<float>(b) - 127.5f) * 0.015625f;
 }
 
-__device__ void normalize_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                RowRef out) {
     const uint64_t chunks = P.in_row_bytes / 16;     // 16 input bytes -> 64 output bytes
     const uint64_t total = (uint64_t)n * chunks;
@@ -87,7 +87,7 @@ __device__ void normalize_body(const StageCtx& cx, const StageParams& P, RowRef 
 // integer sum <= 1020, times 1/4, minus 127.5, times 1/64), so the bf16 result
 // is the round-to-nearest-even of the exact value.
 // ---------------------------------------------------------------------------
-__device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                               RowRef out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int H = P.H, W = P.W, C = P.C, Ho = H / 2, Wo = W / 2;
@@ -126,7 +126,7 @@ __device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef i
 // give one coalesced 512-byte load per neuron slot and k-quad, and the query
 // activations are broadcast from the warp's shared-memory copy of the chunk.
 // ---------------------------------------------------------------------------
-__device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
+static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
                             float* Pbuf) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kQGroup * kMaxKC / 4);
@@ -187,7 +187,7 @@ __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, 
     }
 }
 
-__device__ void dense_reduce(const StageCtx& cx, const LayerParams& L, int n, const float* Pbuf,
+static __device__ void dense_reduce(const StageCtx& cx, const LayerParams& L, int n, const float* Pbuf,
                              RowRef out) {
     const int total = n * L.N;
     const size_t cstride = (size_t)n * L.Npad;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void warp_best(float& v, int& i) {
 // the 32 lane partials of each output are then summed by an xor butterfly,
 // which builds the same addition tree in every lane.  Lane j keeps output j;
 // the top-k follows by repeated warp-wide best.
-__device__ void dense_head(const StageCtx& cx, const LayerParams& L, RowRef x, int n, int top_k,
+static __device__ void dense_head(const StageCtx& cx, const LayerParams& L, RowRef x, int n, int top_k,
                            const FinalOut& fo) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KQ = L.K >> 2;
@@ -273,7 +273,7 @@ __device__ void dense_head(const StageCtx& cx, const LayerParams& L, RowRef x, i
 // Top-k of rows z (f32, width N) by one warp per query: every lane keeps its
 // own k best (value desc, index asc) over j = lane, lane+32, ...; k rounds of
 // warp-wide best then pop the winners.
-__device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int k, const FinalOut& fo) {
+static __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int k, const FinalOut& fo) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = cx.rank * kWarps + warp; q < n; q += cx.nctas * kWarps) {
         float bv[kMaxTopK];
@@ -317,7 +317,7 @@ __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int k, con
 }
 
 // The whole FP32 MLP stage.  Returns false if a group barrier failed.
-__device__ bool mlp_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
+static __device__ bool mlp_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
                          const FinalOut& fo) {
     RowRef x = in;
     for (int l = 0; l < P.n_layers; ++l) {
@@ -342,7 +342,7 @@ __device__ bool mlp_body(const StageCtx& cx, const StageParams& P, RowRef in, in
 }
 
 // Dispatch on the stage kind.
-__device__ bool stage_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
+static __device__ bool stage_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
                            const FinalOut& fo) {
     switch (P.kind) {
         case KIND_NORMALIZE_U8: normalize_body(cx, P, in, n, out); return true;
