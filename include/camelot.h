@@ -153,8 +153,9 @@ camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const v
  *     behind; the call clears the part that must start at zero.  Calls whose
  *     kernels overlap on the GPU (other streams, other host threads) race on
  *     the array and give wrong results: order them on one stream.
- *   - Errors: EINVAL when the batch needs more than the 16 MiB (for the plain
- *     2-stage MLP stage: batches above 62 queries), plus those of
+ *   - Errors: EINVAL when the batch needs more than the 16 MiB (the FP32 stage
+ *     of the plain 2-stage pipeline needs about 37 KB per query and fits at
+ *     every batch it accepts; very wide layers may not), plus those of
  *     camelot_stage_launch. */
 camelot_status camelot_stage_launch_noalloc(const camelot_stage* st, int n_ctas, const void* in,
                                             uint32_t n, void* out, int32_t* out_idx,
@@ -178,7 +179,8 @@ typedef struct {
 typedef struct {
     uint32_t query_slots;   /* capacity of the query ring and of the completion ring
                                (power of two, default 65536)                          */
-    uint32_t batch_slots;   /* capacity of each inter-stage batch ring (default 8)       */
+    uint32_t batch_slots;   /* least capacity of each inter-stage batch ring (default 8;
+                               raised to 2 x the instances on both sides)              */
     int64_t max_wait_ns;    /* batch trigger: a partial batch leaves once its oldest query
                                has waited this long (default 200000)                   */
     int64_t idle_exit_ns;   /* the persistent kernel ends after this long without work;

@@ -97,7 +97,7 @@ static void stage_free(camelot_stage* st) {
     delete st;
 }
 
-// K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, 128].
+// K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, kMaxKC].
 static int choose_kc(int K) {
     int kc = (K + 127) / 128;
     kc = (kc + 3) / 4 * 4;
@@ -110,7 +110,8 @@ static size_t layout_scratch(StageParams& sp, int B) {
     size_t p_bytes = 0, h_bytes = 0;
     for (int l = 0; l < sp.n_layers; ++l) {
         LayerParams& L = sp.layer[l];
-        if (!L.head) p_bytes = std::max(p_bytes, (size_t)L.C * B * L.Npad * sizeof(float));
+        const size_t G = (L.C + kWarps - 1) / kWarps;    // chunk groups
+        if (!L.head) p_bytes = std::max(p_bytes, G * B * L.Npad * sizeof(float));
         h_bytes = std::max(h_bytes, (size_t)B * L.N * sizeof(float));
     }
     size_t off = 0;
@@ -334,6 +335,7 @@ struct camelot_pipeline {
     GroupSync* groups = nullptr;
     char* scratch = nullptr;
     HostRing out_rings[kMaxStages], in_rings[kMaxStages];
+    unsigned ring_slots[kMaxStages] = {};
     QDesc* qring = nullptr;            // pinned
     char* qdata = nullptr;             // pinned
     CompSlot* comp = nullptr;          // pinned
@@ -661,11 +663,16 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     for (int s = 0; s + 1 < n_stages; ++s) {
         const size_t slot_bytes = align_up((size_t)B * stages[s]->sp.out_row_bytes, 256);
         const bool staged = (mode == CAMELOT_HANDOFF_HOST_STAGED);
-        cs = alloc_ring(p->out_rings[s], o.batch_slots, slot_bytes, staged);
+        // every producer and consumer instance of the boundary can hold a slot,
+        // with as many again in flight
+        const unsigned need = 2u * (unsigned)(alloc->instances[s] + alloc->instances[s + 1]);
+        const unsigned slots = std::max(o.batch_slots, need);
+        p->ring_slots[s] = slots;
+        cs = alloc_ring(p->out_rings[s], slots, slot_bytes, staged);
         if (cs != CAMELOT_OK) return bail(cs);
         hp.out_ring[s] = ring_view(p->out_rings[s]);
         if (staged) {
-            cs = alloc_ring(p->in_rings[s + 1], o.batch_slots, slot_bytes, true);
+            cs = alloc_ring(p->in_rings[s + 1], slots, slot_bytes, true);
             if (cs != CAMELOT_OK) return bail(cs);
             // the producer side publishes notes, the consumer side frees them
             hp.out_ring[s].note_free = nullptr;
@@ -674,12 +681,12 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
             hp.in_ring[s + 1].note_n = nullptr;
             P_TRY(cudaStreamCreateWithFlags(&p->r_d2h[s], cudaStreamNonBlocking));
             P_TRY(cudaStreamCreateWithFlags(&p->r_h2d[s], cudaStreamNonBlocking));
-            p->r_ev[s].resize(o.batch_slots);
+            p->r_ev[s].resize(slots);
             for (auto& e : p->r_ev[s]) P_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            P_TRY(cudaHostAlloc((void**)&p->r_stage[s], (size_t)o.batch_slots * slot_bytes, cudaHostAllocPortable));
-            P_TRY(cudaHostAlloc((void**)&p->r_hdr[s], o.batch_slots * sizeof(BatchHdr), cudaHostAllocPortable));
-            P_TRY(cudaHostAlloc((void**)&p->r_valA[s], o.batch_slots * 8, cudaHostAllocPortable));
-            P_TRY(cudaHostAlloc((void**)&p->r_valB[s], o.batch_slots * 8, cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_stage[s], (size_t)slots * slot_bytes, cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_hdr[s], slots * sizeof(BatchHdr), cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_valA[s], slots * 8, cudaHostAllocPortable));
+            P_TRY(cudaHostAlloc((void**)&p->r_valB[s], slots * 8, cudaHostAllocPortable));
         } else {
             hp.out_ring[s].note_pub = nullptr;
             hp.out_ring[s].note_n = nullptr;

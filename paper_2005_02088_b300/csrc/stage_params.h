@@ -9,12 +9,13 @@ namespace camelot {
 constexpr int kMaxLayers = 4;
 constexpr int kMaxStages = 8;
 constexpr int kMaxTopK = 5;
-constexpr int kThreads = 512;          // threads per CTA (one CTA per SM)
+constexpr int kThreads = 256;          // threads per CTA (one CTA per SM)
 constexpr int kWarps = kThreads / 32;
 constexpr int kQGroup = 16;            // queries per register tile of the FP32 layers
 constexpr int kNBlock = 128;           // neurons per warp task (4 per lane)
 constexpr int kMaxKC = 128;            // largest K-chunk of a warp task
-constexpr size_t kSmemBytes = 160 * 1024;  // dynamic shared memory per CTA: > half an SM,
+constexpr int kWRing = 8;              // weight quads in flight per warp (cp.async ring)
+constexpr size_t kSmemBytes = 200 * 1024;  // dynamic shared memory per CTA: > half an SM,
                                            // so exactly one CTA fits on an SM
 
 enum StageKind : int32_t { KIND_NORMALIZE_U8 = 1, KIND_NORM_POOL2_BF16 = 2, KIND_MLP_FP32 = 3,

@@ -32,6 +32,22 @@ struct FinalOut {
     RowRef logits;     // final layer output rows (base == nullptr: not wanted)
 };
 
+// 16-byte global -> shared copy that bypasses L1 and completes asynchronously;
+// one commit group per weight quad, waited for per lane.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// Same, reading `src_bytes` (0 or 16) bytes and zero-filling the rest.
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, unsigned src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ float apply_act(float v, int act) {
     if (act == ACT_RELU) return v > 0.f ? v : 0.f;
     if (act == ACT_GELU) return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
@@ -93,7 +109,7 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
     const int H = P.H, W = P.W, C = P.C, Ho = H / 2, Wo = W / 2;
     const int pair_bytes = 2 * W * C;
     const int out_vals = Wo * C;
-    uint8_t* sm = reinterpret_cast<uint8_t*>(cx.smem) + warp * 8192;
+    uint8_t* sm = reinterpret_cast<uint8_t*>(cx.smem) + warp * 8192;   // 8 warps x 8 KB
     const int units = n * Ho;
     for (int u = cx.rank * kWarps + warp; u < units; u += cx.nctas * kWarps) {
         const int q = u / Ho, ho = u - q * Ho;
@@ -118,90 +134,133 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
 // ---------------------------------------------------------------------------
 // FP32 dense layers (MLP_FP32).
 // Task layer: y[q][j] = act(sum_k W[j][k] x[q][k]).  The K axis is cut into
-// fixed chunks of KC; warp task (query group of 16, 128-neuron block, chunk c)
-// accumulates, for each of its 16 x 128 outputs, the chunk's products in
-// ascending k with FMA, and stores the chunk partial P[c][q][j].  The reduce
-// phase sums P over c in ascending order.  Each lane owns neurons lane,
+// fixed chunks of KC, and chunks into fixed groups of 8 (one per warp).  CTA
+// task (query group of 16, 128-neuron block, chunk group g): warp w accumulates
+// chunk 8g+w for the 16 x 128 outputs, each in ascending k with FMA; the 8 chunk
+// partials are added in chunk order in shared memory and stored as the group
+// partial P[g][q][j]; the reduce phase adds the groups in ascending order.  Each lane owns neurons lane,
 // lane+32, lane+64, lane+96 of the block: the packed weights [K/4][Npad][4]
-// give one coalesced 512-byte load per neuron slot and k-quad, and the query
-// activations are broadcast from the warp's shared-memory copy of the chunk.
+// give one coalesced 512-byte load per neuron slot and k-quad.  Weights
+// stream into a per-warp shared-memory ring kWRing quads ahead with cp.async;
+// the query activations are broadcast from the warp's copy of the chunk.
 // ---------------------------------------------------------------------------
 static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
                             float* Pbuf) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kQGroup * kMaxKC / 4);
+    // per-warp shared memory: the query chunk [16][KC] and a ring of kWRing
+    // weight quads (each lane's 4 x 16 bytes, written and read by that lane)
+    constexpr int kXs = kQGroup * kMaxKC / 4;          // float4 per warp
+    constexpr int kWs = kWRing * kNBlock;              // float4 per warp
+    float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kXs + kWs);
+    float4* wr = xs + kXs;
     const int QG = (n + kQGroup - 1) / kQGroup, NBLK = L.Npad / kNBlock;
-    const int ntask = QG * NBLK * L.C;
+    const int G = (L.C + kWarps - 1) / kWarps;         // chunk groups
+    const int ntask = QG * NBLK * G;
     const float4* wp = reinterpret_cast<const float4*>(L.w);
-    for (int t = cx.rank * kWarps + warp; t < ntask; t += cx.nctas * kWarps) {
-        const int c = t % L.C;
-        const int r = t / L.C;
+    const size_t ws = (size_t)L.Npad;
+    for (int t = cx.rank; t < ntask; t += cx.nctas) {
+        const int g = t % G;
+        const int r = t / G;
         const int nb = r % NBLK, qg = r / NBLK;
-        const int k0 = c * L.KC;
-        const int kq_n = min(L.KC, L.K - k0) >> 2;
-        for (int e = lane; e < kQGroup * kq_n; e += 32) {
-            const int q = e / kq_n, kq = e - q * kq_n;
-            const int gq = qg * kQGroup + q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gq < n) v = __ldcg(reinterpret_cast<const float4*>(x.row(gq)) + (k0 >> 2) + kq);
-            xs[q * (kMaxKC / 4) + kq] = v;
-        }
-        __syncwarp();
+        const int c = g * kWarps + warp;               // this warp's chunk
         float acc[kQGroup][4];
 #pragma unroll
         for (int q = 0; q < kQGroup; ++q)
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
-        const float4* wq = wp + (size_t)(k0 >> 2) * L.Npad + nb * kNBlock + lane;
-        float4 w0 = __ldg(wq), w1 = __ldg(wq + 32), w2 = __ldg(wq + 64), w3 = __ldg(wq + 96);
-        for (int kq = 0; kq < kq_n; ++kq) {
-            float4 n0 = w0, n1 = w1, n2 = w2, n3 = w3;
-            if (kq + 1 < kq_n) {
-                const float4* wn = wq + (size_t)(kq + 1) * L.Npad;
-                n0 = __ldg(wn); n1 = __ldg(wn + 32); n2 = __ldg(wn + 64); n3 = __ldg(wn + 96);
+        if (c < L.C) {
+            const int k0 = c * L.KC;
+            const int kq_n = min(L.KC, L.K - k0) >> 2;
+            const float4* wq = wp + (size_t)(k0 >> 2) * ws + nb * kNBlock + lane;
+            // group 0: the query chunk (zero rows past the batch) and weight quad 0
+            for (int e = lane; e < kQGroup * kq_n; e += 32) {
+                const int q = e / kq_n, kq = e - q * kq_n;
+                const int gq = qg * kQGroup + q;
+                const float4* src = reinterpret_cast<const float4*>(x.row(gq < n ? gq : 0)) +
+                                    (k0 >> 2) + kq;
+                cp_async16_zfill(xs + q * (kMaxKC / 4) + kq, src, gq < n ? 16u : 0u);
             }
 #pragma unroll
-            for (int q = 0; q < kQGroup; ++q) {
-                const float4 xv = xs[q * (kMaxKC / 4) + kq];
-                acc[q][0] = fmaf(xv.x, w0.x, acc[q][0]); acc[q][0] = fmaf(xv.y, w0.y, acc[q][0]);
-                acc[q][0] = fmaf(xv.z, w0.z, acc[q][0]); acc[q][0] = fmaf(xv.w, w0.w, acc[q][0]);
-                acc[q][1] = fmaf(xv.x, w1.x, acc[q][1]); acc[q][1] = fmaf(xv.y, w1.y, acc[q][1]);
-                acc[q][1] = fmaf(xv.z, w1.z, acc[q][1]); acc[q][1] = fmaf(xv.w, w1.w, acc[q][1]);
-                acc[q][2] = fmaf(xv.x, w2.x, acc[q][2]); acc[q][2] = fmaf(xv.y, w2.y, acc[q][2]);
-                acc[q][2] = fmaf(xv.z, w2.z, acc[q][2]); acc[q][2] = fmaf(xv.w, w2.w, acc[q][2]);
-                acc[q][3] = fmaf(xv.x, w3.x, acc[q][3]); acc[q][3] = fmaf(xv.y, w3.y, acc[q][3]);
-                acc[q][3] = fmaf(xv.z, w3.z, acc[q][3]); acc[q][3] = fmaf(xv.w, w3.w, acc[q][3]);
+            for (int d = 0; d < kWRing - 1; ++d) {
+                if (d < kq_n) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        cp_async16(wr + d * kNBlock + 32 * i + lane, wq + (size_t)d * ws + 32 * i);
+                }
+                cp_async_commit();
             }
-            w0 = n0; w1 = n1; w2 = n2; w3 = n3;
+            for (int kq = 0; kq < kq_n; ++kq) {
+                const int nxt = kq + kWRing - 1;
+                if (nxt < kq_n) {
+                    float4* dst = wr + (nxt % kWRing) * kNBlock + lane;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        cp_async16(dst + 32 * i, wq + (size_t)nxt * ws + 32 * i);
+                }
+                cp_async_commit();
+                cp_async_wait<kWRing - 1>();      // this lane's copies up to quad kq have landed
+                if (kq == 0) __syncwarp();        // ... and every lane's part of the query chunk
+                const float4* wv = wr + (kq % kWRing) * kNBlock + lane;
+                const float4 a0 = wv[0], a1 = wv[32], a2 = wv[64], a3 = wv[96];
+#pragma unroll
+                for (int q = 0; q < kQGroup; ++q) {
+                    const float4 xv = xs[q * (kMaxKC / 4) + kq];
+                    acc[q][0] = fmaf(xv.x, a0.x, acc[q][0]); acc[q][0] = fmaf(xv.y, a0.y, acc[q][0]);
+                    acc[q][0] = fmaf(xv.z, a0.z, acc[q][0]); acc[q][0] = fmaf(xv.w, a0.w, acc[q][0]);
+                    acc[q][1] = fmaf(xv.x, a1.x, acc[q][1]); acc[q][1] = fmaf(xv.y, a1.y, acc[q][1]);
+                    acc[q][1] = fmaf(xv.z, a1.z, acc[q][1]); acc[q][1] = fmaf(xv.w, a1.w, acc[q][1]);
+                    acc[q][2] = fmaf(xv.x, a2.x, acc[q][2]); acc[q][2] = fmaf(xv.y, a2.y, acc[q][2]);
+                    acc[q][2] = fmaf(xv.z, a2.z, acc[q][2]); acc[q][2] = fmaf(xv.w, a2.w, acc[q][2]);
+                    acc[q][3] = fmaf(xv.x, a3.x, acc[q][3]); acc[q][3] = fmaf(xv.y, a3.y, acc[q][3]);
+                    acc[q][3] = fmaf(xv.z, a3.z, acc[q][3]); acc[q][3] = fmaf(xv.w, a3.w, acc[q][3]);
+                }
+            }
+            cp_async_wait<0>();
         }
-#pragma unroll
-        for (int q = 0; q < kQGroup; ++q) {
-            const int gq = qg * kQGroup + q;
-            if (gq < n) {
-                float* prow = Pbuf + ((size_t)c * n + gq) * L.Npad + nb * kNBlock + lane;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) __stcg(prow + 32 * i, acc[q][i]);
-            }
-        }
+        // the warp's chunk partial [16][128] goes to its (now free) query and
+        // weight areas
+        static_assert(kQGroup * kNBlock <= 4 * (kXs + kWs), "partial does not fit");
         __syncwarp();
+        float* part = reinterpret_cast<float*>(xs);
+#pragma unroll
+        for (int q = 0; q < kQGroup; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) part[q * kNBlock + 32 * i + lane] = acc[q][i];
+        __syncthreads();
+        // group partial = chunk partials added in warp (= chunk) order
+        for (int o = threadIdx.x; o < kQGroup * kNBlock; o += kThreads) {
+            const int q = o / kNBlock, j = o - q * kNBlock;
+            const int gq = qg * kQGroup + q;
+            float sum = 0.f;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w)
+                sum += reinterpret_cast<const float*>(cx.smem)[w * (kXs + kWs) * 4 + q * kNBlock + j];
+            if (gq < n) __stcg(Pbuf + ((size_t)g * n + gq) * L.Npad + nb * kNBlock + j, sum);
+        }
+        __syncthreads();
     }
 }
 
+// Reduction over the G chunk groups, in ascending group order; each thread
+// owns outputs and issues its group loads eight at a time.
 static __device__ void dense_reduce(const StageCtx& cx, const LayerParams& L, int n, const float* Pbuf,
                              RowRef out) {
     const int total = n * L.N;
-    const size_t cstride = (size_t)n * L.Npad;
+    const int G = (L.C + kWarps - 1) / kWarps;
+    const size_t gstride = (size_t)n * L.Npad;
     for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
         const int q = e / L.N, j = e - q * L.N;
         const float* p = Pbuf + (size_t)q * L.Npad + j;
         float s = 0.f;
-        int c = 0;
-        for (; c + 4 <= L.C; c += 4) {
-            const float a0 = __ldcg(p + (size_t)c * cstride), a1 = __ldcg(p + (size_t)(c + 1) * cstride);
-            const float a2 = __ldcg(p + (size_t)(c + 2) * cstride), a3 = __ldcg(p + (size_t)(c + 3) * cstride);
-            s += a0; s += a1; s += a2; s += a3;
+        int g = 0;
+        for (; g + 8 <= G; g += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (size_t)(g + u) * gstride);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
         }
-        for (; c < L.C; ++c) s += __ldcg(p + (size_t)c * cstride);
+        for (; g < G; ++g) s += __ldcg(p + (size_t)g * gstride);
         __stcg(reinterpret_cast<float*>(out.row(q)) + j, apply_act(s, L.act));
     }
 }

@@ -55,10 +55,24 @@ def test_noalloc_matches_caller_scratch_twice(orc):
                 assert np.array_equal(a, b)
             z64, bound = chain_bound(orc, xs, ws, [1, 1, 0])
             assert np.all(np.abs(got[2] - z64) <= bound + 1e-30)
-        # a batch whose scratch exceeds the static buffer is refused, not run
-        y = torch.zeros((64, 12288), dtype=torch.float32, device="cuda")
+    finally:
+        cm.camelot_stage_release(st)
+
+
+def test_noalloc_refuses_batches_beyond_the_static_buffer():
+    # a 256 -> 65536 layer needs about 0.5 MiB of scratch per query: 64 queries
+    # exceed the 16 MiB buffer and are refused before anything runs
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    w = torch.zeros((65536, 256), dtype=torch.float32, device="cuda")
+    st = pl.stage_dense(cm.STAGE_MLP_FP32, [w], [0], top_k=0, max_batch=64)
+    try:
+        y = torch.zeros((64, 256), dtype=torch.float32, device="cuda")
+        out = torch.zeros((64, 65536), dtype=torch.float32, device="cuda")
         with pytest.raises(cm.CamelotError) as e:
-            _run_noalloc(cm, st, y, 64, 8)
+            cm.camelot_stage_launch_noalloc(st, 8, y, 64, out, None, None, None, None)
         assert e.value.status == cm.EINVAL
+        cm.camelot_stage_launch_noalloc(st, 8, y, 4, out, None, None, None, None)   # small: runs
+        torch.cuda.synchronize()
+        assert float(out[:4].abs().sum()) == 0.0
     finally:
         cm.camelot_stage_release(st)
