@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "pipeline_params.h"
-#include "stages.cuh"
+#include "stage_dispatch.cuh"
 
 namespace camelot {
 
@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     __shared__ unsigned long long sh_in, sh_first, sh_out;
     __shared__ long long sh_tb;
     LeaderState ls{~0ull, 0, gtime()};
+    const bool tensor_stage = (SP.kind == KIND_GEMM_BF16);
+    if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
 
     for (;;) {
         // ---- the leader finds work and posts it in the instance's mailbox
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
         }
     }
     __syncthreads();
+    if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));
     if (leader && threadIdx.x == 0) {
         __threadfence();
         atomicAdd(&P.ctl->exited[s].v, 1ull);
@@ -328,7 +331,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     StageCtx cx{(int)blockIdx.x, (int)gridDim.x, gs, ctl, (uint64_t)limit_ns, 0u, scratch,
                 reinterpret_cast<float*>(smem4)};
     FinalOut fo{idx, val, logits};
+    const bool tensor_stage = (sp->kind == KIND_GEMM_BF16);
+    if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
     stage_body(cx, *sp, in, n, out, fo);
+    if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));
 }
 
 }  // namespace camelot

@@ -1,5 +1,7 @@
 // Host runtime of libcamelot: stage preparation, pipeline rings and lifecycle,
 // submission, completion polling, trace replay and the host-staged relay.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <time.h>
 #include <immintrin.h>
@@ -97,6 +99,43 @@ static void stage_free(camelot_stage* st) {
     delete st;
 }
 
+// cuTensorMapEncodeTiled, looked up through the runtime (no link-time driver
+// dependency, so the library loads on machines without a GPU).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// TMA map of a row-major bf16 matrix [rows][K]: boxes of 128 rows x 64 K
+// (128 bytes, the swizzle width) with the 128-byte swizzle.
+static bool make_weight_map(CUtensorMap* m, const void* base, int rows, int K) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// K-chunk of a tensor-core layer: 1024 for long K, else 256 (multiples of 64).
+static int choose_kc_gemm(int K) { return std::min(K, K >= 8192 ? 1024 : 256); }
+
 // K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, kMaxKC].
 static int choose_kc(int K) {
     int kc = (K + 127) / 128;
@@ -110,6 +149,11 @@ static size_t layout_scratch(StageParams& sp, int B) {
     size_t p_bytes = 0, h_bytes = 0;
     for (int l = 0; l < sp.n_layers; ++l) {
         LayerParams& L = sp.layer[l];
+        if (sp.kind == KIND_GEMM_BF16) {
+            if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * B * L.Npad * sizeof(float));
+            h_bytes = std::max(h_bytes, (size_t)B * L.Npad * sizeof(float));
+            continue;
+        }
         const size_t G = (L.C + kWarps - 1) / kWarps;    // chunk groups
         if (!L.head) p_bytes = std::max(p_bytes, G * B * L.Npad * sizeof(float));
         h_bytes = std::max(h_bytes, (size_t)B * L.N * sizeof(float));
@@ -219,8 +263,47 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             sp.scratch_bytes = layout_scratch(sp, d->max_batch);
             break;
         }
-        case CAMELOT_STAGE_GEMM_BF16:
-            return bail(fail(CAMELOT_EINVAL, "GEMM_BF16 stages are not available in this build"));
+        case CAMELOT_STAGE_GEMM_BF16: {
+            const int L = d->n_layers;
+            if (L < 1 || L > kMaxLayers) return bail(fail(CAMELOT_EINVAL, "n_layers %d outside 1..4", L));
+            if (d->max_batch > 32) return bail(fail(CAMELOT_EINVAL, "GEMM_BF16 stages take batches of at most 32"));
+            for (int l = 0; l <= L; ++l)
+                if (d->dims[l] <= 0) return bail(fail(CAMELOT_EINVAL, "dims[%d] must be > 0", l));
+            for (int l = 0; l < L; ++l) {
+                if (d->dims[l] % 64) return bail(fail(CAMELOT_EINVAL, "layer input width dims[%d]=%d must be a multiple of 64", l, d->dims[l]));
+                if (!d->weights[l]) return bail(fail(CAMELOT_EINVAL, "weights[%d] is null", l));
+                if (d->act[l] < 0 || d->act[l] > 2) return bail(fail(CAMELOT_EINVAL, "act[%d] invalid", l));
+            }
+            if (d->top_k > d->dims[L]) return bail(fail(CAMELOT_EINVAL, "top_k exceeds the final width"));
+            if (!d->top_k && d->dims[L] % 8)
+                return bail(fail(CAMELOT_EINVAL, "an intermediate stage's output width must be a multiple of 8"));
+            sp.n_layers = L;
+            sp.in_row_bytes = (size_t)d->dims[0] * 2;
+            sp.out_row_bytes = d->top_k ? 0 : (size_t)d->dims[L] * 2;
+            sp.out_width = d->dims[L];
+            for (int l = 0; l < L; ++l) {
+                LayerParams& Lp = sp.layer[l];
+                const int K = d->dims[l], N = d->dims[l + 1];
+                Lp.K = K; Lp.N = N; Lp.act = d->act[l]; Lp.head = 0;
+                Lp.Npad = (N + 127) / 128 * 128;
+                Lp.KC = choose_kc_gemm(K);
+                Lp.C = (K + Lp.KC - 1) / Lp.KC;
+                std::vector<__nv_bfloat16> w((size_t)Lp.Npad * K, __float2bfloat16_rn(0.f));
+                if (cudaMemcpy(w.data(), d->weights[l], (size_t)N * K * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return bail(fail(CAMELOT_EINVAL, "weights[%d] is not readable device memory", l));
+                void* dp = nullptr;
+                if (cudaMalloc(&dp, w.size() * 2) != cudaSuccess)
+                    return bail(fail(CAMELOT_ENOMEM, "weight copy allocation failed"));
+                st->allocs.push_back(dp);
+                if (cudaMemcpy(dp, w.data(), w.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+                    return bail(fail(CAMELOT_ECUDA, "weight upload failed"));
+                Lp.w = (const float*)dp;
+                if (!make_weight_map(&Lp.tmap, dp, Lp.Npad, K))
+                    return bail(fail(CAMELOT_ECUDA, "TMA map of weights[%d] could not be encoded", l));
+            }
+            sp.scratch_bytes = layout_scratch(sp, d->max_batch);
+            break;
+        }
         default:
             return bail(fail(CAMELOT_EINVAL, "unknown stage kind %d", d->kind));
     }
@@ -244,7 +327,7 @@ static const size_t kDirectHeader = align_up(sizeof(Ctl), 256) + align_up(sizeof
 // Internal helpers shared with noalloc.cu (not part of the C ABI).
 const StageParams* camelot_internal_stage_params(const camelot_stage* st) { return &st->sp; }
 size_t camelot_internal_layout_scratch(StageParams& sp, int B) {
-    return sp.kind == KIND_MLP_FP32 ? layout_scratch(sp, B) : 0;
+    return (sp.kind == KIND_MLP_FP32 || sp.kind == KIND_GEMM_BF16) ? layout_scratch(sp, B) : 0;
 }
 int camelot_internal_sm_count() { return sm_count(); }
 camelot_status camelot_internal_fail(camelot_status st, const char* msg) { return fail(st, "%s", msg); }
@@ -599,7 +682,8 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     const int sms = sm_count();
     if (per_sm < 1 || total > per_sm * sms)
         return fail(CAMELOT_EINVAL, "allocation needs %d SMs, the device offers %d", total, sms * per_sm);
-    if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32)
+    if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32 &&
+        stages[n_stages - 1]->sp.kind != KIND_GEMM_BF16)
         return fail(CAMELOT_EINVAL, "logits_sink needs a dense final stage");
 
     auto* p = new camelot_pipeline();
@@ -637,7 +721,8 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         hp.inst_begin[s] = inst;
         hp.st[s] = stages[s]->sp;
         StageParams tmp = stages[s]->sp;
-        const size_t per = tmp.kind == KIND_MLP_FP32 ? align_up(layout_scratch(tmp, B), 256) : 0;
+        const bool dense = tmp.kind == KIND_MLP_FP32 || tmp.kind == KIND_GEMM_BF16;
+        const size_t per = dense ? align_up(layout_scratch(tmp, B), 256) : 0;
         hp.st[s] = tmp;   // scratch offsets laid out for batch B
         hp.inst_scratch[s] = per;
         hp.scratch_off[s] = scr;

@@ -1,6 +1,8 @@
 // Plain-data description of a prepared stage, shared by the host runtime and
 // the device code (passed by value in kernel parameters).
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; the library does not link the driver)
+
 #include <cstddef>
 #include <cstdint>
 
@@ -29,7 +31,12 @@ enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
 //    whose partial sums are reduced over chunks in chunk order.
 //  - "head" layer (last layer of a final stage with N <= 32): weights row-major
 //    [N][K]; one warp computes a whole query.
+//  - tensor-core layers (GEMM_BF16): weights bf16 [Npad][K] (rows >= N zero),
+//    Npad = N rounded up to 128, read through the 2-D TMA map `tmap` (boxes of
+//    128 rows x 64 K with the 128-byte swizzle); K is cut into chunks of KC
+//    (a multiple of 64) whose fp32 partials are reduced in chunk order.
 struct LayerParams {
+    CUtensorMap tmap;   // tensor-core layers only
     const float* w;     // device, kernel layout (see above)
     int32_t K, N, Npad;
     int32_t KC, C;      // K-chunk (multiple of 4) and number of chunks

@@ -1,0 +1,138 @@
+"""GPU parity of the tensor-core GEMM_BF16 stages (tcgen05 MMA, TMA weight
+stream, TMEM accumulator) against the FP64 oracle on bf16-rounded operands,
+and of the whole 3-stage pipeline (2x2 pool + normalise to bf16 -> 37632 ->
+1024 -> 1024 GELU -> 1024 -> 1000 logits + top-5).
+
+Tolerance: the accumulation is FP32 in an order the tensor core fixes, so a
+pre-activation may differ from the exact sum by up to 4 K 2^-24 sum|w x|; the
+GELU passes at most 1.13 times that on, and rounding to bf16 adds one bf16
+unit (2^-8 relative) where the two sides round on different sides of a tie."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+
+
+def _f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _scratch(cm, st, n):
+    _, _, sb = cm.camelot_stage_info(st, n)
+    return torch.empty(sb + 256, dtype=torch.uint8, device="cuda"), sb
+
+
+def _layer_bound(orc, x64, w64, act):
+    ref, a = orc.linear(x64, w64, act, want_absdot=True)
+    K = x64.shape[1]
+    return ref, (1.13 if act == 2 else 1.0) * 4 * K * U * a
+
+
+@pytest.mark.parametrize("K,N,n,act,ctas", [(1024, 256, 16, 2, 8), (4096, 1024, 32, 2, 37),
+                                             (1024, 1000, 5, 0, 3), (512, 128, 1, 1, 1),
+                                             (37632, 1024, 9, 2, 74)])
+def test_gemm_layer_matches_oracle(orc, K, N, n, act, ctas):
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    g = np.random.default_rng(K + N + n)
+    x = _bf(g.standard_normal((n, K)))
+    w = _bf(g.standard_normal((N, K)) / np.sqrt(K))
+    xd, wd = x.cuda(), w.cuda()
+    st = pl.stage_dense(cm.STAGE_GEMM_BF16, [wd], [act], top_k=0, max_batch=32)
+    try:
+        out = torch.full((n, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+        scr, sb = _scratch(cm, st, n)
+        cm.camelot_stage_launch(st, ctas, xd, n, out, None, None, None, scr, sb, None)
+        torch.cuda.synchronize()
+        got = _f64(out)
+        ref, bound = _layer_bound(orc, _f64(x), _f64(w), act)
+        err = np.abs(got - ref)
+        lim = bound + 2.0 ** -8 * np.abs(ref) + 1e-30
+        assert np.all(np.isfinite(got))
+        assert np.all(err <= lim), float((err / lim).max())
+    finally:
+        cm.camelot_stage_release(st)
+
+
+def test_gemm_chain_topk_and_partition_independence(orc):
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    g = np.random.default_rng(5)
+    n = 12
+    dims = [2048, 1024, 1000]
+    x = _bf(g.standard_normal((n, dims[0])))
+    ws = [_bf(g.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i])) for i in range(2)]
+    st = pl.stage_dense(cm.STAGE_GEMM_BF16, [w.cuda() for w in ws], [2, 0], top_k=5, max_batch=32)
+    try:
+        res = []
+        for ctas in (1, 9, 64, 148):
+            idx = torch.empty((n, 5), dtype=torch.int32, device="cuda")
+            val = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+            lg = torch.empty((n, 1000), dtype=torch.float32, device="cuda")
+            scr, sb = _scratch(cm, st, n)
+            cm.camelot_stage_launch(st, ctas, x.cuda(), n, None, idx, val, lg, scr, sb, None)
+            torch.cuda.synchronize()
+            res.append((idx.cpu().numpy(), val.cpu().numpy(), lg.cpu().numpy()))
+        for r in res[1:]:
+            for a, b in zip(res[0], r):
+                assert np.array_equal(a, b)
+        idx, val, lg = res[0]
+        # top-5 is exact on the GPU's own logits
+        ref_idx, ref_val = orc.topk(lg.astype(np.float64), 5)
+        assert np.array_equal(idx, ref_idx) and np.array_equal(val, ref_val.astype(np.float32))
+        # logits within the bound of the bf16-emulated FP64 chain
+        h, b1 = _layer_bound(orc, _f64(x), _f64(ws[0]), 2)
+        h_r = orc.round_bf16(h)
+        z, b2 = _layer_bound(orc, h_r, _f64(ws[1]), 0)
+        # the hidden layer's bf16 rounding may differ by one unit: propagate it
+        e_h = b1 + 2.0 ** -8 * np.abs(h) + 1e-30
+        bound = b2 + e_h @ np.abs(_f64(ws[1])).T
+        assert np.all(np.abs(lg - z) <= bound)
+    finally:
+        cm.camelot_stage_release(st)
+
+
+def test_three_stage_pipeline_bf16(orc):
+    """cfg2 end to end through the persistent pipeline, both handoffs."""
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    n = 48
+    x, ws32 = synth.cfg2_inputs(0, n_queries=n)
+    wb = [_bf(w) for w in ws32]
+    s0 = pl.stage_norm_pool2(224, 224, 3, max_batch=32)
+    s1 = pl.stage_dense(cm.STAGE_GEMM_BF16, [wb[0].cuda(), wb[1].cuda()], [2, 2], top_k=0, max_batch=32)
+    s2 = pl.stage_dense(cm.STAGE_GEMM_BF16, [wb[2].cuda()], [0], top_k=5, max_batch=32)
+    try:
+        outs = {}
+        for mode in (0, 1):
+            sink = torch.zeros((65536, 1000), dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            p = cm.camelot_pipeline_create([s0, s1, s2], pl.alloc([1, 2, 1], [8, 24, 8], 16), mode,
+                                           pl.options(logits_sink=sink.data_ptr()))
+            try:
+                comps = pl.run_all(p, x, stream_id=3, chunk=16, timeout_s=120)
+            finally:
+                cm.camelot_pipeline_destroy(p)
+            outs[mode] = (comps, sink[:n].cpu().numpy())
+        comps, lg = outs[0]
+        assert [c.query_id for c in comps] == list(range(n))
+        assert np.array_equal(lg, outs[1][1])                     # handoff-independent
+        idx = np.array([[c.idx[r] for r in range(5)] for c in comps])
+        ref_idx, _ = orc.topk(lg.astype(np.float64), 5)
+        assert np.array_equal(idx, ref_idx)                        # exact on its own logits
+        z_emul, idx_emul = orc.pipeline_gemm3(x, [_f64(w) for w in wb], top_k=5, emulate_bf16=True)
+        rel = np.abs(lg - z_emul).max() / np.abs(z_emul).max()
+        assert rel < 2e-2, rel
+        agree = np.mean([set(a) == set(b) for a, b in zip(idx, idx_emul)])
+        assert agree >= 0.8, agree
+        top1 = np.mean(idx[:, 0] == idx_emul[:, 0])
+        assert top1 >= 0.9, top1
+    finally:
+        for s in (s0, s1, s2):
+            cm.camelot_stage_release(s)
