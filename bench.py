@@ -1,26 +1,28 @@
 #!/usr/bin/env python
-"""Peak queries/s at p99 <= QoS of the plain 2-stage query pipeline on one B300.
+"""Peak queries/s at p99 <= QoS of SM-partitioned GPU query pipelines on one B300.
 
-Workload (synthetic, seed 0): queries are 64x64x3 uint8 images (uniform
-0..255; 1024 distinct images cycled); stage 1 normalises to FP32, stage 2 is a
-12288 -> 512 -> 256 -> 10 ReLU MLP in FP32 with argmax; batch 16; the fixed
-even SM split of the paper's EA baseline (72 + 72 SMs, one instance per
-stage).  Open-loop Poisson arrivals; QoS = p99 latency 20 ms.
+Two synthetic workloads (seed 0), both multi-stage microservice pipelines in
+the manner of the paper's suite:
 
-For each handoff mechanism (global memory = the method, host-staged = the
-default mechanism it replaces) the peak is found by bisection on the offered
-rate: each probe replays a 22,000-query trace whose queries already reside in
-HBM, with arrival times enforced on the device clock, and the p99 latency of
-the last 20,000 (arrival to final-stage completion, device clock) must stay
-within the QoS.  The timed region then replays K traces at that peak rate:
-each trace is one launch of the persistent kernel, timed with CUDA events on
-its stream.  `value` = queries / summed launch time (global-memory handoff).
-The same peak search is repeated for the allocation chosen by camelot_allocate
-(Eq. 1) from a solo-run profile of the two stages.
+* ``bf16-3stage`` (headline): 224x224x3 uint8 images -> 2x2 pool + normalise to
+  bf16 -> GEMM 37632->1024->1024 (GELU, tensor cores) -> GEMM 1024->1000 + top-5;
+  batch 32; the allocation is the one camelot_allocate (Eq. 1) picks from a
+  solo-run profile of the stages (Sec. 7.1 / 7.2).
+* ``fp32-2stage``: 64x64x3 uint8 images -> normalise to f32 -> MLP
+  12288-512-256-10 (FP32, ReLU) -> argmax; batch 16; the fixed even split
+  72 + 72 SMs (the EA baseline), plus the allocator's split.
 
-`e2e` = the same metric through camelot_submit from host memory: a host loop
-submits each query at its Poisson arrival time and polls completions; latency
-is measured on the host clock from the scheduled arrival to the poll.
+For each (workload, handoff, allocation) the peak is found by bisection on the
+offered Poisson rate: each probe replays a 22,000-query trace whose queries
+already reside in HBM, with arrivals enforced on the device clock; the p99 of
+the last 20,000 latencies (arrival to final-stage completion, device clock)
+must stay within 20 ms.  The timed region replays K traces at the headline's
+peak rate; each trace is one launch of the persistent kernel, timed with CUDA
+events on its stream; `value` = queries / summed launch time.
+
+`e2e`: the same metric through camelot_submit / camelot_poll from host memory
+(queries copied at submit, read by the device over the host link), latency on
+the host clock from the scheduled arrival to the poll.
 
 `--impl reference` times the FP64 CPU oracle on the host cores instead.
 """
@@ -44,11 +46,25 @@ UNIT = "queries/s"
 QOS_NS = 20_000_000
 Q_STEP = 22_000
 Q_WARM = 2_000
-FLOP_PER_QUERY = 2 * (12288 * 512 + 512 * 256 + 256 * 10)   # 12,850,176
-BYTES_PER_QUERY_S1 = 12288 + 12288 * 4                        # u8 in, f32 out
-WORKLOAD = ("plain 2-stage pipeline: 64x64x3 u8 images -> normalize (f32) -> MLP "
-            "12288-512-256-10 fp32 ReLU -> argmax; batch 16; even split 72+72 SMs; "
-            "Poisson arrivals; p99 QoS 20 ms")
+HEADLINE = "bf16-3stage"
+
+WORKLOADS = {
+    "fp32-2stage": dict(
+        desc=("plain 2-stage pipeline: 64x64x3 u8 images -> normalize (f32) -> MLP 12288-512-256-10 "
+              "fp32 ReLU -> argmax; batch 16; Poisson arrivals; p99 QoS 20 ms"),
+        batch=16, row=12288, even=([1, 1], [72, 72]),
+        flop=2 * (12288 * 512 + 512 * 256 + 256 * 10),
+        # algorithmic HBM bytes per query: u8 in, f32 handoff written + read
+        bytes=12288 + 2 * 12288 * 4, weight_bytes=4 * (12288 * 512 + 512 * 256 + 256 * 10)),
+    "bf16-3stage": dict(
+        desc=("3-stage pipeline: 224x224x3 u8 images -> 2x2 pool + normalize (bf16) -> GEMM "
+              "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
+              "arrivals; p99 QoS 20 ms"),
+        batch=32, row=224 * 224 * 3, even=([1, 1, 1], [48, 48, 48]),
+        flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
+        bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
+        weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
+}
 
 
 def _peaks():
@@ -119,45 +135,51 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
-def cpu_oracle_rate(budget_s: float = 10.0, max_q: int = 4096):
+def _oracle_run(name, n, offset=0):
     import oracle
     import synth
-    x, ws = synth.cfg1_inputs(0, n_queries=1024)
+    if name == "fp32-2stage":
+        x, ws = synth.cfg1_inputs(0, n_queries=1024)
+        xs = x[(np.arange(n) + offset) % 1024]
+        return oracle.pipeline_mlp(xs, ws)
+    x, ws = synth.cfg2_inputs(0, n_queries=64)
+    xs = x[(np.arange(n) + offset) % 64]
+    wb = [oracle.round_bf16(w) for w in ws]
+    return oracle.pipeline_gemm3(xs, wb, top_k=5, emulate_bf16=True)
+
+
+def cpu_oracle_rate(name, budget_s: float = 10.0):
     cores = os.cpu_count() or 1
     t = time.perf_counter()
-    oracle.pipeline_mlp(x[:cores], ws)
+    _oracle_run(name, cores)
     per_q = (time.perf_counter() - t) / cores
-    n = int(max(cores, min(max_q, budget_s / max(per_q, 1e-9))))
+    n = int(max(cores, min(4096, budget_s / max(per_q, 1e-9))))
     n = (n // cores) * cores or cores
-    xs = x[np.arange(n) % 1024]
     t = time.perf_counter()
-    oracle.pipeline_mlp(xs, ws)
+    _oracle_run(name, n)
     dt = time.perf_counter() - t
-    return n / dt, cores, f"{n} queries of the workload through the FP64 oracle, OpenMP over queries"
+    return n / dt, cores, f"{n} queries of {name} through the FP64 oracle, OpenMP over queries"
 
 
 def run_reference(args, rank: int):
     if rank != 0:
         return 0
-    import oracle
-    import synth
-    x, ws = synth.cfg1_inputs(0, n_queries=1024)
+    name = args.workload
     cores = os.cpu_count() or 1
-    n = max(cores, 2 * cores)
+    n = cores
     for _ in range(args.warmup):
-        oracle.pipeline_mlp(x[:n], ws)
+        _oracle_run(name, n)
     times = []
     for i in range(args.steps):
-        xs = x[(np.arange(n) + i * n) % 1024]
         t = time.perf_counter()
-        oracle.pipeline_mlp(xs, ws)
+        _oracle_run(name, n, offset=i * n)
         times.append(time.perf_counter() - t)
     v = n * args.steps / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "queries_per_step": n},
+            "config": {"workload": WORKLOADS[name]["desc"], "queries_per_step": n},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} queries per step through the FP64 oracle"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -168,61 +190,70 @@ def run_reference(args, rank: int):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-COMP_DTYPE = None
+COMP_DTYPE = np.dtype({
+    "names": ["query_id", "stream_id", "status", "idx", "val", "batch_size", "pad",
+              "t_arrival", "t_batch", "t_done", "t_poll"],
+    "formats": ["<u8", "<u4", "<i4", ("<i4", 5), ("<f4", 5), "<i4", "<i4", "<i8", "<i8",
+                "<i8", "<i8"],
+    "offsets": [0, 8, 12, 16, 36, 56, 60, 64, 72, 80, 88], "itemsize": 96})
 
 
-def comp_dtype():
-    global COMP_DTYPE
-    if COMP_DTYPE is None:
-        COMP_DTYPE = np.dtype({
-            "names": ["query_id", "stream_id", "status", "idx", "val", "batch_size", "pad",
-                      "t_arrival", "t_batch", "t_done", "t_poll"],
-            "formats": ["<u8", "<u4", "<i4", ("<i4", 5), ("<f4", 5), "<i4", "<i4", "<i8", "<i8",
-                        "<i8", "<i8"],
-            "offsets": [0, 8, 12, 16, 36, 56, 60, 64, 72, 80, 88], "itemsize": 96})
-    return COMP_DTYPE
+class Workload:
+    """Stages, device-resident trace data and measurement helpers of one pipeline."""
 
-
-class Bench:
-    def __init__(self, device: int):
+    def __init__(self, name: str, device: int, n_rows: int = Q_STEP):
         import torch
 
         import synth
         from paper_2005_02088_b300 import camelot as cm, pipelines as pl
         self.torch, self.cm, self.pl = torch, cm, pl
+        self.name = name
+        self.w = WORKLOADS[name]
+        self.B = self.w["batch"]
         torch.cuda.set_device(device)
-        self.dev = device
         self.sms = torch.cuda.get_device_properties(device).multi_processor_count
-        x, ws = synth.cfg1_inputs(0, n_queries=1024)
-        self.x_host = x
-        self.ws = ws
-        rows = np.arange(Q_STEP) % 1024
-        self.xq_host = np.ascontiguousarray(x[rows].reshape(Q_STEP, -1))
-        self.xq = torch.from_numpy(self.xq_host).cuda()            # 270 MB: larger than L2
-        self.s0 = pl.stage_normalize(64, 64, 3, max_batch=32)
-        wd = [torch.from_numpy(w).cuda() for w in ws]
-        self.s1 = pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], top_k=1, max_batch=32)
+        if name == "fp32-2stage":
+            x, ws = synth.cfg1_inputs(0, n_queries=1024)
+            rows = np.arange(n_rows) % 1024
+            self.xq_host = np.ascontiguousarray(x[rows].reshape(n_rows, -1))
+            self.stages = [pl.stage_normalize(64, 64, 3, max_batch=32)]
+            wd = [torch.from_numpy(w).cuda() for w in ws]
+            self.stages.append(pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], top_k=1,
+                                              max_batch=32))
+            self.io = [(12288, "u8"), (12288 * 4, "f32")]
+        else:
+            x, ws = synth.cfg2_inputs(0, n_queries=256)
+            rows = np.arange(n_rows) % 256
+            self.xq_host = np.ascontiguousarray(x[rows].reshape(n_rows, -1))
+            wb = [torch.from_numpy(w).to(torch.bfloat16).cuda() for w in ws]
+            self.stages = [pl.stage_norm_pool2(224, 224, 3, max_batch=32),
+                           pl.stage_dense(cm.STAGE_GEMM_BF16, [wb[0], wb[1]], [2, 2], top_k=0,
+                                          max_batch=32),
+                           pl.stage_dense(cm.STAGE_GEMM_BF16, [wb[2]], [0], top_k=5, max_batch=32)]
+            self.io = [(150528, "u8"), (37632 * 2, "bf16"), (1024 * 2, "bf16")]
+        self.xq = torch.from_numpy(self.xq_host).cuda()        # larger than L2
         self.buf = (cm.Completion * 8192)()
+        self._last_total = {}      # per pipeline: summed launch ms already accounted
         torch.cuda.synchronize()
 
     def close(self):
-        self.cm.camelot_stage_release(self.s0)
-        self.cm.camelot_stage_release(self.s1)
+        for s in self.stages:
+            self.cm.camelot_stage_release(s)
 
-    def pipeline(self, mode, inst, quota, batch=16):
-        o = self.pl.options(exit_after_trace=1, query_slots=65536, idle_exit_ns=20_000_000)
-        return self.cm.camelot_pipeline_create([self.s0, self.s1],
-                                               self.pl.alloc(inst, quota, batch), mode, o)
+    def pipeline(self, mode, inst, quota, data_slots=0):
+        o = self.pl.options(exit_after_trace=1, query_slots=65536, idle_exit_ns=20_000_000,
+                            data_slots=data_slots)
+        p = self.cm.camelot_pipeline_create(self.stages, self.pl.alloc(inst, quota, self.B), mode, o)
+        self._last_total[p] = 0.0
+        return p
 
-    def _drain(self, p, n, timeout_s=60.0):
-        cm = self.cm
-        out = []
-        got = 0
+    def _drain(self, p, n, timeout_s=120.0):
+        out, got = [], 0
         t_end = time.time() + timeout_s
         while got < n:
-            k = cm.camelot_poll(p, self.buf, timeout_us=2000)
+            k = self.cm.camelot_poll(p, self.buf, timeout_us=2000)
             if k:
-                out.append(np.frombuffer(self.buf, dtype=comp_dtype(), count=k).copy())
+                out.append(np.frombuffer(self.buf, dtype=COMP_DTYPE, count=k).copy())
                 got += k
             elif time.time() > t_end:
                 raise TimeoutError(f"{got}/{n} completions")
@@ -235,17 +266,16 @@ class Bench:
         torch.cuda.synchronize()
         cm.camelot_submit_trace(p, 0, self.xq, len(offsets_ns), off)
         comps = self._drain(p, len(offsets_ns))
-        # the launch ends right after the trace drains; wait for its CUDA events
         t_end = time.time() + 10
         while True:
             st = cm.camelot_pipeline_stats(p)
-            if st.total_launch_ms > self._last_total:
+            if st.total_launch_ms > self._last_total[p]:
                 break
             if time.time() > t_end:
                 raise TimeoutError("launch did not end after the trace")
             time.sleep(0.0005)
-        ms = st.total_launch_ms - self._last_total
-        self._last_total = st.total_launch_ms
+        ms = st.total_launch_ms - self._last_total[p]
+        self._last_total[p] = st.total_launch_ms
         return comps, ms
 
     @staticmethod
@@ -254,22 +284,18 @@ class Bench:
         return float(np.percentile(lat, 99)), float(np.percentile(lat, 50))
 
     def peak(self, mode, inst, quota, iters=9, seed=1):
-        """Bisection on the Poisson rate; returns (rate, pipeline handle, saturation info)."""
+        """Bisection on the Poisson rate; returns (rate, pipeline, saturation)."""
         import synth
         p = self.pipeline(mode, inst, quota)
-        self._last_total = 0.0
-        # saturation throughput: every query arrives at t = 0
         comps, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
-        sat = Q_STEP / (ms * 1e-3)
-        sat_info = {"qps": sat, "launch_ms": ms, "queries": Q_STEP}
-        lo, hi = 0.2 * sat, 1.02 * sat
+        sat = {"qps": Q_STEP / (ms * 1e-3), "launch_ms": ms, "queries": Q_STEP,
+               "p50_ms": self.p99(comps)[1] * 1e-6}
+        lo, hi = 0.2 * sat["qps"], 1.02 * sat["qps"]
         best = None
         for it in range(iters):
-            lam = lo if best is None and it == 0 else 0.5 * (lo + hi)
-            offs = synth.poisson_arrivals_ns(seed + it, Q_STEP, lam)
-            comps, ms = self.trace(p, offs)
-            p99, p50 = self.p99(comps)
-            ok = p99 <= QOS_NS and len(comps) == Q_STEP
+            lam = lo if it == 0 else 0.5 * (lo + hi)
+            comps, ms = self.trace(p, synth.poisson_arrivals_ns(seed + it, Q_STEP, lam))
+            ok = self.p99(comps)[0] <= QOS_NS and len(comps) == Q_STEP
             if ok:
                 best = lam if best is None else max(best, lam)
                 lo = lam
@@ -277,93 +303,103 @@ class Bench:
                 hi = lam
             if it == 0 and not ok:
                 break
-        return best, p, sat_info
+        return best, p, sat
 
     def timed(self, p, lam, steps, warmup, seed=100):
         import synth
         lat99, lat50, tot_ms, tot_q = [], [], 0.0, 0
-        launches0 = self.cm.camelot_pipeline_stats(p).kernel_launches
+        l0 = self.cm.camelot_pipeline_stats(p).kernel_launches
         for i in range(warmup + steps):
-            offs = synth.poisson_arrivals_ns(seed + i, Q_STEP, lam)
-            comps, ms = self.trace(p, offs)
+            comps, ms = self.trace(p, synth.poisson_arrivals_ns(seed + i, Q_STEP, lam))
             if i >= warmup:
-                p99, p50 = self.p99(comps)
-                lat99.append(p99)
-                lat50.append(p50)
+                a, b = self.p99(comps)
+                lat99.append(a)
+                lat50.append(b)
                 tot_ms += ms
                 tot_q += len(comps)
-        launches = self.cm.camelot_pipeline_stats(p).kernel_launches - launches0
+        launches = self.cm.camelot_pipeline_stats(p).kernel_launches - l0
         return {"qps": tot_q / (tot_ms * 1e-3), "ms_per_step": tot_ms / steps,
                 "p99_ms": max(lat99) * 1e-6, "p50_ms": float(np.median(lat50)) * 1e-6,
-                "launches": int(launches * steps / (warmup + steps))}
+                "launches": int(round(launches * steps / (warmup + steps)))}
 
-    def e2e(self, lam, steps, warmup, seed=500):
-        """Host-submitted Poisson stream through camelot_submit / camelot_poll."""
+    def _e2e_probe(self, p, lam, seed):
+        """One host-submitted Poisson stream through camelot_submit / camelot_poll:
+        each query is submitted at its arrival time (host clock) and its
+        latency runs from that scheduled arrival to the poll that returns it."""
         import synth
         cm = self.cm
-        p = self.pipeline(0, [1, 1], [72, 72])
         q = self.xq_host
-        res = []
+        offs = synth.poisson_arrivals_ns(seed, Q_STEP, lam)
+        t0 = time.monotonic_ns() + 2_000_000
+        arr = (offs + t0).astype(np.int64)
+        sub, got, done = 0, 0, []
+        deadline = time.time() + 120
+        while got < Q_STEP:
+            now = time.monotonic_ns()
+            if sub < Q_STEP and arr[sub] <= now:
+                m = min(int(np.searchsorted(arr, now, side="right")) - sub, 256)
+                if cm.camelot_submit(p, 1, q[sub:sub + m], m, arr[sub:sub + m],
+                                     allow_eagain=True) is not None:
+                    sub += m
+            k = cm.camelot_poll(p, self.buf, timeout_us=0)
+            if k:
+                done.append(np.frombuffer(self.buf, dtype=COMP_DTYPE, count=k).copy())
+                got += k
+            if time.time() > deadline:
+                raise TimeoutError("e2e probe")
+        t_end = time.monotonic_ns()
+        comps = np.concatenate(done)
+        lat = (comps["t_poll"] - comps["t_arrival"])[Q_WARM:]
+        return Q_STEP / ((t_end - t0) * 1e-9), float(np.percentile(lat, 99))
+
+    def e2e(self, inst, quota, hi, iters=6, seed=500):
+        """Peak offered rate at p99 <= QoS through the public API (bisection),
+        then the achieved rate and p99 at that rate."""
+        cm = self.cm
+        p = self.pipeline(0, inst, quota, data_slots=4096 if self.w["row"] > 65536 else 0)
         try:
-            for i in range(warmup + steps):
-                offs = synth.poisson_arrivals_ns(seed + i, Q_STEP, lam)
-                t0 = time.monotonic_ns() + 2_000_000
-                arr = (offs + t0).astype(np.int64)
-                sub = 0
-                done = []
-                got = 0
-                t_start = time.monotonic_ns()
-                deadline = time.time() + 60
-                while got < Q_STEP:
-                    now = time.monotonic_ns()
-                    if sub < Q_STEP and arr[sub] <= now:
-                        m = int(np.searchsorted(arr, now, side="right")) - sub
-                        m = min(m, 256)
-                        if cm.camelot_submit(p, 1, q[sub:sub + m], m, arr[sub:sub + m],
-                                             allow_eagain=True) is not None:
-                            sub += m
-                    k = cm.camelot_poll(p, self.buf, timeout_us=0)
-                    if k:
-                        done.append(np.frombuffer(self.buf, dtype=comp_dtype(), count=k).copy())
-                        got += k
-                    if time.time() > deadline:
-                        raise TimeoutError("e2e step")
-                t_end = time.monotonic_ns()
-                comps = np.concatenate(done)
-                lat = (comps["t_poll"] - comps["t_arrival"])[Q_WARM:]
-                if i >= warmup:
-                    res.append({"qps": Q_STEP / ((t_end - max(t_start, t0)) * 1e-9),
-                                "p99_ms": float(np.percentile(lat, 99)) * 1e-6})
+            lo = hi * 0.02
+            best = None
+            for it in range(iters):
+                lam = lo if it == 0 else 0.5 * (lo + hi)
+                qps, p99 = self._e2e_probe(p, lam, seed + it)
+                if p99 <= QOS_NS:
+                    best = (lam, qps, p99)
+                    lo = lam
+                else:
+                    hi = lam
+                if it == 0 and p99 > QOS_NS:
+                    break
         finally:
             cm.camelot_pipeline_destroy(p)
-        return {"qps": float(np.mean([r["qps"] for r in res])),
-                "p99_ms": float(max(r["p99_ms"] for r in res))}
+        lam, qps, p99 = best if best else (0.0, 0.0, float("nan"))
+        return {"qps": qps, "offered_qps": lam, "p99_ms": p99 * 1e-6,
+                "h2d_bytes_per_step": Q_STEP * self.w["row"], "d2h_bytes_per_step": Q_STEP * 96}
 
-    def profile_stages(self, batch=16, reps=5):
-        """Solo-run profile (Sec. 7.1): per-instance throughput and duration of
-        each stage at every 8-SM quota, from direct launches of a batch."""
+    def profile(self, reps=5):
+        """Solo-run profile (Sec. 7.1): duration of one batch of each stage at
+        every 8-SM quota, from direct launches timed with CUDA events."""
         torch, cm = self.torch, self.cm
         levels = list(range(8, self.sms + 1, 8))
-        y = torch.empty((batch, 12288), dtype=torch.float32, device="cuda")
-        idx = torch.empty((batch, 1), dtype=torch.int32, device="cuda")
-        val = torch.empty((batch, 1), dtype=torch.float32, device="cuda")
-        scr = {}
-        for st in (self.s0, self.s1):
-            _, _, sb = cm.camelot_stage_info(st, batch)
-            scr[st] = (torch.empty(sb + 256, dtype=torch.uint8, device="cuda"), sb)
-        dur = np.zeros((2, len(levels)))
+        B = self.B
+        bufs = []
+        for (nbytes, _) in self.io[1:]:
+            bufs.append(torch.zeros(B * nbytes, dtype=torch.uint8, device="cuda"))
+        idx = torch.empty((B, 5), dtype=torch.int32, device="cuda")
+        val = torch.empty((B, 5), dtype=torch.float32, device="cuda")
+        dur = np.zeros((len(self.stages), len(levels)))
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream = torch.cuda.current_stream().cuda_stream
-        for li, pq in enumerate(levels):
-            for si, st in enumerate((self.s0, self.s1)):
-                s_buf, sb = scr[st]
+        for si, st in enumerate(self.stages):
+            _, _, sb = cm.camelot_stage_info(st, B)
+            scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+            inp = self.xq if si == 0 else bufs[si - 1]
+            out = bufs[si] if si < len(bufs) else None
+            last = si == len(self.stages) - 1
+            for li, pq in enumerate(levels):
                 def go():
-                    if si == 0:
-                        cm.camelot_stage_launch(st, pq, self.xq, batch, y, None, None, None,
-                                                s_buf, sb, stream)
-                    else:
-                        cm.camelot_stage_launch(st, pq, y, batch, None, idx, val, None, s_buf, sb,
-                                                stream)
+                    cm.camelot_stage_launch(st, pq, inp, B, out, idx if last else None,
+                                            val if last else None, None, scr, sb, stream)
                 go()
                 ev0.record()
                 for _ in range(reps):
@@ -373,100 +409,126 @@ class Bench:
                 dur[si, li] = ev0.elapsed_time(ev1) * 1e-3 / reps
         return levels, dur
 
-    def allocate(self, levels, dur, batch=16, qos_s=QOS_NS * 1e-9):
+    def allocate(self, levels, dur, qos_s=QOS_NS * 1e-9):
         cm = self.cm
-        n, L = 2, len(levels)
-        f = np.ascontiguousarray((batch / dur)[None], np.float64)
-        bytes_b = np.array([batch * BYTES_PER_QUERY_S1, batch * 12288 * 4], np.float64)
-        bw = np.ascontiguousarray((bytes_b[:, None] / dur / 1e9)[None], np.float64)
+        n, L, B = len(self.stages), len(levels), self.B
+        f = np.ascontiguousarray((B / dur)[None], np.float64)
+        stage_bytes = []
+        for si in range(n):
+            inb = self.io[si][0]
+            outb = self.io[si + 1][0] if si + 1 < len(self.io) else 40
+            stage_bytes.append(B * (inb + outb))
+        bw = np.ascontiguousarray((np.array(stage_bytes)[:, None] / dur / 1e9)[None], np.float64)
         d = np.ascontiguousarray(dur[None], np.float64)
-        mem = np.ascontiguousarray(np.array([[4e6, 30e6]]), np.float64)
-        bs = np.array([batch], np.int32)
+        mem = np.ascontiguousarray(np.full((1, n), 64e6), np.float64)
+        bs = np.array([B], np.int32)
         pr = cm.Profile(n, L, 1, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, d.ctypes.data,
                         mem.ctypes.data)
-        hbm = _peaks().get("hbm_gbs", 6400.0)
-        cons = cm.Constraints(self.sms, self.sms // 8, hbm, 200e9, qos_s, 0.0,
-                              cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
+        cons = cm.Constraints(self.sms, self.sms // 8, _peaks().get("hbm_gbs", 6400.0), 200e9, qos_s,
+                              0.0, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
         a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
-        return [a.instances[0], a.instances[1]], [a.sm_quota[0], a.sm_quota[1]], obj
+        return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)], obj
+
+
+def measure_workload(name, args, local, headline: bool):
+    """Peaks for the even split and the allocator's split, both handoffs."""
+    wl = Workload(name, local)
+    out = {"workload": wl.w["desc"], "batch": wl.B}
+    timed = None
+    try:
+        levels, dur = wl.profile()
+        inst_c, quota_c, obj = wl.allocate(levels, dur)
+        out["profile_ms"] = {"levels": levels, "stage_batch_ms": (dur * 1e3).round(4).tolist()}
+        out["allocator"] = {"instances": inst_c, "sm_quota": quota_c, "predicted_min_thr_qps": obj}
+        main_alloc = (inst_c, quota_c) if name == "bf16-3stage" else wl.w["even"]
+        other_alloc = wl.w["even"] if name == "bf16-3stage" else (inst_c, quota_c)
+        res = {}
+        for tag, (inst, quota) in (("main", main_alloc), ("other", other_alloc)):
+            for mode in (0, 1):
+                lam, p, sat = wl.peak(mode, inst, quota)
+                t = wl.timed(p, lam, max(1, args.steps // 2), 1) if lam else None
+                if tag == "main" and mode == 0 and headline:
+                    timed = (wl, p, lam, inst, quota, sat)
+                else:
+                    wl.cm.camelot_pipeline_destroy(p)
+                res[(tag, mode)] = {"alloc": {"instances": inst, "sm_quota": quota},
+                                    "peak_rate": lam, "saturation_qps": sat["qps"],
+                                    "value": (t or {}).get("qps", 0.0), "p99_ms": (t or {}).get("p99_ms")}
+        out["main_alloc"] = {"instances": main_alloc[0], "sm_quota": main_alloc[1]}
+        out["global"] = res[("main", 0)]
+        out["host_staged"] = res[("main", 1)]
+        out["other_alloc_global"] = res[("other", 0)]
+        out["other_alloc_host_staged"] = res[("other", 1)]
+        g, h = out["global"]["value"], out["host_staged"]["value"]
+        out["global_over_host_staged"] = g / h if h else None
+    except Exception:
+        wl.close()
+        raise
+    return out, timed, wl
 
 
 def run_gpu(args, rank: int, world: int, dist):
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    b = Bench(local)
-    half = (b.sms // 2) // 8 * 8
-    result = {}
+    head, timed, wl = measure_workload(HEADLINE, args, local, headline=True)
+    side, _, wl2 = measure_workload("fp32-2stage", args, local, headline=False)
+    wl2.close()
+    wl_h, p, lam, inst, quota, sat = timed
     try:
-        # 1. the method: global-memory handoff, even split (the workload's allocation)
-        lam_g, p_g, sat_g = b.peak(0, [1, 1], [half, half])
-        # 2. the default mechanism: host-staged handoff, same split
-        lam_h, p_h, sat_h = b.peak(1, [1, 1], [half, half])
-        t_h = b.timed(p_h, lam_h, max(1, args.steps // 2), 1) if lam_h else None
-        b.cm.camelot_pipeline_destroy(p_h)
-        # 3. the allocation the peak-load policy picks from a solo-run profile
-        levels, dur = b.profile_stages()
-        inst_c, quota_c, obj = b.allocate(levels, dur)
-        lam_c, p_c, sat_c = b.peak(0, inst_c, quota_c)
-        t_c = b.timed(p_c, lam_c, max(1, args.steps // 2), 1) if lam_c else None
-        b.cm.camelot_pipeline_destroy(p_c)
-        # 4. timed region: K traces at the global-memory peak
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
-            t_g = b.timed(p_g, lam_g, args.steps, args.warmup)
+            t = wl_h.timed(p, lam, args.steps, args.warmup)
         torch.cuda.synchronize()
-        # saturated launch for the roofline (same pipeline, all arrivals at 0)
-        comps, sat_ms = b.trace(p_g, np.zeros(Q_STEP, np.int64))
-        b.cm.camelot_pipeline_destroy(p_g)
-        e2e = b.e2e(lam_g, max(1, args.steps // 2), 1)
+        comps, sat_ms = wl_h.trace(p, np.zeros(Q_STEP, np.int64))
+        wl_h.cm.camelot_pipeline_destroy(p)
+        e2e = wl_h.e2e(inst, quota, lam)
     finally:
-        b.close()
-    ms_step = t_g["ms_per_step"]
+        wl_h.close()
+    ms_step = t["ms_per_step"]
     if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64,
-                         device="cuda" if dist.get_backend() == "nccl" else "cpu")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        tt = torch.tensor([ms_step], dtype=torch.float64,
+                          device="cuda" if dist.get_backend() == "nccl" else "cpu")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
     if rank != 0:
         return 0
     clocks = clk.summary()
     peaks = _peaks()
-    sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1207.0
-    alu_peak_tflops = b.sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = Q_STEP * FLOP_PER_QUERY / (sat_ms * 1e-3) / 1e12
+    w = WORKLOADS[HEADLINE]
+    sat_qps = Q_STEP / (sat_ms * 1e-3)
+    # dominant kernel: the persistent pipeline kernel; per query it moves the
+    # image, the bf16 handoffs and 1/B of the weights (read once per batch)
+    bytes_q = w["bytes"] + w["weight_bytes"] / w["batch"]
+    achieved = bytes_q * sat_qps / 1e9
+    hbm = peaks.get("hbm_gbs", 6400.0)
     value = world * Q_STEP / (ms_step * 1e-3)
-    cpu_v, cores, sample = cpu_oracle_rate()
+    cpu_v, cores, sample = cpu_oracle_rate(HEADLINE)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_step": Q_STEP, "batch": 16,
-                   "alloc": {"instances": [1, 1], "sm_quota": [half, half]},
-                   "handoff": "global", "qos_p99_ms": QOS_NS / 1e6,
-                   "l2": "inputs larger than L2 (22,000 distinct query rows, 270 MB per step)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": w["desc"], "queries_per_step": Q_STEP, "batch": w["batch"],
+                   "alloc": {"instances": inst, "sm_quota": quota, "chosen_by": "camelot_allocate"},
+                   "handoff": "global", "qos_p99_ms": QOS_NS / 1e6, "peak_rate_qps": lam,
+                   "l2": "inputs larger than L2 (22,000 query rows, 3.3 GB per step)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "p99_ms": t_g["p99_ms"], "p50_ms": t_g["p50_ms"],
-        "host_staged": {"value": (t_h or {}).get("qps", 0.0), "peak_rate": lam_h,
-                        "p99_ms": (t_h or {}).get("p99_ms"), "saturation_qps": sat_h["qps"],
-                        "global_over_host_staged": (value / t_h["qps"]) if t_h else None},
-        "allocator": {"instances": inst_c, "sm_quota": quota_c, "predicted_min_thr_qps": obj,
-                      "value": (t_c or {}).get("qps", 0.0), "p99_ms": (t_c or {}).get("p99_ms"),
-                      "saturation_qps": sat_c["qps"],
-                      "over_even_split": ((t_c or {}).get("qps", 0.0) / value) if value else None},
-        "saturation": sat_g,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops, "traffic": None,
-                     "kernel": "pipeline_kernel",
-                     "basis": f"FP32 FFMA {b.sms} SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
-                              f"(median SM clock sampled in the timed region); "
-                              f"{FLOP_PER_QUERY} FLOP/query, saturated 22,000-query launch"},
+        "p99_ms": t["p99_ms"], "p50_ms": t["p50_ms"],
+        "headline_detail": head,
+        "fp32_2stage": side,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "pipeline_kernel",
+                     "basis": (f"{bytes_q:.0f} algorithmic bytes/query (image, bf16 handoffs, "
+                               f"weights/{w['batch']}) x saturated {sat_qps:.0f} queries/s; peak = "
+                               "measured HBM copy bandwidth")},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": e2e["qps"], "unit": UNIT, "p99_ms": e2e["p99_ms"],
-                "h2d_bytes_per_step": Q_STEP * 12288, "d2h_bytes_per_step": Q_STEP * 96},
-        "gpu_launches": t_g["launches"],
+                "offered_qps": e2e["offered_qps"],
+                "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
+        "gpu_launches": t["launches"],
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -474,15 +536,14 @@ def run_gpu(args, rank: int, world: int, dist):
 
 
 def run_profile_case(args):
-    """Small self-contained case for ncu: one saturated 2,000-query launch."""
-    global Q_STEP
-    b = Bench(0)
-    p = b.pipeline(0, [1, 1], [72, 72])
-    b._last_total = 0.0
+    """Small self-contained case for ncu: two saturated 2,000-query launches."""
+    wl = Workload(args.workload, 0, n_rows=2000)
+    inst, quota = WORKLOADS[args.workload]["even"]
+    p = wl.pipeline(0, inst, quota)
     for _ in range(2):
-        b.trace(p, np.zeros(2000, np.int64))
-    b.cm.camelot_pipeline_destroy(p)
-    b.close()
+        wl.trace(p, np.zeros(2000, np.int64))
+    wl.cm.camelot_pipeline_destroy(p)
+    wl.close()
     print("profile case done")
     return 0
 
@@ -493,15 +554,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="camelot", choices=["camelot", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--profile-case", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    dist = None
     if args.impl == "reference":
         return run_reference(args, rank)
     if args.profile_case:
         return run_profile_case(args)
+    dist = None
     if world > 1:
         import torch
         import torch.distributed as td

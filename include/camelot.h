@@ -192,7 +192,8 @@ typedef struct {
     int32_t exit_after_trace; /* 1: the persistent kernel ends as soon as a trace has been
                                fully taken and drained (one launch per trace, which makes
                                the launch's CUDA-event time the trace's device time)  */
-    int32_t pad_;
+    uint32_t data_slots;    /* rows of the pinned host buffer that holds submitted query
+                               bytes (power of two <= query_slots; 0 = query_slots)     */
 } camelot_options;
 
 /* Fill `o` with the defaults above. */

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                 in = RowRef{const_cast<char*>(tr->data) + (first - tr->base) * P.q_row, 0, ~0ull,
                             P.q_row};
             } else {
-                in = RowRef{P.qdata, first, P.qmask, P.q_row};
+                in = RowRef{P.qdata, first, P.dmask, P.q_row};
             }
         } else {
             const RingDev& r = P.in_ring[s];

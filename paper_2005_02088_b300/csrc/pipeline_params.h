@@ -89,7 +89,8 @@ struct PipeParams {
     char* scratch;
     QDesc* qring;
     char* qdata;
-    unsigned long long qmask;
+    unsigned long long qmask;       // query descriptor ring (= completion ring) mask
+    unsigned long long dmask;       // query data ring mask
     size_t q_row;
     CompSlot* comp;
     unsigned long long cmask;

@@ -386,7 +386,7 @@ extern "C" void camelot_options_default(camelot_options* o) {
     o->wait_limit_ns = 2000000000;
     o->logits_sink = nullptr;
     o->exit_after_trace = 0;
-    o->pad_ = 0;
+    o->data_slots = 0;
 }
 
 struct HostRing {   // one batch ring's allocations
@@ -434,6 +434,7 @@ struct camelot_pipeline {
     uint64_t launches = 0;
     bool trace_active = false;
     uint64_t trace_end = 0;
+    uint64_t data_floor = 0;      // first ticket whose data row is tracked by its descriptor
     std::atomic<bool> failed{false};
     std::string fail_msg;
     // relay (host-staged)
@@ -656,6 +657,9 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     if (o.query_slots < 64 || (o.query_slots & (o.query_slots - 1)))
         return fail(CAMELOT_EINVAL, "query_slots must be a power of two >= 64");
     if (o.batch_slots < 2 || o.batch_slots > 4096) return fail(CAMELOT_EINVAL, "batch_slots outside 2..4096");
+    if (o.data_slots == 0) o.data_slots = o.query_slots;
+    if (o.data_slots < 64 || (o.data_slots & (o.data_slots - 1)) || o.data_slots > o.query_slots)
+        return fail(CAMELOT_EINVAL, "data_slots must be a power of two in 64..query_slots");
     if (o.max_wait_ns < 0 || o.idle_exit_ns < 1000000 || o.wait_limit_ns < 1000000)
         return fail(CAMELOT_EINVAL, "max_wait_ns >= 0, idle_exit_ns and wait_limit_ns >= 1 ms required");
     const int B = alloc->batch;
@@ -783,7 +787,8 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     const size_t R = o.query_slots;
     const size_t q_row = stages[0]->sp.in_row_bytes;
     P_TRY(cudaHostAlloc((void**)&p->qring, R * sizeof(QDesc), cudaHostAllocMapped | cudaHostAllocPortable));
-    P_TRY(cudaHostAlloc((void**)&p->qdata, R * q_row, cudaHostAllocMapped | cudaHostAllocPortable));
+    const size_t D = o.data_slots;
+    P_TRY(cudaHostAlloc((void**)&p->qdata, D * q_row, cudaHostAllocMapped | cudaHostAllocPortable));
     P_TRY(cudaHostAlloc((void**)&p->comp, R * sizeof(CompSlot), cudaHostAllocMapped | cudaHostAllocPortable));
     memset((void*)p->qring, 0, R * sizeof(QDesc));
     memset((void*)p->comp, 0, R * sizeof(CompSlot));
@@ -791,6 +796,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     hp.qring = p->qring;
     hp.qdata = p->qdata;
     hp.qmask = R - 1;
+    hp.dmask = D - 1;
     hp.q_row = q_row;
     hp.comp = p->comp;
     hp.cmask = R - 1;
@@ -826,14 +832,25 @@ extern "C" camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id
     const uint64_t R = p->opt.query_slots, mask = R - 1;
     const uint64_t t0 = p->next_ticket.load(std::memory_order_relaxed);
     if (t0 + n - polled > R) return fail(CAMELOT_EAGAIN, "completion ring full (poll first)");
-    for (uint32_t i = 0; i < n; ++i)
-        if (p->qring[(t0 + i) & mask].seq != t0 + i)
-            return fail(CAMELOT_EAGAIN, "query ring full");
+    const uint64_t D = p->opt.data_slots, dmask = D - 1;
+    if (n > D) return fail(CAMELOT_EINVAL, "n=%u exceeds data_slots=%llu", n, (unsigned long long)D);
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t t = t0 + i;
+        if (p->qring[t & mask].seq != t) return fail(CAMELOT_EAGAIN, "query ring full");
+        // the data row of ticket t last held ticket u = t - D (u < t0 since n <= D):
+        // stage 0 must have released u's descriptor (seq = u + R)
+        if (D < R && t >= D) {
+            const uint64_t u = t - D;
+            // tickets before the last trace's end were all done when it was armed
+            if (u >= p->data_floor && p->qring[u & mask].seq != u + R)
+                return fail(CAMELOT_EAGAIN, "query data ring full");
+        }
+    }
     const size_t row = p->hp.q_row;
     const int64_t now = host_now_ns();
     for (uint32_t i = 0; i < n; ++i) {
         const uint64_t t = t0 + i;
-        memcpy(p->qdata + (t & mask) * row, (const char*)queries + (size_t)i * row, row);
+        memcpy(p->qdata + (t & dmask) * row, (const char*)queries + (size_t)i * row, row);
         QDesc& d = p->qring[t & mask];
         d.t_arrival = arrival_ns ? arrival_ns[i] : now;
         d.stream_id = stream_id;
@@ -881,6 +898,7 @@ extern "C" camelot_status camelot_submit_trace(camelot_pipeline* p, uint32_t str
     }
     p->trace_active = true;
     p->trace_end = next;
+    p->data_floor = next;
     p->next_ticket.store(next, std::memory_order_release);
     if (first_query_id) *first_query_id = base;
     return check_and_run(p, true);

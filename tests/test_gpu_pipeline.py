@@ -151,6 +151,15 @@ def test_backpressure_eagain_then_drain(stages):
         cm.camelot_pipeline_destroy(p)
 
 
+def test_small_data_ring_wraps(stages):
+    # 64 pinned query rows behind 256 descriptors: submissions wait for stage 0
+    # to free data rows, results are unchanged
+    _, ref, _ = _run(stages, 0)
+    comps, logits, _ = _run(stages, 0, opts=pl.options(query_slots=256, data_slots=64), chunk=32)
+    assert [c.query_id for c in comps] == list(range(N_Q))
+    assert np.array_equal(logits, ref)
+
+
 def test_idle_exit_and_relaunch(stages):
     x, _ = cfg1_data(N_Q)
     o = pl.options(idle_exit_ns=20_000_000)
