@@ -2,13 +2,14 @@
 //
 // Each layer computes y[q][m] = act(sum_k W[m][k] x[q][k]) for a batch of at
 // most 32 queries.  The batch is small, so the operands are swapped: the
-// weights are the M = 128 operand (128 x 64 tiles streamed by TMA through a
-// shared-memory ring with the 128-byte swizzle) and the queries are the N = 32
-// operand (a K-chunk of all queries, staged with cp.async in the same swizzled
-// layout into a double buffer and reused by every weight tile of the chunk).
-// The CTA's warps specialise: one streams weight tiles, one stages query
-// chunks, one thread issues tcgen05.mma (M=128, N=32, K=16) into one of two
-// TMEM accumulators, four warps drain the other accumulator.  A unit is
+// weights are the M = 128 operand (128 x 64 tiles, stored pre-tiled and
+// pre-swizzled as contiguous 16 KB blocks and streamed by 1-D bulk copies
+// through a shared-memory ring) and the queries are the N = 32
+// operand (32 x 64 tiles staged with cp.async in the same swizzled layout, in
+// the same ring stage as the weight tile they multiply).  The CTA's warps
+// specialise: one streams weight tiles, one stages query tiles, one thread
+// issues tcgen05.mma (M=128, N=32, K=16) into one of two TMEM accumulators,
+// four warps drain the other accumulator.  A unit is
 // (K-chunk, 128-row tile); chunk partials are added in chunk order, so the
 // result is the same whatever the number of CTAs.
 #pragma once
@@ -21,32 +22,28 @@
 
 namespace camelot {
 
-constexpr int kGemmStages = 4;                   // weight-tile ring depth
+constexpr int kGemmStages = 5;                   // ring depth
+constexpr int kKbPerStage = 2;                   // k-blocks per stage: one 32 KB weight copy
 constexpr int kGemmN = 32;                       // queries per MMA (N)
-constexpr int kGemmMaxKC = 1024;                 // largest K-chunk (elements)
 constexpr uint32_t kATileBytes = 128 * 64 * 2;   // one 128 x 64 bf16 weight tile
-constexpr uint32_t kBTileBytes = kGemmN * 64 * 2;
-constexpr uint32_t kBChunkBytes = (kGemmMaxKC / 64) * kBTileBytes;   // 64 KB
+constexpr uint32_t kBTileBytes = kGemmN * 64 * 2;   // the matching 32 x 64 query tile
+constexpr uint32_t kStageBytes = kKbPerStage * (kATileBytes + kBTileBytes);   // 40 KB
 constexpr uint32_t kTmemCols = 64;               // two 32-column accumulators
 
 // Warp roles inside a CTA running tensor-core layers.
-constexpr int kWarpTma = 0;     // weight tiles, TMA
+constexpr int kWarpTma = 0;     // weight tiles, bulk copies
 constexpr int kWarpMma = 1;     // tcgen05.mma issue (one thread)
-constexpr int kWarpB = 2;       // query chunks, cp.async into the double buffer
+constexpr int kWarpB = 2;       // query tiles, cp.async
 constexpr int kWarpEpi0 = 4;    // warps 4..7 read the accumulators
 
 struct GemmSmem {
-    char* a_ring;          // kGemmStages x 16 KB weight tiles
-    char* b_buf;           // 2 x 64 KB query chunks
-    uint64_t* full;        // [kGemmStages] weight tile landed
-    uint64_t* empty;       // [kGemmStages] MMAs reading the tile are done
-    uint64_t* bfull;       // [2] query chunk staged (32 arrivals: warp kWarpB)
-    uint64_t* bempty;      // [2] MMAs reading the chunk are done
+    char* ring;            // kGemmStages x (2 weight tiles, 32 KB, then 2 query tiles, 8 KB)
+    uint64_t* full;        // [kGemmStages] both tiles landed (1 copy arrival + tx, 32 loader arrivals)
+    uint64_t* empty;       // [kGemmStages] MMAs reading the stage are done
     uint64_t* tfull;       // [2] accumulator complete
     uint64_t* tfree;       // [2] accumulator read out (4 arrivals: epilogue warps)
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
-    uint32_t* ring_it;     // weight tiles so far (all launches of this CTA)
-    uint32_t* b_it;        // query chunks staged so far
+    uint32_t* ring_it;     // stages filled so far (all launches of this CTA)
     uint32_t* acc_it;      // units finished so far
 };
 
@@ -54,19 +51,15 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     char* base = reinterpret_cast<char*>(
         (reinterpret_cast<uintptr_t>(smem) + 1023) & ~static_cast<uintptr_t>(1023));
     GemmSmem g;
-    g.a_ring = base;
-    g.b_buf = base + kGemmStages * kATileBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(g.b_buf + 2 * kBChunkBytes);
+    g.ring = base;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kGemmStages * kStageBytes);
     g.full = bars;
     g.empty = g.full + kGemmStages;
-    g.bfull = g.empty + kGemmStages;
-    g.bempty = g.bfull + 2;
-    g.tfull = g.bempty + 2;
+    g.tfull = g.empty + kGemmStages;
     g.tfree = g.tfull + 2;
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2);
     g.ring_it = g.tmem_slot + 1;
-    g.b_it = g.ring_it + 1;
-    g.acc_it = g.b_it + 1;
+    g.acc_it = g.ring_it + 1;
     return g;
 }
 
@@ -75,17 +68,14 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
     GemmSmem g = gemm_smem(smem);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGemmStages; ++s) {
-            mbar_init(&g.full[s], 1);
+            mbar_init(&g.full[s], 1 + 32);
             mbar_init(&g.empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&g.bfull[b], 32);
-            mbar_init(&g.bempty[b], 1);
             mbar_init(&g.tfull[b], 1);
             mbar_init(&g.tfree[b], 4);
         }
         *g.ring_it = 0;
-        *g.b_it = 0;
         *g.acc_it = 0;
         mbar_fence_init();
     }
@@ -132,9 +122,12 @@ __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float
 }
 
 // One layer.  Work units u = (chunk c, 128-row tile mt) in chunk-major order
-// (u = c * MT + mt); CTA r takes the contiguous units [r U / p, (r+1) U / p),
-// so consecutive units share their query chunk.  Every unit accumulates the
-// same K range in the same MMA order whichever CTA runs it.
+// (u = c * MT + mt); CTA r takes the contiguous units [r U / p, (r+1) U / p).
+// Every unit accumulates the same K range in the same MMA order whichever CTA
+// runs it.  Each ring stage carries two consecutive weight tiles (one 32 KB
+// bulk copy: the copy engine's cost is per operation, so larger copies stream
+// faster; kept in L2 with the evict-last policy) and the matching query tiles
+// (cp.async by the loader warp, 128-byte swizzle).
 static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
                                         float* Pbuf, const LayerOut& direct) {
     const GemmSmem g = gemm_smem(cx.smem);
@@ -143,84 +136,104 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     const int U = MT * L.C;
     const int u0 = (int)((long long)cx.rank * U / cx.nctas);
     const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
-    const uint32_t ring0 = *g.ring_it, b0 = *g.b_it, a0 = *g.acc_it;
+    const uint32_t ring0 = *g.ring_it, a0 = *g.acc_it;
     const uint32_t tmem = *g.tmem_slot;
     auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) / 64; };
+    auto stages_of = [&](int c) { return (chunk_kb(c) + kKbPerStage - 1) / kKbPerStage; };
 
     if (u0 < u1) {
         if (warp == kWarpTma && lane == 0) {
-            // weight tiles of every unit, in order, through the ring
+            // weight tiles of every unit, in order: tiles (mt, kb) and (mt, kb+1)
+            // are adjacent in memory, so a stage is one bulk copy
+            const uint64_t pol = l2_policy_evict_last();
+            const char* wt = reinterpret_cast<const char*>(L.w);
+            const int KB = L.K / 64;                     // weight tiles per 128-row block
             uint32_t gi = ring0;
             for (int u = u0; u < u1; ++u) {
                 const int c = u / MT, mt = u - c * MT;
                 const int nkb = chunk_kb(c);
-                for (int kb = 0; kb < nkb; ++kb, ++gi) {
+                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
+                    const int nk = min(kKbPerStage, nkb - kb);
                     const int s = gi % kGemmStages;
-                    if (gi >= ring0 + kGemmStages || gi >= (uint32_t)kGemmStages) {
-                        if (gi >= (uint32_t)kGemmStages &&
-                            !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
-                            goto done;
-                    }
-                    mbar_arrive_expect_tx(&g.full[s], kATileBytes);
-                    tma_load_2d(g.a_ring + s * kATileBytes, &L.tmap, &g.full[s], c * L.KC + kb * 64,
-                                mt * 128);
+                    if (gi >= (uint32_t)kGemmStages &&
+                        !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
+                        goto done;
+                    mbar_arrive_expect_tx(&g.full[s], nk * kATileBytes);
+                    bulk_load_hint(g.ring + s * kStageBytes,
+                                   wt + ((size_t)mt * KB + c * (L.KC / 64) + kb) * kATileBytes,
+                                   nk * kATileBytes, &g.full[s], pol);
                 }
             }
         } else if (warp == kWarpB) {
-            // query chunks: once per distinct chunk of the range, double-buffered
-            uint32_t h = b0;
-            for (int c = u0 / MT; c <= (u1 - 1) / MT; ++c, ++h) {
-                const int buf = h & 1;
-                if (h >= 2 && !mbar_wait_bounded(&g.bempty[buf], ((h >> 1) - 1) & 1, cx, 2)) break;
-                const int kc = chunk_kb(c) * 64;
-                char* dstb = g.b_buf + buf * kBChunkBytes;
-                const int per_row = kc / 8;                      // 16-byte pieces per row
-                for (int e = lane; e < kGemmN * per_row; e += 32) {
-                    const int r = e / per_row, pc = e - r * per_row;
-                    const int kb = pc >> 3, j = pc & 7;
-                    const char* src = x.row(r < n ? r : 0) + (size_t)(c * L.KC + 8 * pc) * 2;
-                    cp_async16_zfill(dstb + kb * kBTileBytes + r * 128 + ((j ^ (r & 7)) << 4), src,
-                                     r < n ? 16u : 0u);
+            // query tiles of every (unit, k-block): 32 rows x 128 bytes, 16-byte
+            // piece j of row r at r * 128 + ((j ^ (r & 7)) * 16).  One cp.async
+            // group per stage; kBLag groups stay in flight, and a stage is
+            // signalled full once its group has landed.
+            constexpr int kBLag = kGemmStages - 2;
+            uint32_t gi = ring0;
+            for (int u = u0; u < u1; ++u) {
+                const int c = u / MT;
+                const int nkb = chunk_kb(c);
+                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
+                    const int nk = min(kKbPerStage, nkb - kb);
+                    const int s = gi % kGemmStages;
+                    if (gi >= (uint32_t)kGemmStages &&
+                        !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 2))
+                        goto done;
+                    char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
+                    for (int t = 0; t < nk; ++t) {
+                        char* dst = dstb + t * kBTileBytes;
+                        const size_t k_off = (size_t)(c * L.KC + (kb + t) * 64) * 2;
+#pragma unroll
+                        for (int i = 0; i < (kGemmN * 8) / 32; ++i) {
+                            const int e = lane + 32 * i;
+                            const int r = e >> 3, j = e & 7;
+                            const char* src = x.row(r < n ? r : 0) + k_off + 16 * j;
+                            cp_async16_zfill(dst + r * 128 + ((j ^ (r & 7)) << 4), src, r < n ? 16u : 0u);
+                        }
+                    }
+                    cp_async_commit();
+                    if (gi >= ring0 + kBLag) {
+                        cp_async_wait<kBLag>();
+                        fence_proxy_async_smem();
+                        mbar_arrive(&g.full[(gi - kBLag) % kGemmStages]);
+                    }
                 }
-                cp_async_commit();
-                cp_async_wait<0>();
-                fence_proxy_async_smem();
-                mbar_arrive(&g.bfull[buf]);
             }
+            // the last kBLag (or fewer) stages
+            cp_async_wait<0>();
+            fence_proxy_async_smem();
+            const uint32_t gend = gi;
+            for (uint32_t g2 = (gend >= ring0 + kBLag ? gend - kBLag : ring0); g2 < gend; ++g2)
+                mbar_arrive(&g.full[g2 % kGemmStages]);
         } else if (warp == kWarpMma && lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(128, kGemmN);
-            uint32_t gi = ring0, h = b0, a = a0;
-            int cur_c = -1;
+            uint32_t gi = ring0, a = a0;
             for (int u = u0; u < u1; ++u, ++a) {
                 const int c = u / MT;
                 const int nkb = chunk_kb(c);
-                if (c != cur_c) {
-                    if (cur_c >= 0) { tc_commit(&g.bempty[h & 1]); ++h; }
-                    cur_c = c;
-                    if (!mbar_wait_bounded(&g.bfull[h & 1], (h >> 1) & 1, cx, 3)) goto done;
-                }
                 const int acc = a & 1;
-                if (a >= a0 + 2 || a >= 2) {
-                    if (a >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((a >> 1) - 1) & 1, cx, 4)) goto done;
-                }
+                if (a >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((a >> 1) - 1) & 1, cx, 4)) goto done;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + acc * kGemmN;
-                const uint32_t b_base = smem_u32(g.b_buf + (h & 1) * kBChunkBytes);
-                for (int kb = 0; kb < nkb; ++kb, ++gi) {
+                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
+                    const int nk = min(kKbPerStage, nkb - kb);
                     const int s = gi % kGemmStages;
                     if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) goto done;
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(g.a_ring + s * kATileBytes);
-                    const uint32_t b_addr = b_base + kb * kBTileBytes;
+                    const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
+                    for (int t = 0; t < nk; ++t) {
+                        const uint32_t a_addr = sbase + t * kATileBytes;
+                        const uint32_t b_addr = sbase + kKbPerStage * kATileBytes + t * kBTileBytes;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tc_mma_f16(d_tmem, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k),
-                                   idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        for (int k = 0; k < 4; ++k)
+                            tc_mma_f16(d_tmem, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k),
+                                       idesc, (kb + t > 0 || k > 0) ? 1u : 0u);
+                    }
                     tc_commit(&g.empty[s]);
                 }
                 tc_commit(&g.tfull[acc]);
             }
-            if (cur_c >= 0) tc_commit(&g.bempty[h & 1]);
         } else if (warp >= kWarpEpi0) {
             // accumulator rows 32 (warp % 4) .. +31, all 32 query columns
             const int sub = warp & 3;
@@ -241,11 +254,10 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 if (m < L.N) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int q = j;
-                        if (q < n) {
+                        if (j < n) {
                             const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                            if (L.C == 1) store_out(direct, q, m, apply_act(v, L.act));
-                            else __stcg(Pbuf + ((size_t)c * n + q) * L.Npad + m, v);
+                            if (L.C == 1) store_out(direct, j, m, apply_act(v, L.act));
+                            else __stcg(Pbuf + ((size_t)c * n + j) * L.Npad + m, v);
                         }
                     }
                 }
@@ -255,35 +267,57 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
 done:
     __syncthreads();
     if (threadIdx.x == 0 && u0 < u1) {
-        uint32_t tiles = 0;
-        for (int u = u0; u < u1; ++u) tiles += chunk_kb(u / MT);
-        *g.ring_it = ring0 + tiles;
-        *g.b_it = b0 + (uint32_t)((u1 - 1) / MT - u0 / MT + 1);
+        uint32_t stages = 0;
+        for (int u = u0; u < u1; ++u) stages += stages_of(u / MT);
+        *g.ring_it = ring0 + stages;
         *g.acc_it = a0 + (uint32_t)(u1 - u0);
     }
     __syncthreads();
     return !has_error(cx.ctl);
 }
 
-// out[q][m] = act(sum over chunks, in chunk order) for m < N.
+// out[q][m] = act(sum over chunks, in chunk order) for m < N.  Each thread
+// owns two groups of four consecutive outputs and keeps 2 x 8 float4 loads in
+// flight; the four lanes of a float4 are summed independently, each in chunk
+// order, so the result equals the scalar chunk-order sum.
 static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int n, const float* Pbuf,
                                    const LayerOut& o) {
-    const int total = n * L.N;
-    const size_t cstride = (size_t)n * L.Npad;
-    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
-        const int q = e / L.N, m = e - q * L.N;
-        const float* p = Pbuf + (size_t)q * L.Npad + m;
-        float s = 0.f;
-        int c = 0;
-        for (; c + 8 <= L.C; c += 8) {
-            float v[8];
+    const int m4n = L.Npad / 4;                   // float4 groups per query row
+    const int total = n * m4n;
+    const size_t cstride4 = (size_t)n * m4n;      // float4 stride between chunks
+    const float4* P4 = reinterpret_cast<const float4*>(Pbuf);
+    const int nthreads = cx.nctas * kThreads;
+    for (int base = cx.rank * kThreads + threadIdx.x; base < total; base += 2 * nthreads) {
+        const int e0 = base, e1 = base + nthreads;
+        const bool has1 = e1 < total;
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+        for (int c = 0; c < L.C; c += 8) {
+            float4 v0[8], v1[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (size_t)(c + u) * cstride);
+            for (int u = 0; u < 8; ++u) {
+                if (c + u < L.C) {
+                    v0[u] = __ldcg(P4 + (size_t)(c + u) * cstride4 + e0);
+                    if (has1) v1[u] = __ldcg(P4 + (size_t)(c + u) * cstride4 + e1);
+                }
+            }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u];
+            for (int u = 0; u < 8; ++u) {
+                if (c + u < L.C) {
+                    s0.x += v0[u].x; s0.y += v0[u].y; s0.z += v0[u].z; s0.w += v0[u].w;
+                    if (has1) { s1.x += v1[u].x; s1.y += v1[u].y; s1.z += v1[u].z; s1.w += v1[u].w; }
+                }
+            }
         }
-        for (; c < L.C; ++c) s += __ldcg(p + (size_t)c * cstride);
-        store_out(o, q, m, apply_act(s, L.act));
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has1) break;
+            const int e = h ? e1 : e0;
+            const float4 v = h ? s1 : s0;
+            const int q = e / m4n, m = (e - q * m4n) * 4;
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (m + i < L.N) store_out(o, q, m + i, apply_act(vv[i], L.act));
+        }
     }
 }
 

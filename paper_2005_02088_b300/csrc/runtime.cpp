@@ -1,6 +1,5 @@
 // Host runtime of libcamelot: stage preparation, pipeline rings and lifecycle,
 // submission, completion polling, trace replay and the host-staged relay.
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <time.h>
@@ -97,40 +96,6 @@ static void stage_free(camelot_stage* st) {
     for (void* p : st->allocs) cudaFree(p);
     if (st->d_sp) cudaFree(st->d_sp);
     delete st;
-}
-
-// cuTensorMapEncodeTiled, looked up through the runtime (no link-time driver
-// dependency, so the library loads on machines without a GPU).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                  CUtensorMapFloatOOBfill);
-static EncodeTiledFn encode_tiled() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    });
-    return fn;
-}
-
-// TMA map of a row-major bf16 matrix [rows][K]: boxes of 128 rows x 64 K
-// (128 bytes, the swizzle width) with the 128-byte swizzle.
-static bool make_weight_map(CUtensorMap* m, const void* base, int rows, int K) {
-    EncodeTiledFn fn = encode_tiled();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {64, 128};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // K-chunk of a tensor-core layer: 1024 for long K, else 256 (multiples of 64).
@@ -288,18 +253,31 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                 Lp.Npad = (N + 127) / 128 * 128;
                 Lp.KC = choose_kc_gemm(K);
                 Lp.C = (K + Lp.KC - 1) / Lp.KC;
-                std::vector<__nv_bfloat16> w((size_t)Lp.Npad * K, __float2bfloat16_rn(0.f));
-                if (cudaMemcpy(w.data(), d->weights[l], (size_t)N * K * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
+                std::vector<uint16_t> w((size_t)N * K);
+                if (cudaMemcpy(w.data(), d->weights[l], w.size() * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
                     return bail(fail(CAMELOT_EINVAL, "weights[%d] is not readable device memory", l));
+                // tile (mt, kb): 128 rows x 64 columns, 16-byte piece j of row r at
+                // r * 128 + ((j ^ (r & 7)) * 16) -- the 128-byte-swizzle layout
+                const int KB = K / 64;
+                std::vector<uint16_t> t((size_t)Lp.Npad * K, 0);
+                for (int mt = 0; mt < Lp.Npad / 128; ++mt)
+                    for (int kb = 0; kb < KB; ++kb) {
+                        uint16_t* tile = t.data() + ((size_t)mt * KB + kb) * (128 * 64);
+                        for (int r = 0; r < 128; ++r) {
+                            const int row = mt * 128 + r;
+                            if (row >= N) continue;
+                            for (int j = 0; j < 8; ++j)
+                                memcpy(tile + r * 64 + ((j ^ (r & 7)) * 8),
+                                       w.data() + (size_t)row * K + kb * 64 + 8 * j, 16);
+                        }
+                    }
                 void* dp = nullptr;
-                if (cudaMalloc(&dp, w.size() * 2) != cudaSuccess)
+                if (cudaMalloc(&dp, t.size() * 2) != cudaSuccess)
                     return bail(fail(CAMELOT_ENOMEM, "weight copy allocation failed"));
                 st->allocs.push_back(dp);
-                if (cudaMemcpy(dp, w.data(), w.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+                if (cudaMemcpy(dp, t.data(), t.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
                     return bail(fail(CAMELOT_ECUDA, "weight upload failed"));
                 Lp.w = (const float*)dp;
-                if (!make_weight_map(&Lp.tmap, dp, Lp.Npad, K))
-                    return bail(fail(CAMELOT_ECUDA, "TMA map of weights[%d] could not be encoded", l));
             }
             sp.scratch_bytes = layout_scratch(sp, d->max_batch);
             break;

@@ -1,8 +1,6 @@
 // Plain-data description of a prepared stage, shared by the host runtime and
 // the device code (passed by value in kernel parameters).
 #pragma once
-#include <cuda.h>   // CUtensorMap (type only; the library does not link the driver)
-
 #include <cstddef>
 #include <cstdint>
 
@@ -17,7 +15,7 @@ constexpr int kQGroup = 16;            // queries per register tile of the FP32 
 constexpr int kNBlock = 128;           // neurons per warp task (4 per lane)
 constexpr int kMaxKC = 128;            // largest K-chunk of a warp task
 constexpr int kWRing = 8;              // weight quads in flight per warp (cp.async ring)
-constexpr size_t kSmemBytes = 200 * 1024;  // dynamic shared memory per CTA: > half an SM,
+constexpr size_t kSmemBytes = 216 * 1024;  // dynamic shared memory per CTA: > half an SM,
                                            // so exactly one CTA fits on an SM
 
 enum StageKind : int32_t { KIND_NORMALIZE_U8 = 1, KIND_NORM_POOL2_BF16 = 2, KIND_MLP_FP32 = 3,
@@ -31,12 +29,13 @@ enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
 //    whose partial sums are reduced over chunks in chunk order.
 //  - "head" layer (last layer of a final stage with N <= 32): weights row-major
 //    [N][K]; one warp computes a whole query.
-//  - tensor-core layers (GEMM_BF16): weights bf16 [Npad][K] (rows >= N zero),
-//    Npad = N rounded up to 128, read through the 2-D TMA map `tmap` (boxes of
-//    128 rows x 64 K with the 128-byte swizzle); K is cut into chunks of KC
-//    (a multiple of 64) whose fp32 partials are reduced in chunk order.
+//  - tensor-core layers (GEMM_BF16): weights bf16 in 128 x 64 tiles, tile
+//    (mt, kb) a contiguous 16 KB block at ((mt * K/64) + kb) * 16 KB holding rows
+//    128 mt.. and columns 64 kb.. in the 128-byte-swizzle layout (row r's
+//    16-byte piece j at r * 128 + (j ^ (r % 8)) * 16); rows >= N are zero and
+//    Npad = N rounded up to 128.  K is cut into chunks of KC (a multiple of 64)
+//    whose fp32 partials are reduced in chunk order.
 struct LayerParams {
-    CUtensorMap tmap;   // tensor-core layers only
     const float* w;     // device, kernel layout (see above)
     int32_t K, N, Npad;
     int32_t KC, C;      // K-chunk (multiple of 4) and number of chunks

@@ -76,7 +76,7 @@ static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, 
             const uint64_t e = base + u * stride;
             if (e < total) {
                 const uint64_t q = e / chunks, c = e - q * chunks;
-                v[u] = __ldcg(reinterpret_cast<const uint4*>(in.row(q)) + c);
+                v[u] = __ldcs(reinterpret_cast<const uint4*>(in.row(q)) + c);   // read once
             }
         }
 #pragma unroll
@@ -115,7 +115,7 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
         const int q = u / Ho, ho = u - q * Ho;
         const uint4* src = reinterpret_cast<const uint4*>(in.row(q) + (size_t)2 * ho * W * C);
         uint4* dst = reinterpret_cast<uint4*>(sm);
-        for (int i = lane; i < pair_bytes / 16; i += 32) dst[i] = __ldcg(src + i);
+        for (int i = lane; i < pair_bytes / 16; i += 32) dst[i] = __ldcs(src + i);   // read once: evict first
         __syncwarp();
         const uint8_t* r0 = sm;
         const uint8_t* r1 = sm + W * C;

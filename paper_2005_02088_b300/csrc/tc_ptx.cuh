@@ -1,5 +1,5 @@
-// Inline-PTX wrappers for the Blackwell tensor-core path: mbarriers, TMA tile
-// loads, tcgen05 (TMEM allocation, MMA, commit, loads) and the shared-memory
+// Inline-PTX wrappers for the Blackwell tensor-core path: mbarriers, bulk
+// (TMA-engine) copies and L2 prefetches, tcgen05 (TMEM allocation, MMA, commit, loads) and the shared-memory
 // matrix / instruction descriptors of tcgen05.mma.  Written from the PTX ISA's
 // descriptions of these instructions.
 #pragma once
@@ -35,15 +35,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// ---- TMA ----------------------------------------------------------------------
-// 2-D tile load global -> shared, completion counted in bytes on `bar`.
-// x (innermost, elements) must start on a 16-byte boundary.
-__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_t* bar, int x, int y) {
+// ---- bulk copies (TMA engine) -------------------------------------------------
+// 1-D bulk copy global -> shared (contiguous, 16-byte aligned, size a multiple
+// of 16), completion counted in bytes on `bar`, with an L2 cache policy.
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
+}
+// Bring a contiguous range into L2 ahead of its load.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes, uint64_t policy) {
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes),
+                 "l"(policy)
+                 : "memory");
+}
+// L2 policy: keep the lines (they are reused by every instance and batch).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 // ---- tcgen05 ---------------------------------------------------------------------
