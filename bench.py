@@ -536,6 +536,92 @@ def run_gpu(args, rank: int, world: int, dist):
     return 0
 
 
+def cfg1_stage_runners(max_batch=64):
+    """The two cfg1 stages (normalize; MLP 12288-512-256-10 + argmax) with
+    device buffers of max_batch rows, for the predictor's profiling runs."""
+    import torch
+    import synth
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl, predictor as pr
+    x, ws = synth.cfg1_inputs(0, max_batch)
+    s1 = pl.stage_normalize(64, 64, 3, max_batch)
+    wd = [torch.from_numpy(w).cuda() for w in ws]
+    s2 = pl.stage_dense(cm.STAGE_MLP_FP32, wd, [cm.ACT_RELU, cm.ACT_RELU, cm.ACT_NONE], top_k=1,
+                        max_batch=max_batch)
+    xin = torch.from_numpy(np.ascontiguousarray(x.reshape(max_batch, -1))).cuda()
+    r1 = pr.StageRunner(s1, xin, max_batch)
+    r1.time_ms(max_batch, 8, 1)
+    torch.cuda.synchronize()
+    r2 = pr.StageRunner(s2, r1.out, max_batch, top_k=1)
+    costs = {1: pr.StageCost(1, 2 * 12288, 0.0, 12288 + 49152),
+             2: pr.dense_cost(2, [12288, 512, 256, 10], 12288 * 4, 8)}
+    return (s1, s2), {1: r1, 2: r2}, costs, wd
+
+
+def oracle_training_rate(X, y, budget_s=10.0):
+    """FP64 oracle minibatch steps (gradient + Adam, 256 samples) per second
+    on one host core: the CPU baseline of the predictor's GPU training."""
+    import oracle
+    g = np.random.default_rng(0)
+    th = np.ascontiguousarray(g.standard_normal(oracle.pred_nparams()) * 0.1)
+    m, v = np.zeros_like(th), np.zeros_like(th)
+    Xs = (X - X.mean(0)) / np.where(X.std(0) > 0, X.std(0), 1.0)
+    t0, steps = time.time(), 0
+    while time.time() - t0 < budget_s:
+        i = g.integers(0, len(y), 256)
+        _, grad = oracle.pred_grad(th, Xs[i], y[i])
+        oracle.adam_step(th, grad, m, v, steps + 1)
+        steps += 1
+    return steps / (time.time() - t0)
+
+
+def run_predictor(args):
+    """The learned latency predictor, end to end: profiling samples of the
+    cfg1 stages under random SM quotas, batch sizes and a 1 GB FP32-copy
+    co-runner, GPU training, held-out MAPE, and allocation against brute force."""
+    import torch
+    from paper_2005_02088_b300 import camelot as cm, predictor as prm
+    stages, runners, costs, _ = cfg1_stage_runners()
+    try:
+        with ClockSampler(0) as clk:
+            r = prm.study(
+                runners, costs, n_samples=args.pred_samples, runs=args.pred_runs,
+                bw_gbs=_peaks().get("hbm_gbs", 6400.0),
+                log=lambda m: print(m, file=sys.stderr, flush=True))
+        torch.cuda.synchronize()
+    finally:
+        for s in stages:
+            cm.camelot_stage_release(s)
+    pred = r.pop("_predictor")
+    data, solo = r.pop("_data"), r.pop("_solo")
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    pred.save(os.path.join(ROOT, "gpurun_out", "predictor_cfg1.npz"))
+    np.savez(os.path.join(ROOT, "gpurun_out", "predictor_samples.npz"), solo_p99_us=solo,
+             **{k: np.asarray(v) for k, v in data.items()})
+    pred.close()
+    X = prm.feature_rows(costs, data["stage"], data["batch"], data["sms"], data["corunner_sms"],
+                         data["corunner_gbs"]).astype(np.float64)
+    cpu_rate = oracle_training_rate(X, np.log(data["p99_us"]))
+    line = {
+        "metric": "latency-predictor MAPE vs measured p99 on held-out profiling samples (cfg1 stages, "
+                  "co-runner contention); predictor-driven Eq. 1 allocation vs brute-force profiled search",
+        "value": r["mape"]["all"], "unit": "fraction (mean |pred - p99| / p99)", "higher_is_better": False,
+        "n_gpus": 1, "steps": r["train"]["steps"], "warmup": 0, "ms_per_step": 1e3 / r["train"]["steps_per_s"],
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": (f"{args.pred_samples} profiling samples of the 2 cfg1 stages, B uniform 1..64, "
+                                "SM quota uniform 8..144 in 8s, co-runner (1 GB FP32 copy) absent 25% or on a "
+                                f"random disjoint 8-SM multiple; label p99 of {args.pred_runs} launches; "
+                                "MLP 12-64-64-1 FP32, 70/30 split, Adam lr 3e-3 -> 3e-4, minibatch 256")},
+        "predictor": r,
+        "cpu_baseline": {"value": cpu_rate, "unit": "training steps/s (minibatch 256, gradient + Adam)",
+                         "cores": 1, "kind": "oracle", "sample": "10 s of FP64 oracle steps on this data"},
+        "gpu_training_steps_per_s": r["train"]["steps_per_s"],
+        "gpu_launches": 2 * r["train"]["steps"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Small self-contained case for ncu: two saturated 2,000-query launches."""
     wl = Workload(args.workload, 0, n_rows=2000)
@@ -558,6 +644,10 @@ def main():
     ap.add_argument("--impl", default="camelot", choices=["camelot", "reference"])
     ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--predictor", action="store_true",
+                    help="run the latency-predictor study (profiling, GPU training, allocation) instead")
+    ap.add_argument("--pred-samples", type=int, default=20000)
+    ap.add_argument("--pred-runs", type=int, default=100)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -565,6 +655,8 @@ def main():
         return run_reference(args, rank)
     if args.profile_case:
         return run_profile_case(args)
+    if args.predictor:
+        return run_predictor(args)
     dist = None
     if world > 1:
         import torch

@@ -161,6 +161,89 @@ camelot_status camelot_stage_launch_noalloc(const camelot_stage* st, int n_ctas,
                                             uint32_t n, void* out, int32_t* out_idx,
                                             float* out_val, float* out_logits, void* stream);
 
+/* Profiling of one stage (Sec. 7.1: the allocator's inputs are measured by
+ * running each microservice alone under a given SM percentage and batch):
+ * issue `runs` back-to-back camelot_stage_launch calls with the same arguments
+ * on `stream`, with a CUDA event between consecutive launches, wait for them,
+ * and write each launch's event-to-event duration in milliseconds to ms_out
+ * (host, [runs]).  runs in 1..65536.  Errors: those of camelot_stage_launch,
+ * ECUDA. */
+camelot_status camelot_stage_time(const camelot_stage* st, int n_ctas, const void* in, uint32_t n,
+                                  void* out, int32_t* out_idx, float* out_val, float* out_logits,
+                                  void* scratch, size_t scratch_bytes, void* stream, uint32_t runs,
+                                  float* ms_out);
+
+/* Bandwidth-hog co-runner for profiling under memory contention (the
+ * co-location interference of Sec. 4.2 and the bandwidth term of Eq. 1):
+ * a kernel of n_ctas CTAs, one per SM (each reserves 120 KB of shared memory,
+ * so no stage CTA can share its SM), that streams `bytes` (rounded down to a
+ * multiple of 16) from src to dst (device, 16-byte aligned, not overlapping)
+ * pass after pass until camelot_corunner_stop, or until max_ns nanoseconds
+ * have passed (its own deadline, so it always ends).  Returns once every CTA is
+ * resident (ETIMEDOUT, with the kernel stopped, if that takes over 5 s), so a
+ * stage launched afterwards gets the other SMs.  n_ctas in 1..SM count, at most
+ * 256.  The caller keeps src and dst alive until stop returns. */
+typedef struct camelot_corunner camelot_corunner;
+camelot_status camelot_corunner_start(const void* src, void* dst, size_t bytes, int n_ctas,
+                                      int64_t max_ns, camelot_corunner** out);
+/* Stop the co-runner, wait for it, free it, and report (nullable) the bytes it
+ * moved (read + written, full passes) per second of its run, in GB/s.  Returns
+ * ETIMEDOUT if it had already stopped at its own deadline (c is freed either
+ * way). */
+camelot_status camelot_corunner_stop(camelot_corunner* c, double* gbytes_per_s);
+
+/* ------------------------------------------------------- latency predictor */
+/* A learned stand-in for the per-microservice performance models of Sec. 7.1
+ * (which are decision trees there): an MLP 12 -> 64 -> 64 -> 1 in FP32 with
+ * ReLU hidden layers and a linear output, h1 = relu(W1 x + b1), h2 = relu(W2 h1
+ * + b2), y = W3 h2 + b3, where x is the feature vector z-scored with the stored
+ * mean and inverse standard deviation.  Parameters are one flat FP32 vector of
+ * CAMELOT_PRED_PARAMS values in the order W1 [64x12 row-major], b1 [64], W2
+ * [64x64], b2 [64], W3 [64], b3 [1].  Training minimises the mean squared error
+ * (1/n) sum_q (y_q - t_q)^2 with Adam (beta1 0.9, beta2 0.999, eps 1e-8).  All
+ * computation runs in the library's kernels; forward, grad and train_step are
+ * asynchronous on `stream`, and calls on one predictor must be ordered on one
+ * stream (they share its device scratch). */
+#define CAMELOT_PRED_FEATURES 12
+#define CAMELOT_PRED_PARAMS 5057
+typedef struct camelot_predictor camelot_predictor;
+
+/* Allocate a predictor on the current device with parameters init_params
+ * (host, CAMELOT_PRED_PARAMS floats), zero Adam moments, identity feature
+ * scaling (mean 0, inv_std 1).  Holds ~71 MB of device scratch for minibatches
+ * of up to 65536 samples.  Errors: EINVAL, ENOMEM, ECUDA. */
+camelot_status camelot_predictor_create(const float* init_params, camelot_predictor** out);
+/* Replace the parameters (host) and reset the Adam moments and step count.
+ * Synchronous. */
+camelot_status camelot_predictor_set_params(camelot_predictor* p, const float* params);
+/* Copy the parameters to host memory (CAMELOT_PRED_PARAMS floats).  The caller
+ * first synchronises the stream its training ran on. */
+camelot_status camelot_predictor_get_params(camelot_predictor* p, float* out);
+/* Feature scaling applied by later launches: x_k = (raw_k - mean[k]) *
+ * inv_std[k] (host arrays of CAMELOT_PRED_FEATURES floats). */
+camelot_status camelot_predictor_set_norm(camelot_predictor* p, const float* mean, const float* inv_std);
+/* y[q] = network(X[q]) for q < n.  X: device [n][12] row-major raw features;
+ * y: device [n].  Errors: EINVAL (null pointer, n = 0), ECUDA. */
+camelot_status camelot_predictor_forward(camelot_predictor* p, const float* X, uint32_t n, float* y,
+                                         void* stream);
+/* Gradient of the mean squared error over a minibatch of n samples (1..65536)
+ * with respect to every parameter: sample q is row idx[q] of X and t (device
+ * uint32 [n]; NULL = rows 0..n-1).  X: device [rows][12]; t: device [rows]
+ * targets; grad: device [CAMELOT_PRED_PARAMS]; loss (device float, nullable)
+ * receives the minibatch loss.  Each gradient is summed over the samples in
+ * minibatch order, so the result is deterministic.  Errors: EINVAL, ECUDA. */
+camelot_status camelot_predictor_grad(camelot_predictor* p, const float* X, const float* t,
+                                      const uint32_t* idx, uint32_t n, float* grad, float* loss,
+                                      void* stream);
+/* One Adam step (step count + 1, bias corrections 1 - beta^step) on the
+ * gradient camelot_predictor_grad would give for the same arguments, with
+ * learning rate lr > 0.  loss (device, nullable) receives the minibatch loss
+ * before the step. */
+camelot_status camelot_predictor_train_step(camelot_predictor* p, const float* X, const float* t,
+                                            const uint32_t* idx, uint32_t n, float lr, float* loss,
+                                            void* stream);
+camelot_status camelot_predictor_destroy(camelot_predictor* p);
+
 /* ----------------------------------------------------------- pipelines */
 typedef enum {
     CAMELOT_HANDOFF_GLOBAL = 0,      /* pointer + flag in device memory, no copy (Sec. 6.2) */

@@ -13,6 +13,7 @@ import os
 from . import build as _build
 
 MAX_LAYERS, MAX_STAGES, MAX_TOPK = 4, 8, 5
+PRED_FEATURES, PRED_PARAMS = 12, 5057
 
 OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, ECUDA, ESTATE, EINFEASIBLE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EAGAIN", "ETIMEDOUT", "ECUDA", "ESTATE", "EINFEASIBLE"]
@@ -87,6 +88,18 @@ _SIGS = {
     "camelot_stage_info": (C.c_int, [P, P, P, C.c_uint32, P]),
     "camelot_stage_launch": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P]),
     "camelot_stage_launch_noalloc": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P]),
+    "camelot_stage_time": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P,
+                                     C.c_uint32, P]),
+    "camelot_corunner_start": (C.c_int, [P, P, C.c_size_t, C.c_int, C.c_int64, P]),
+    "camelot_corunner_stop": (C.c_int, [P, P]),
+    "camelot_predictor_create": (C.c_int, [P, P]),
+    "camelot_predictor_set_params": (C.c_int, [P, P]),
+    "camelot_predictor_get_params": (C.c_int, [P, P]),
+    "camelot_predictor_set_norm": (C.c_int, [P, P, P]),
+    "camelot_predictor_forward": (C.c_int, [P, P, C.c_uint32, P, P]),
+    "camelot_predictor_grad": (C.c_int, [P, P, P, P, C.c_uint32, P, P, P]),
+    "camelot_predictor_train_step": (C.c_int, [P, P, P, P, C.c_uint32, C.c_float, P, P]),
+    "camelot_predictor_destroy": (C.c_int, [P]),
     "camelot_options_default": (None, [P]),
     "camelot_pipeline_create": (C.c_int, [P, C.c_int, P, C.c_int, P, P]),
     "camelot_submit": (C.c_int, [P, C.c_uint32, P, C.c_uint32, P, P]),
@@ -178,6 +191,81 @@ def camelot_stage_launch_noalloc(st: int, n_ctas: int, inp, n: int, out=None, ou
     """Stage launch whose scratch is the library's static device buffer."""
     _check(load().camelot_stage_launch_noalloc(st, n_ctas, _ptr(inp), n, _ptr(out), _ptr(out_idx),
                                                _ptr(out_val), _ptr(out_logits), _ptr(stream)))
+
+
+def camelot_stage_time(st: int, n_ctas: int, inp, n: int, out=None, out_idx=None, out_val=None,
+                       out_logits=None, scratch=None, scratch_bytes: int = 0, stream=None,
+                       runs: int = 1):
+    """Per-launch durations (ms, numpy float32 [runs]) of ``runs`` back-to-back launches."""
+    import numpy as np
+    ms = np.zeros(runs, np.float32)
+    _check(load().camelot_stage_time(st, n_ctas, _ptr(inp), n, _ptr(out), _ptr(out_idx),
+                                     _ptr(out_val), _ptr(out_logits), _ptr(scratch), scratch_bytes,
+                                     _ptr(stream), runs, ms.ctypes.data))
+    return ms
+
+
+def camelot_corunner_start(src, dst, nbytes: int, n_ctas: int, max_ns: int = 120_000_000_000) -> int:
+    h = C.c_void_p()
+    _check(load().camelot_corunner_start(_ptr(src), _ptr(dst), nbytes, n_ctas, max_ns, C.byref(h)))
+    return h.value
+
+
+def camelot_corunner_stop(c: int) -> float:
+    """Stops the co-runner; returns the GB/s it streamed (read + write)."""
+    g = C.c_double()
+    _check(load().camelot_corunner_stop(c, C.byref(g)))
+    return g.value
+
+
+def _f32_host(a, n):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def camelot_predictor_create(init_params) -> int:
+    a = _f32_host(init_params, PRED_PARAMS)
+    h = C.c_void_p()
+    _check(load().camelot_predictor_create(a.ctypes.data, C.byref(h)))
+    return h.value
+
+
+def camelot_predictor_set_params(p: int, params) -> None:
+    a = _f32_host(params, PRED_PARAMS)
+    _check(load().camelot_predictor_set_params(p, a.ctypes.data))
+
+
+def camelot_predictor_get_params(p: int):
+    import numpy as np
+    out = np.empty(PRED_PARAMS, np.float32)
+    _check(load().camelot_predictor_get_params(p, out.ctypes.data))
+    return out
+
+
+def camelot_predictor_set_norm(p: int, mean, inv_std) -> None:
+    m, s = _f32_host(mean, PRED_FEATURES), _f32_host(inv_std, PRED_FEATURES)
+    _check(load().camelot_predictor_set_norm(p, m.ctypes.data, s.ctypes.data))
+
+
+def camelot_predictor_forward(p: int, X, n: int, y, stream=None) -> None:
+    _check(load().camelot_predictor_forward(p, _ptr(X), n, _ptr(y), _ptr(stream)))
+
+
+def camelot_predictor_grad(p: int, X, t, idx, n: int, grad, loss=None, stream=None) -> None:
+    _check(load().camelot_predictor_grad(p, _ptr(X), _ptr(t), _ptr(idx), n, _ptr(grad), _ptr(loss),
+                                         _ptr(stream)))
+
+
+def camelot_predictor_train_step(p: int, X, t, idx, n: int, lr: float, loss=None, stream=None) -> None:
+    _check(load().camelot_predictor_train_step(p, _ptr(X), _ptr(t), _ptr(idx), n, lr, _ptr(loss),
+                                               _ptr(stream)))
+
+
+def camelot_predictor_destroy(p: int) -> None:
+    _check(load().camelot_predictor_destroy(p))
 
 
 def camelot_options_default() -> Options:

@@ -1,0 +1,249 @@
+"""GPU parity of the latency-predictor kernels (forward, backward, Adam; FP32)
+against the FP64 oracle, and checks of the profiling harness (stage timing,
+bandwidth-hog co-runner).
+
+Tolerances.  Forward: every layer is an FP32 fused multiply-add chain of at
+most 65 terms, so |y - y64| <= (13 + 65 + 65) 2^-24 |y|_abs with |y|_abs the
+network evaluated on |theta| and |x|; the test allows 2e-5 |y|_abs.
+Gradient: within 1e-4 of the FP64 gradient's norm.  Adam: the oracle's FP64
+step applied to the GPU's own gradient agrees to 1e-6 relative."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _theta(seed=0, scale=0.3):
+    return (np.random.default_rng(seed).standard_normal(5057) * scale).astype(np.float32)
+
+
+def _data(seed, n):
+    g = np.random.default_rng(seed)
+    return g.standard_normal((n, 12)).astype(np.float32), g.standard_normal(n).astype(np.float32)
+
+
+def test_forward_matches_oracle(orc):
+    from paper_2005_02088_b300 import camelot as cm
+    th = _theta(1)
+    X, _ = _data(2, 1000)
+    h = cm.camelot_predictor_create(th)
+    try:
+        y = torch.empty(1000, device="cuda")
+        cm.camelot_predictor_forward(h, torch.from_numpy(X).cuda(), 1000, y)
+        got = y.cpu().numpy().astype(np.float64)
+    finally:
+        cm.camelot_predictor_destroy(h)
+    ref = orc.pred_forward(th, X)
+    yabs = orc.pred_forward(np.abs(th.astype(np.float64)), np.abs(X.astype(np.float64)))
+    assert np.all(np.abs(got - ref) <= 2e-5 * yabs + 1e-30)
+
+
+def test_forward_applies_feature_scaling(orc):
+    from paper_2005_02088_b300 import camelot as cm
+    th = _theta(3)
+    X, _ = _data(4, 257)
+    X = X * 50 + 7
+    mean = np.linspace(-3, 9, 12).astype(np.float32)
+    inv = np.linspace(0.01, 0.5, 12).astype(np.float32)
+    h = cm.camelot_predictor_create(th)
+    try:
+        cm.camelot_predictor_set_norm(h, mean, inv)
+        y = torch.empty(257, device="cuda")
+        cm.camelot_predictor_forward(h, torch.from_numpy(X).cuda(), 257, y)
+        got = y.cpu().numpy().astype(np.float64)
+    finally:
+        cm.camelot_predictor_destroy(h)
+    # the same FP32 scaling, then the FP64 network
+    Xs = (X - mean) * inv
+    ref = orc.pred_forward(th, Xs)
+    yabs = orc.pred_forward(np.abs(th.astype(np.float64)), np.abs(Xs.astype(np.float64)))
+    assert np.all(np.abs(got - ref) <= 2e-5 * yabs + 1e-30)
+
+
+@pytest.mark.parametrize("n", [1, 255, 256, 1000])
+def test_gradient_matches_oracle(orc, n):
+    from paper_2005_02088_b300 import camelot as cm
+    th = _theta(5, 0.2)
+    X, t = _data(6 + n, n)
+    h = cm.camelot_predictor_create(th)
+    try:
+        g = torch.empty(5057, device="cuda")
+        loss = torch.empty(1, device="cuda")
+        cm.camelot_predictor_grad(h, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), None, n, g, loss)
+        got, lgot = g.cpu().numpy().astype(np.float64), float(loss)
+    finally:
+        cm.camelot_predictor_destroy(h)
+    lref, gref = orc.pred_grad(th, X, t)
+    assert np.linalg.norm(got - gref) <= 1e-4 * np.linalg.norm(gref)
+    assert abs(lgot - lref) <= 1e-5 * lref
+
+
+def test_gradient_deterministic_and_index_gather():
+    from paper_2005_02088_b300 import camelot as cm
+    th = _theta(7)
+    X, t = _data(8, 3000)
+    perm = np.random.default_rng(9).permutation(3000)[:700].astype(np.int32)
+    h = cm.camelot_predictor_create(th)
+    try:
+        Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+        outs = []
+        for _ in range(2):
+            g = torch.empty(5057, device="cuda")
+            cm.camelot_predictor_grad(h, Xd, td, torch.from_numpy(perm).cuda(), 700, g)
+            outs.append(g.cpu().numpy())
+        g = torch.empty(5057, device="cuda")
+        cm.camelot_predictor_grad(h, torch.from_numpy(X[perm]).cuda(), torch.from_numpy(t[perm]).cuda(),
+                                  None, 700, g)
+        gathered = g.cpu().numpy()
+    finally:
+        cm.camelot_predictor_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], gathered)
+
+
+def test_adam_steps_match_oracle(orc):
+    from paper_2005_02088_b300 import camelot as cm
+    th0 = _theta(10, 0.2)
+    X, t = _data(11, 256)
+    lr = 1e-3
+    h = cm.camelot_predictor_create(th0)
+    try:
+        Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+        m = np.zeros(5057)
+        v = np.zeros(5057)
+        for step in range(1, 6):
+            before = cm.camelot_predictor_get_params(h).astype(np.float64)
+            g = torch.empty(5057, device="cuda")
+            cm.camelot_predictor_grad(h, Xd, td, None, 256, g)
+            cm.camelot_predictor_train_step(h, Xd, td, None, 256, lr)
+            torch.cuda.synchronize()
+            after = cm.camelot_predictor_get_params(h).astype(np.float64)
+            ref = before.copy()
+            orc.adam_step(ref, g.cpu().numpy(), m, v, step, lr=lr)
+            assert np.all(np.abs(after - ref) <= 1e-6 * np.abs(ref) + 1e-3 * lr), step
+    finally:
+        cm.camelot_predictor_destroy(h)
+
+
+def test_bad_arguments_are_rejected():
+    from paper_2005_02088_b300 import camelot as cm
+    h = cm.camelot_predictor_create(_theta())
+    try:
+        X = torch.zeros((4, 12), device="cuda")
+        t = torch.zeros(4, device="cuda")
+        with pytest.raises(cm.CamelotError) as e:
+            cm.camelot_predictor_train_step(h, X, t, None, 0, 1e-3)
+        assert e.value.status == cm.EINVAL
+        with pytest.raises(cm.CamelotError):
+            cm.camelot_predictor_train_step(h, X, t, None, 65537, 1e-3)
+        with pytest.raises(cm.CamelotError):
+            cm.camelot_predictor_train_step(h, X, t, None, 4, 0.0)
+        with pytest.raises(cm.CamelotError):
+            cm.camelot_predictor_forward(h, X, 0, t)
+        with pytest.raises(ValueError):
+            cm.camelot_predictor_create(np.zeros(5056, np.float32))
+    finally:
+        cm.camelot_predictor_destroy(h)
+
+
+def test_training_fits_a_smooth_function():
+    """GPU training drives the loss of a smooth target far below its variance."""
+    from paper_2005_02088_b300 import predictor as pr
+    g = np.random.default_rng(12)
+    X = g.uniform(0, 1, (4000, 12)).astype(np.float32)
+    y = (np.log1p(3 * X[:, 0]) + X[:, 1] * X[:, 2] - 0.5 * X[:, 3] ** 2).astype(np.float32)
+    p = pr.LatencyPredictor(seed=0)
+    try:
+        hist = p.fit(X[:3000], y[:3000], epochs=60, lr=3e-3, batch=128, lr_final=3e-4)
+        pred = p.predict(X[3000:])
+    finally:
+        p.close()
+    assert hist[-1] < 0.05 * hist[0]
+    assert np.mean((pred - y[3000:]) ** 2) < 0.1 * np.var(y[3000:])
+
+
+def test_save_load_round_trip(tmp_path):
+    from paper_2005_02088_b300 import predictor as pr
+    X = np.random.default_rng(13).standard_normal((50, 12)).astype(np.float32)
+    p = pr.LatencyPredictor(seed=4)
+    try:
+        p.set_norm(np.arange(12), np.full(12, 0.5))
+        a = p.predict(X)
+        p.save(str(tmp_path / "p.npz"))
+        q = pr.LatencyPredictor.load(str(tmp_path / "p.npz"))
+        try:
+            b = q.predict(X)
+        finally:
+            q.close()
+    finally:
+        p.close()
+    assert np.array_equal(a, b)
+
+
+def _cfg1_runners(max_batch=64):
+    import synth
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl, predictor as pr
+    x, ws = synth.cfg1_inputs(0, max_batch)
+    s1 = pl.stage_normalize(64, 64, 3, max_batch)
+    wd = [torch.from_numpy(w).cuda() for w in ws]
+    s2 = pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], top_k=1, max_batch=max_batch)
+    xin = torch.from_numpy(np.ascontiguousarray(x.reshape(max_batch, -1))).cuda()
+    r1 = pr.StageRunner(s1, xin, max_batch)
+    r1.time_ms(max_batch, 8, 1)
+    torch.cuda.synchronize()
+    r2 = pr.StageRunner(s2, r1.out, max_batch, top_k=1)
+    return x, (s1, s2), {1: r1, 2: r2}, wd
+
+
+def test_stage_time_and_corunner(orc):
+    """Timed launches return positive durations; a co-runner on other SMs
+    streams at a plausible rate and leaves the stage's result unchanged."""
+    from paper_2005_02088_b300 import camelot as cm, predictor as pr
+    x, stages, runners, _ = _cfg1_runners()
+    try:
+        r1 = runners[1]
+        ms = r1.time_ms(64, 16, 20)
+        assert ms.shape == (20,) and np.all(ms > 0) and np.all(ms < 100)
+        torch.cuda.synchronize()
+        alone = r1.out.clone()
+        co = pr.CoRunner(1 << 28)
+        g = co.solo_gbs(32)
+        assert 100 < g < 20000, g
+        r1.out.zero_()
+        h = co.start(96)
+        try:
+            ms2 = r1.time_ms(64, 16, 20)
+        finally:
+            g2 = co.stop(h)
+        assert np.all(ms2 > 0) and g2 > 0
+        assert torch.equal(r1.out, alone)
+        ref = orc.normalize_u8(x.reshape(64, -1)).astype(np.float32)
+        assert np.array_equal(alone.view(torch.float32).cpu().numpy().reshape(64, -1), ref)
+        with pytest.raises(cm.CamelotError):
+            cm.camelot_corunner_start(co.src, co.dst, co.nbytes, 0)
+    finally:
+        for s in stages:
+            cm.camelot_stage_release(s)
+
+
+def test_predictor_study_small():
+    """Profile the cfg1 stages under random quotas, batches and co-runners,
+    train on the GPU, and judge: held-out MAPE, the gain over the
+    contention-unaware solo-profile table, and Eq. 1 allocation from the
+    predicted table within 5% of brute force over the measured table."""
+    from paper_2005_02088_b300 import camelot as cm, predictor as pr
+    _, stages, runners, _ = _cfg1_runners()
+    costs = {1: pr.StageCost(1, 2 * 12288, 0.0, 12288 + 49152),
+             2: pr.dense_cost(2, [12288, 512, 256, 10], 49152, 8)}
+    try:
+        r = pr.study(runners, costs, n_samples=3000, runs=40, batches=(1, 2, 4, 8, 16, 32, 64),
+                     epochs=600, co_bytes=1 << 29)
+        r["_predictor"].close()
+    finally:
+        for s in stages:
+            cm.camelot_stage_release(s)
+    assert r["mape"]["all"] < 0.15, r["mape"]
+    assert r["mape"]["corunner"] < r["without_predictor"]["mape_corunner"], (r["mape"], r["without_predictor"])
+    assert r["allocation"]["max_peak"]["ratio_to_brute_force"] >= 0.95, r["allocation"]["max_peak"]
+    assert r["inference"]["seconds"] < 0.05
