@@ -38,7 +38,7 @@ constexpr int kWarpEpi0 = 4;    // warps 4..7 read the accumulators
 
 struct GemmSmem {
     char* ring;            // kGemmStages x (2 weight tiles, 32 KB, then 2 query tiles, 8 KB)
-    uint64_t* full;        // [kGemmStages] both tiles landed (1 copy arrival + tx, 32 loader arrivals)
+    uint64_t* full;        // [kGemmStages] both tiles landed (1 copy arrival + tx, 32 cp.async arrivals)
     uint64_t* empty;       // [kGemmStages] MMAs reading the stage are done
     uint64_t* tfull;       // [2] accumulator complete
     uint64_t* tfree;       // [2] accumulator read out (4 arrivals: epilogue warps)
@@ -97,17 +97,23 @@ __device__ __forceinline__ void gemm_teardown(float* smem) {
 }
 
 // Bounded wait on an mbarrier phase; records an error and returns false.
+// These waits hand work between the warps of one CTA every few hundred
+// nanoseconds, so they spin on try_wait (which parks the thread in hardware
+// until the phase flips or a short time passes) with no sleep; the deadline,
+// the iteration cap and the pipeline's error word are checked every 256
+// attempts.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, const StageCtx& cx,
                                                   uint32_t where) {
     if (mbar_try_wait(bar, parity)) return true;
-    Backoff bo(cx.limit_ns);
-    while (!mbar_try_wait(bar, parity)) {
-        if (has_error(cx.ctl) || !bo.step()) {
+    const uint64_t deadline = gtime() + cx.limit_ns;
+    const uint64_t cap = cx.limit_ns / 16 + 4000000ull;
+    for (uint64_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && (it > cap || gtime() > deadline || has_error(cx.ctl))) {
             record_error(cx.ctl, DEV_ERR_GROUP_BARRIER, 400 + 10 * cx.where + where);
             return false;
         }
     }
-    return true;
 }
 
 // Output of one layer: bf16 rows (hidden / next stage) or f32 rows (logits).
@@ -166,10 +172,9 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             }
         } else if (warp == kWarpB) {
             // query tiles of every (unit, k-block): 32 rows x 128 bytes, 16-byte
-            // piece j of row r at r * 128 + ((j ^ (r & 7)) * 16).  One cp.async
-            // group per stage; kBLag groups stay in flight, and a stage is
-            // signalled full once its group has landed.
-            constexpr int kBLag = kGemmStages - 2;
+            // piece j of row r at r * 128 + ((j ^ (r & 7)) * 16).  Each lane's
+            // cp.async completion arrives on the stage's full barrier by itself,
+            // so the loader runs as far ahead as the ring allows.
             uint32_t gi = ring0;
             for (int u = u0; u < u1; ++u) {
                 const int c = u / MT;
@@ -192,20 +197,9 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                             cp_async16_zfill(dst + r * 128 + ((j ^ (r & 7)) << 4), src, r < n ? 16u : 0u);
                         }
                     }
-                    cp_async_commit();
-                    if (gi >= ring0 + kBLag) {
-                        cp_async_wait<kBLag>();
-                        fence_proxy_async_smem();
-                        mbar_arrive(&g.full[(gi - kBLag) % kGemmStages]);
-                    }
+                    cp_async_mbar_arrive_noinc(&g.full[s]);
                 }
             }
-            // the last kBLag (or fewer) stages
-            cp_async_wait<0>();
-            fence_proxy_async_smem();
-            const uint32_t gend = gi;
-            for (uint32_t g2 = (gend >= ring0 + kBLag ? gend - kBLag : ring0); g2 < gend; ++g2)
-                mbar_arrive(&g.full[g2 % kGemmStages]);
         } else if (warp == kWarpMma && lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(128, kGemmN);
             uint32_t gi = ring0, a = a0;
@@ -220,15 +214,32 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                     const int nk = min(kKbPerStage, nkb - kb);
                     const int s = gi % kGemmStages;
                     if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) goto done;
+                    // the query tiles were written by cp.async (generic proxy):
+                    // order them before the tensor core's reads
+                    fence_proxy_async_smem();
                     tc_fence_after();
+                    // descriptors of the stage's first A and B slices; a slice
+                    // 32 bytes further along is the start field + 2 (the field is
+                    // address >> 4 and shared memory stays below 256 KB, so the
+                    // additions never carry out of it)
                     const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
-                    for (int t = 0; t < nk; ++t) {
-                        const uint32_t a_addr = sbase + t * kATileBytes;
-                        const uint32_t b_addr = sbase + kKbPerStage * kATileBytes + t * kBTileBytes;
+                    const uint64_t da = sw128_desc(sbase);
+                    const uint64_t db = sw128_desc(sbase + kKbPerStage * kATileBytes);
+                    if (nk == kKbPerStage) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            tc_mma_f16(d_tmem, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k),
-                                       idesc, (kb + t > 0 || k > 0) ? 1u : 0u);
+                        for (int t = 0; t < kKbPerStage; ++t)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * k) / 16,
+                                           db + (t * kBTileBytes + 32 * k) / 16, idesc,
+                                           (kb + t > 0 || k > 0) ? 1u : 0u);
+                    } else {
+                        for (int t = 0; t < nk; ++t)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * k) / 16,
+                                           db + (t * kBTileBytes + 32 * k) / 16, idesc,
+                                           (kb + t > 0 || k > 0) ? 1u : 0u);
                     }
                     tc_commit(&g.empty[s]);
                 }
@@ -265,6 +276,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
         }
     }
 done:
+    cp_async_wait<0>();   // nothing of this layer still lands in the ring (error paths)
     __syncthreads();
     if (threadIdx.x == 0 && u0 < u1) {
         uint32_t stages = 0;
