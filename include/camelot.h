@@ -275,8 +275,12 @@ typedef struct {
     int32_t exit_after_trace; /* 1: the persistent kernel ends as soon as a trace has been
                                fully taken and drained (one launch per trace, which makes
                                the launch's CUDA-event time the trace's device time)  */
-    uint32_t data_slots;    /* rows of the pinned host buffer that holds submitted query
-                               bytes (power of two <= query_slots; 0 = query_slots)     */
+    uint32_t data_slots;    /* rows of the buffer that holds submitted query bytes
+                               (power of two <= query_slots; 0 = query_slots)          */
+    int32_t device_data;    /* 0: that buffer is pinned, mapped host memory which stage 0
+                               reads over the host link; 1: it is device memory which
+                               camelot_submit fills with DMA copies (cudaMemcpyAsync,
+                               at most two per call) and waits for before publishing   */
 } camelot_options;
 
 /* Fill `o` with the defaults above. */
@@ -298,7 +302,8 @@ camelot_status camelot_pipeline_create(camelot_stage* const* stages, int n_stage
                                        const camelot_options* opts, camelot_pipeline** out);
 
 /* Queue n queries from host memory (n * stage-0 input row bytes, rows
- * contiguous); the bytes are copied before return.  Query IDs are assigned
+ * contiguous; pinned memory makes the device_data copies run at the DMA
+ * engine's rate); the bytes are copied before return.  Query IDs are assigned
  * consecutively from *first_query_id (a per-pipeline counter starting at 0).
  * arrival_ns (host, nullable) gives each query's arrival stamp on the host
  * CLOCK_MONOTONIC scale; NULL stamps them with the time of the call.  All or

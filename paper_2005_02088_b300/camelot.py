@@ -46,7 +46,7 @@ class Options(C.Structure):
     _fields_ = [("query_slots", C.c_uint32), ("batch_slots", C.c_uint32), ("max_wait_ns", C.c_int64),
                 ("idle_exit_ns", C.c_int64), ("wait_limit_ns", C.c_int64),
                 ("logits_sink", C.c_void_p), ("exit_after_trace", C.c_int32),
-                ("data_slots", C.c_uint32)]
+                ("data_slots", C.c_uint32), ("device_data", C.c_int32)]
 
 
 class Completion(C.Structure):

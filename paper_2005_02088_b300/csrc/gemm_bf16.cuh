@@ -28,23 +28,26 @@ constexpr int kGemmN = 32;                       // queries per MMA (N)
 constexpr uint32_t kATileBytes = 128 * 64 * 2;   // one 128 x 64 bf16 weight tile
 constexpr uint32_t kBTileBytes = kGemmN * 64 * 2;   // the matching 32 x 64 query tile
 constexpr uint32_t kStageBytes = kKbPerStage * (kATileBytes + kBTileBytes);   // 40 KB
-constexpr uint32_t kTmemCols = 64;               // two 32-column accumulators
+constexpr int kIssuers = 2;                      // MMA-issuing warps
+constexpr uint32_t kTmemCols = 2 * kIssuers * kGemmN;   // two 32-column accumulators per issuer
 
 // Warp roles inside a CTA running tensor-core layers.
 constexpr int kWarpTma = 0;     // weight tiles, bulk copies
-constexpr int kWarpMma = 1;     // tcgen05.mma issue (one thread)
 constexpr int kWarpB = 2;       // query tiles, cp.async
 constexpr int kWarpEpi0 = 4;    // warps 4..7 read the accumulators
+// warps 1 and 3 issue tcgen05.mma (one thread each): issuer 0 takes the
+// CTA's even units, issuer 1 the odd ones
+__device__ __forceinline__ int issuer_of_warp(int warp) { return warp == 1 ? 0 : (warp == 3 ? 1 : -1); }
 
 struct GemmSmem {
     char* ring;            // kGemmStages x (2 weight tiles, 32 KB, then 2 query tiles, 8 KB)
     uint64_t* full;        // [kGemmStages] both tiles landed (1 copy arrival + tx, 32 cp.async arrivals)
     uint64_t* empty;       // [kGemmStages] MMAs reading the stage are done
-    uint64_t* tfull;       // [2] accumulator complete
-    uint64_t* tfree;       // [2] accumulator read out (4 arrivals: epilogue warps)
+    uint64_t* tfull;       // [2 * kIssuers] accumulator complete
+    uint64_t* tfree;       // [2 * kIssuers] accumulator read out (4 arrivals: epilogue warps)
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
     uint32_t* ring_it;     // stages filled so far (all launches of this CTA)
-    uint32_t* acc_it;      // units finished so far
+    uint32_t* acc_it;      // [kIssuers] units finished so far by each issuer
 };
 
 __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
@@ -56,8 +59,8 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     g.full = bars;
     g.empty = g.full + kGemmStages;
     g.tfull = g.empty + kGemmStages;
-    g.tfree = g.tfull + 2;
-    g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2);
+    g.tfree = g.tfull + 2 * kIssuers;
+    g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
     g.ring_it = g.tmem_slot + 1;
     g.acc_it = g.ring_it + 1;
     return g;
@@ -71,12 +74,12 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
             mbar_init(&g.full[s], 1 + 32);
             mbar_init(&g.empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 2 * kIssuers; ++b) {
             mbar_init(&g.tfull[b], 1);
             mbar_init(&g.tfree[b], 4);
         }
         *g.ring_it = 0;
-        *g.acc_it = 0;
+        for (int w = 0; w < kIssuers; ++w) g.acc_it[w] = 0;
         mbar_fence_init();
     }
     if (threadIdx.x < 32) {
@@ -127,13 +130,35 @@ __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float
     else reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = __float2bfloat16_rn(v);
 }
 
+// The order in which a CTA's ring stages carry its units: units are taken in
+// pairs (r, r + 1) relative to the CTA's first unit, and the stages of a pair
+// alternate between its two units, so both issuers always have stages in the
+// ring.  f(u, r, j, gi) is called for stage j of unit u0 + r at ring position
+// gi, in ring order; it returns false to stop.
+template <class StagesOf, class F>
+__device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, StagesOf stages_of, F f) {
+    uint32_t gi = ring0;
+    for (int r = 0; u0 + r < u1; r += 2) {
+        const int ua = u0 + r;
+        const bool pair = ua + 1 < u1;
+        const int na = stages_of(ua), nb = pair ? stages_of(ua + 1) : 0;
+        const int nmax = na > nb ? na : nb;
+        for (int j = 0; j < nmax; ++j) {
+            if (j < na && !f(ua, r, j, gi++)) return false;
+            if (j < nb && !f(ua + 1, r + 1, j, gi++)) return false;
+        }
+    }
+    return true;
+}
+
 // One layer.  Work units u = (chunk c, 128-row tile mt) in chunk-major order
 // (u = c * MT + mt); CTA r takes the contiguous units [r U / p, (r+1) U / p).
-// Every unit accumulates the same K range in the same MMA order whichever CTA
-// runs it.  Each ring stage carries two consecutive weight tiles (one 32 KB
-// bulk copy: the copy engine's cost is per operation, so larger copies stream
-// faster; kept in L2 with the evict-last policy) and the matching query tiles
-// (cp.async by the loader warp, 128-byte swizzle).
+// Every unit accumulates the same K range in the same MMA order, issued by
+// one thread into one accumulator, whichever CTA or issuer runs it.  Each ring
+// stage carries two consecutive weight tiles (one 32 KB bulk copy: the copy
+// engine's cost is per operation, so larger copies stream faster; kept in L2
+// with the evict-last policy) and the matching query tiles (cp.async by the
+// loader warp, 128-byte swizzle).
 static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
                                         float* Pbuf, const LayerOut& direct) {
     const GemmSmem g = gemm_smem(cx.smem);
@@ -142,116 +167,135 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     const int U = MT * L.C;
     const int u0 = (int)((long long)cx.rank * U / cx.nctas);
     const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
-    const uint32_t ring0 = *g.ring_it, a0 = *g.acc_it;
+    const uint32_t ring0 = *g.ring_it;
+    uint32_t accb[kIssuers];
+#pragma unroll
+    for (int w = 0; w < kIssuers; ++w) accb[w] = g.acc_it[w];
     const uint32_t tmem = *g.tmem_slot;
     auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) / 64; };
-    auto stages_of = [&](int c) { return (chunk_kb(c) + kKbPerStage - 1) / kKbPerStage; };
+    auto stages_of = [&](int u) { return (chunk_kb(u / MT) + kKbPerStage - 1) / kKbPerStage; };
+    // accumulator of the unit that is issuer w's k-th (counting all its
+    // earlier units): two per issuer, alternating
+    auto acc_of = [&](int w, uint32_t k) { return 2 * w + (int)(k & 1u); };
+    const int iw = issuer_of_warp(warp);
 
     if (u0 < u1) {
         if (warp == kWarpTma && lane == 0) {
-            // weight tiles of every unit, in order: tiles (mt, kb) and (mt, kb+1)
-            // are adjacent in memory, so a stage is one bulk copy
+            // tiles (mt, kb) and (mt, kb+1) are adjacent in memory: one bulk copy
             const uint64_t pol = l2_policy_evict_last();
             const char* wt = reinterpret_cast<const char*>(L.w);
             const int KB = L.K / 64;                     // weight tiles per 128-row block
-            uint32_t gi = ring0;
-            for (int u = u0; u < u1; ++u) {
+            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
                 const int c = u / MT, mt = u - c * MT;
-                const int nkb = chunk_kb(c);
-                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
-                    const int nk = min(kKbPerStage, nkb - kb);
-                    const int s = gi % kGemmStages;
-                    if (gi >= (uint32_t)kGemmStages &&
-                        !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
-                        goto done;
-                    mbar_arrive_expect_tx(&g.full[s], nk * kATileBytes);
-                    bulk_load_hint(g.ring + s * kStageBytes,
-                                   wt + ((size_t)mt * KB + c * (L.KC / 64) + kb) * kATileBytes,
-                                   nk * kATileBytes, &g.full[s], pol);
-                }
-            }
+                const int kb = j * kKbPerStage;
+                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
+                const int s = gi % kGemmStages;
+                if (gi >= (uint32_t)kGemmStages &&
+                    !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
+                    return false;
+                mbar_arrive_expect_tx(&g.full[s], nk * kATileBytes);
+                bulk_load_hint(g.ring + s * kStageBytes,
+                               wt + ((size_t)mt * KB + c * (L.KC / 64) + kb) * kATileBytes,
+                               nk * kATileBytes, &g.full[s], pol);
+                return true;
+            });
         } else if (warp == kWarpB) {
-            // query tiles of every (unit, k-block): 32 rows x 128 bytes, 16-byte
-            // piece j of row r at r * 128 + ((j ^ (r & 7)) * 16).  Each lane's
-            // cp.async completion arrives on the stage's full barrier by itself,
-            // so the loader runs as far ahead as the ring allows.
-            uint32_t gi = ring0;
-            for (int u = u0; u < u1; ++u) {
-                const int c = u / MT;
-                const int nkb = chunk_kb(c);
-                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
-                    const int nk = min(kKbPerStage, nkb - kb);
-                    const int s = gi % kGemmStages;
-                    if (gi >= (uint32_t)kGemmStages &&
-                        !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 2))
-                        goto done;
-                    char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
-                    for (int t = 0; t < nk; ++t) {
-                        char* dst = dstb + t * kBTileBytes;
-                        const size_t k_off = (size_t)(c * L.KC + (kb + t) * 64) * 2;
+            // query tiles: 32 rows x 128 bytes, 16-byte piece j of row r at
+            // r * 128 + ((j ^ (r & 7)) * 16).  Lane l always copies piece
+            // j = l % 8 of rows r = l / 8 + 4 i (i < 8): its source rows and
+            // destination offsets are fixed for the layer.  Each lane's cp.async
+            // completion arrives on the stage's full barrier by itself, so the
+            // loader runs as far ahead as the ring allows.
+            const int jj = lane & 7;
+            const char* src_row[8];
+            uint32_t dst_off[8], src_bytes[8];
 #pragma unroll
-                        for (int i = 0; i < (kGemmN * 8) / 32; ++i) {
-                            const int e = lane + 32 * i;
-                            const int r = e >> 3, j = e & 7;
-                            const char* src = x.row(r < n ? r : 0) + k_off + 16 * j;
-                            cp_async16_zfill(dst + r * 128 + ((j ^ (r & 7)) << 4), src, r < n ? 16u : 0u);
-                        }
-                    }
-                    cp_async_mbar_arrive_noinc(&g.full[s]);
-                }
+            for (int i = 0; i < 8; ++i) {
+                const int r = (lane >> 3) + 4 * i;
+                src_row[i] = x.row(r < n ? r : 0) + 16 * jj;
+                src_bytes[i] = r < n ? 16u : 0u;
+                dst_off[i] = (uint32_t)(r * 128 + ((jj ^ (r & 7)) << 4));
             }
-        } else if (warp == kWarpMma && lane == 0) {
+            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
+                const int c = u / MT;
+                const int kb = j * kKbPerStage;
+                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
+                const int s = gi % kGemmStages;
+                if (gi >= (uint32_t)kGemmStages &&
+                    !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 2))
+                    return false;
+                char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
+                for (int t = 0; t < nk; ++t) {
+                    char* dst = dstb + t * kBTileBytes;
+                    const size_t k_off = (size_t)(c * L.KC + (kb + t) * 64) * 2;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) cp_async16_zfill(dst + dst_off[i], src_row[i] + k_off, src_bytes[i]);
+                }
+                cp_async_mbar_arrive_noinc(&g.full[s]);
+                return true;
+            });
+        } else if (iw >= 0 && lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(128, kGemmN);
-            uint32_t gi = ring0, a = a0;
-            for (int u = u0; u < u1; ++u, ++a) {
+            uint32_t k = accb[iw];
+            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int r, int j, uint32_t gi) {
+                if ((r & 1) != iw) return true;
+                const int acc = acc_of(iw, k);
+                const int ns = stages_of(u);
+                if (j == 0 && k >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((k >> 1) - 1) & 1, cx, 4))
+                    return false;
                 const int c = u / MT;
-                const int nkb = chunk_kb(c);
-                const int acc = a & 1;
-                if (a >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((a >> 1) - 1) & 1, cx, 4)) goto done;
+                const int kb = j * kKbPerStage;
+                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
+                const int s = gi % kGemmStages;
+                if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) return false;
+                // the query tiles were written by cp.async (generic proxy):
+                // order them before the tensor core's reads
+                fence_proxy_async_smem();
                 tc_fence_after();
+                // descriptors of the stage's first A and B slices; a slice 32
+                // bytes further along is the start field + 2 (the field is
+                // address >> 4 and shared memory stays below 256 KB, so the
+                // additions never carry out of it)
                 const uint32_t d_tmem = tmem + acc * kGemmN;
-                for (int kb = 0; kb < nkb; kb += kKbPerStage, ++gi) {
-                    const int nk = min(kKbPerStage, nkb - kb);
-                    const int s = gi % kGemmStages;
-                    if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) goto done;
-                    // the query tiles were written by cp.async (generic proxy):
-                    // order them before the tensor core's reads
-                    fence_proxy_async_smem();
-                    tc_fence_after();
-                    // descriptors of the stage's first A and B slices; a slice
-                    // 32 bytes further along is the start field + 2 (the field is
-                    // address >> 4 and shared memory stays below 256 KB, so the
-                    // additions never carry out of it)
-                    const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
-                    const uint64_t da = sw128_desc(sbase);
-                    const uint64_t db = sw128_desc(sbase + kKbPerStage * kATileBytes);
-                    if (nk == kKbPerStage) {
+                const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
+                const uint64_t da = sw128_desc(sbase);
+                const uint64_t db = sw128_desc(sbase + kKbPerStage * kATileBytes);
+                if (nk == kKbPerStage) {
 #pragma unroll
-                        for (int t = 0; t < kKbPerStage; ++t)
+                    for (int t = 0; t < kKbPerStage; ++t)
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * k) / 16,
-                                           db + (t * kBTileBytes + 32 * k) / 16, idesc,
-                                           (kb + t > 0 || k > 0) ? 1u : 0u);
-                    } else {
-                        for (int t = 0; t < nk; ++t)
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
+                                       db + (t * kBTileBytes + 32 * kk) / 16, idesc,
+                                       (kb + t > 0 || kk > 0) ? 1u : 0u);
+                } else {
+                    for (int t = 0; t < nk; ++t)
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * k) / 16,
-                                           db + (t * kBTileBytes + 32 * k) / 16, idesc,
-                                           (kb + t > 0 || k > 0) ? 1u : 0u);
-                    }
-                    tc_commit(&g.empty[s]);
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
+                                       db + (t * kBTileBytes + 32 * kk) / 16, idesc,
+                                       (kb + t > 0 || kk > 0) ? 1u : 0u);
                 }
-                tc_commit(&g.tfull[acc]);
-            }
+                tc_commit(&g.empty[s]);
+                if (j == ns - 1) {
+                    tc_commit(&g.tfull[acc]);
+                    ++k;
+                }
+                return true;
+            });
         } else if (warp >= kWarpEpi0) {
-            // accumulator rows 32 (warp % 4) .. +31, all 32 query columns
+            // accumulator rows 32 (warp % 4) .. +31, all 32 query columns; units
+            // in order, each from its issuer's accumulator
             const int sub = warp & 3;
-            for (int u = u0, a = (int)a0; u < u1; ++u, ++a) {
+            uint32_t kw[kIssuers];
+#pragma unroll
+            for (int w = 0; w < kIssuers; ++w) kw[w] = accb[w];
+            for (int u = u0; u < u1; ++u) {
+                const int w = (u - u0) & 1;
+                const uint32_t k = kw[w]++;
                 const int c = u / MT, mt = u - c * MT;
-                const int acc = a & 1;
-                if (!mbar_wait_bounded(&g.tfull[acc], (a >> 1) & 1, cx, 6)) break;
+                const int acc = acc_of(w, k);
+                if (!mbar_wait_bounded(&g.tfull[acc], (k >> 1) & 1, cx, 6)) break;
                 tc_fence_after();
                 uint32_t r0[16], r1[16];
                 const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + acc * kGemmN;
@@ -275,14 +319,15 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             }
         }
     }
-done:
     cp_async_wait<0>();   // nothing of this layer still lands in the ring (error paths)
     __syncthreads();
     if (threadIdx.x == 0 && u0 < u1) {
         uint32_t stages = 0;
-        for (int u = u0; u < u1; ++u) stages += stages_of(u / MT);
+        for (int u = u0; u < u1; ++u) stages += stages_of(u);
         *g.ring_it = ring0 + stages;
-        *g.acc_it = a0 + (uint32_t)(u1 - u0);
+        const uint32_t cnt = (uint32_t)(u1 - u0);
+        g.acc_it[0] = accb[0] + (cnt + 1) / 2;
+        g.acc_it[1] = accb[1] + cnt / 2;
     }
     __syncthreads();
     return !has_error(cx.ctl);

@@ -365,6 +365,7 @@ extern "C" void camelot_options_default(camelot_options* o) {
     o->logits_sink = nullptr;
     o->exit_after_trace = 0;
     o->data_slots = 0;
+    o->device_data = 0;
 }
 
 struct HostRing {   // one batch ring's allocations
@@ -398,7 +399,8 @@ struct camelot_pipeline {
     HostRing out_rings[kMaxStages], in_rings[kMaxStages];
     unsigned ring_slots[kMaxStages] = {};
     QDesc* qring = nullptr;            // pinned
-    char* qdata = nullptr;             // pinned
+    char* qdata = nullptr;             // pinned (device_data = 0) or device memory
+    cudaStream_t h2d = nullptr;        // device_data: submit's copies
     CompSlot* comp = nullptr;          // pinned
     TraceDev* trace = nullptr;         // device
     cudaStream_t kstream = nullptr, side = nullptr;
@@ -503,7 +505,11 @@ static void pipeline_free(camelot_pipeline* p) {
     if (p->trace) cudaFree(p->trace);
     if (p->hflags) cudaFreeHost(p->hflags);
     if (p->qring) cudaFreeHost(p->qring);
-    if (p->qdata) cudaFreeHost(p->qdata);
+    if (p->qdata) {
+        if (p->opt.device_data) cudaFree(p->qdata);
+        else cudaFreeHost(p->qdata);
+    }
+    if (p->h2d) cudaStreamDestroy(p->h2d);
     if (p->comp) cudaFreeHost(p->comp);
     if (p->kdone) cudaEventDestroy(p->kdone);
     if (p->kstart) cudaEventDestroy(p->kstart);
@@ -766,7 +772,12 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     const size_t q_row = stages[0]->sp.in_row_bytes;
     P_TRY(cudaHostAlloc((void**)&p->qring, R * sizeof(QDesc), cudaHostAllocMapped | cudaHostAllocPortable));
     const size_t D = o.data_slots;
-    P_TRY(cudaHostAlloc((void**)&p->qdata, D * q_row, cudaHostAllocMapped | cudaHostAllocPortable));
+    if (o.device_data) {
+        P_TRY(cudaMalloc(&p->qdata, D * q_row));
+        P_TRY(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking));
+    } else {
+        P_TRY(cudaHostAlloc((void**)&p->qdata, D * q_row, cudaHostAllocMapped | cudaHostAllocPortable));
+    }
     P_TRY(cudaHostAlloc((void**)&p->comp, R * sizeof(CompSlot), cudaHostAllocMapped | cudaHostAllocPortable));
     memset((void*)p->qring, 0, R * sizeof(QDesc));
     memset((void*)p->comp, 0, R * sizeof(CompSlot));
@@ -826,9 +837,21 @@ extern "C" camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id
     }
     const size_t row = p->hp.q_row;
     const int64_t now = host_now_ns();
+    if (p->opt.device_data) {
+        // rows t0 .. t0+n-1 occupy one or two contiguous runs of the ring
+        const uint64_t first = t0 & dmask;
+        const uint64_t run1 = std::min<uint64_t>(n, D - first);
+        if (cudaMemcpyAsync(p->qdata + first * row, queries, run1 * row, cudaMemcpyHostToDevice, p->h2d) !=
+                cudaSuccess ||
+            (run1 < n && cudaMemcpyAsync(p->qdata, (const char*)queries + run1 * row, (n - run1) * row,
+                                         cudaMemcpyHostToDevice, p->h2d) != cudaSuccess) ||
+            cudaStreamSynchronize(p->h2d) != cudaSuccess)
+            return fail(CAMELOT_ECUDA, "query copy to the device data ring failed");
+    }
     for (uint32_t i = 0; i < n; ++i) {
         const uint64_t t = t0 + i;
-        memcpy(p->qdata + (t & dmask) * row, (const char*)queries + (size_t)i * row, row);
+        if (!p->opt.device_data)
+            memcpy(p->qdata + (t & dmask) * row, (const char*)queries + (size_t)i * row, row);
         QDesc& d = p->qring[t & mask];
         d.t_arrival = arrival_ns ? arrival_ns[i] : now;
         d.stream_id = stream_id;

@@ -160,6 +160,17 @@ def test_small_data_ring_wraps(stages):
     assert np.array_equal(logits, ref)
 
 
+@pytest.mark.parametrize("data_slots,chunk", [(0, 64), (64, 48)])
+def test_device_data_ring_identical(stages, data_slots, chunk):
+    # query bytes DMA-copied into a device ring at submit (wrapping when the
+    # ring is small): the same results as the mapped host ring
+    _, ref, _ = _run(stages, 0)
+    o = pl.options(query_slots=256, data_slots=data_slots, device_data=1)
+    comps, logits, _ = _run(stages, 0, opts=o, chunk=chunk)
+    assert [c.query_id for c in comps] == list(range(N_Q))
+    assert np.array_equal(logits, ref)
+
+
 def test_idle_exit_and_relaunch(stages):
     x, _ = cfg1_data(N_Q)
     o = pl.options(idle_exit_ns=20_000_000)
