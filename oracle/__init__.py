@@ -64,6 +64,9 @@ def _declare(L):
         "orc_round_bf16": (None, [P, I64, P]),
         "orc_bf16_bits": (None, [P, I64, P]),
         "orc_round_e4m3": (None, [P, I64, P]),
+        "orc_e4m3_decode": (None, [P, I64, P]),
+        "orc_quantize_e4m3": (C.c_double, [P, I64, P]),
+        "orc_linear_fp8": (None, [P, I64, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_double, P, P, P]),
         "orc_pipeline_mlp": (None, [P, I64, P, P, P, P, P, P, C.c_int]),
         "orc_pipeline_gemm3": (None, [P, I64, C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_int,
                                       P, P, C.c_int]),
@@ -176,6 +179,64 @@ def round_e4m3(v) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # whole pipelines
 # ---------------------------------------------------------------------------
+def e4m3_decode(codes) -> np.ndarray:
+    """Values of OCP FP8 E4M3 codes (uint8 array)."""
+    c = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.empty(c.shape, np.float64)
+    lib().orc_e4m3_decode(_p(c), c.size, _p(out))
+    return out
+
+
+def quantize_e4m3(w):
+    """Per-tensor FP8 quantisation: (scale s, code values of w / s)."""
+    w = _f64(w)
+    q = np.empty_like(w)
+    s = lib().orc_quantize_e4m3(_p(w), w.size, _p(q))
+    return s, q
+
+
+def linear_fp8(xq, wq, vscale: float, act: int = ACT_NONE, s_out: float = 0.0):
+    """FP8-arm dense layer on code values: (y, output code values or None,
+    sum |wq xq| * vscale)."""
+    xq, wq = _f64(xq), _f64(wq)
+    nq, K = xq.shape
+    N = wq.shape[0]
+    y = np.empty((nq, N), np.float64)
+    a = np.empty((nq, N), np.float64)
+    yq = np.empty((nq, N), np.float64) if s_out > 0 else None
+    lib().orc_linear_fp8(_p(xq), nq, K, _p(wq), N, float(vscale), act, float(s_out), _p(y),
+                         _p(yq) if yq is not None else None, _p(a))
+    return y, yq, a
+
+
+def f32(v) -> float:
+    return float(np.float32(v))
+
+
+def pipeline_fp8(x_u8: np.ndarray, ws, act_scales):
+    """The FP8 arm of the plain 2-stage pipeline, emulated on code values:
+    stage 1 = e4m3(2 x - 255) (scale 1/128); each layer l of the ReLU MLP uses
+    e4m3 weights with scale s_w = max|W| / 448 and input scale s_l (s_0 = 1/128,
+    s_1, s_2 = act_scales); hidden outputs are re-quantised with the next
+    layer's scale; the logits stay unquantised.  Returns (logits, argmax,
+    [hidden code values], [s_w])."""
+    x = np.ascontiguousarray(x_u8, dtype=np.uint8).reshape(x_u8.shape[0], -1).astype(np.float64)
+    xq = round_e4m3((x - 127.5) * 2.0)
+    scales = [f32(1.0 / 128.0)] + [f32(s) for s in act_scales]
+    hidden, sws = [], []
+    for l, w in enumerate(ws):
+        sw, wq = quantize_e4m3(w)
+        sws.append(sw)
+        vscale = f32(sw * scales[l])
+        last = l == len(ws) - 1
+        y, yq, _ = linear_fp8(xq, wq, vscale, ACT_NONE if last else ACT_RELU,
+                              0.0 if last else scales[l + 1])
+        if last:
+            return y, argmax(y), hidden, sws
+        hidden.append(yq)
+        xq = yq
+
+
 def pipeline_mlp(x_u8: np.ndarray, ws, nthreads: int = 0):
     """Plain 2-stage pipeline: normalise, 3-layer ReLU MLP, argmax.
     Returns (logits [n, N3] float64, idx [n] int32)."""

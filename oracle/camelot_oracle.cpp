@@ -10,7 +10,8 @@
 // Parts (each function below cites the passage it follows):
 //   1. stage math of the synthetic microservices (stand-ins for the Sec. 3
 //      suite): u8 normalisation, 2x2 pooling, dense layers with ReLU / erf-GELU,
-//      argmax / top-k, and the number formats the reduced-precision arms use;
+//      argmax / top-k, the number formats the reduced-precision arms use, and
+//      the FP8 arm's per-tensor quantisation and scaled dense layers;
 //   2. whole-pipeline references (the plain 2-stage and the 3-stage BF16 pipelines);
 //   3. an event-driven simulator of the wait queue, batch trigger and
 //      multi-instance stage pipeline (Sec. 5.2 steps 1-2, Sec. 4.1);
@@ -188,6 +189,59 @@ void orc_round_e4m3(const double* in, int64_t n, double* out) {
         }
         out[i] = std::copysign(r, v);
     }
+}
+
+// Value of each OCP FP8 E4M3 code: bit 7 sign, bits 6-3 exponent (bias 7),
+// bits 2-0 mantissa; exponent field 0 encodes subnormals m * 2^-9; S.1111.111
+// is NaN (the format has no infinities).
+void orc_e4m3_decode(const uint8_t* codes, int64_t n, double* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        const int c = codes[i];
+        const int e = (c >> 3) & 15, m = c & 7;
+        double v;
+        if (e == 15 && m == 7) v = std::nan("");
+        else if (e == 0) v = std::ldexp((double)m, -9);
+        else v = std::ldexp(1.0 + m / 8.0, e - 7);
+        out[i] = (c & 0x80) ? -v : v;
+    }
+}
+
+// Per-tensor quantisation of the FP8 arm (the scaling the configuration fixes:
+// s = max|w| / 448 computed in binary32, codes e4m3(w / s) with the quotient
+// rounded to binary32 first, as the kernel computes it).  Writes the code
+// values to q and returns s.
+double orc_quantize_e4m3(const double* w, int64_t n, double* q) {
+    double amax = 0.0;
+    for (int64_t i = 0; i < n; ++i) amax = std::max(amax, std::fabs((double)(float)w[i]));
+    const double s = (double)(float)(amax / 448.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double t = (double)(float)((double)(float)w[i] / s);
+        orc_round_e4m3(&t, 1, q + i);
+    }
+    return s;
+}
+
+// Dense layer of the FP8 arm on code values: y[q, j] = act(vscale * sum_k
+// wq[j, k] xq[q, k]) with the sum in FP64 (vscale = the binary32 product of the
+// weight and input scales).  If yq is given, the output codes e4m3(y / s_out)
+// (quotient rounded to binary32).  absdot (nullable): sum_k |wq xq| * vscale.
+void orc_linear_fp8(const double* xq, int64_t nq, int K, const double* wq, int N, double vscale,
+                    int act, double s_out, double* y, double* yq, double* absdot) {
+    for (int64_t q = 0; q < nq; ++q)
+        for (int j = 0; j < N; ++j) {
+            double acc = 0.0, a = 0.0;
+            for (int k = 0; k < K; ++k) {
+                acc += wq[(int64_t)j * K + k] * xq[q * K + k];
+                a += std::fabs(wq[(int64_t)j * K + k] * xq[q * K + k]);
+            }
+            const double v = apply_act(acc * vscale, act);
+            y[q * N + j] = v;
+            if (absdot) absdot[q * N + j] = a * vscale;
+            if (yq) {
+                const double t = (double)(float)(v / s_out);
+                orc_round_e4m3(&t, 1, yq + q * N + j);
+            }
+        }
 }
 
 // ---------------------------------------------------------------------------
