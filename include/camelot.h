@@ -73,12 +73,26 @@ int camelot_version(void);
  *                    (bf16 operands, f32 accumulation in TMEM), each layer's
  *                    output rounded to bf16 after its activation, except the
  *                    last layer of a final (top_k > 0) stage, whose f32 output
- *                    feeds the top-k. */
+ *                    feeds the top-k.  Widths dims[0..L-1] multiples of 64.
+ *   GEMM_FP8       : e4m3 rows -> the same chain with OCP FP8 E4M3 operands and
+ *                    per-tensor scales, f32 accumulation.  Layer l's input code c
+ *                    stands for c * scales[l]; its weights are quantised at
+ *                    prepare time to e4m3(w / s_w), s_w = max|W_l| / 448 (f32),
+ *                    rounding to nearest even, saturating; its output value is
+ *                    act(acc * f32(s_w * scales[l])), stored as the code
+ *                    e4m3(value / scales[l+1]) for hidden layers (and for the
+ *                    last layer of an intermediate stage, with scales[L]), f32
+ *                    for the last layer of a final stage.  Widths dims[0..L-1]
+ *                    multiples of 128; batches of at most 32.
+ *   NORMALIZE_U8_E4M3: u8 image -> e4m3 codes of 128 y (y as NORMALIZE_U8), i.e.
+ *                    e4m3(2 x - 255): the next stage reads them with scale 1/128. */
 typedef enum {
     CAMELOT_STAGE_NORMALIZE_U8 = 1,
     CAMELOT_STAGE_NORM_POOL2_BF16 = 2,
     CAMELOT_STAGE_MLP_FP32 = 3,
-    CAMELOT_STAGE_GEMM_BF16 = 4
+    CAMELOT_STAGE_GEMM_BF16 = 4,
+    CAMELOT_STAGE_GEMM_FP8 = 5,
+    CAMELOT_STAGE_NORMALIZE_U8_E4M3 = 6
 } camelot_stage_kind;
 
 typedef enum { CAMELOT_ACT_NONE = 0, CAMELOT_ACT_RELU = 1, CAMELOT_ACT_GELU = 2 } camelot_act;
@@ -97,8 +111,13 @@ typedef struct {
                                            1..CAMELOT_MAX_TOPK: final stage, emits top-k   */
     int32_t max_batch;                  /* largest batch the stage must accept (1..256)    */
     const void* weights[CAMELOT_MAX_LAYERS]; /* dense: device pointers, row-major
-                                           [dims[l+1]][dims[l]], f32 for MLP_FP32, bf16 for
-                                           GEMM_BF16.  Read once by camelot_stage_prepare. */
+                                           [dims[l+1]][dims[l]], f32 for MLP_FP32 and GEMM_FP8,
+                                           bf16 for GEMM_BF16.  Read once by
+                                           camelot_stage_prepare. */
+    float scales[CAMELOT_MAX_LAYERS + 1]; /* GEMM_FP8 only (> 0): scales[l] is the scale of
+                                           layer l's input codes; scales[n_layers] that of
+                                           an intermediate stage's output codes (static
+                                           scales, calibrated by the caller) */
 } camelot_stage_desc;
 
 /* A prepared stage: validated descriptor plus the library's own copy of its
@@ -111,6 +130,14 @@ typedef struct camelot_stage camelot_stage;
  * call returns.  Errors: EINVAL (shape/kind), ENOMEM, ECUDA. */
 camelot_status camelot_stage_prepare(const camelot_stage_desc* desc, camelot_stage** out);
 camelot_status camelot_stage_release(camelot_stage* st);
+
+/* The weights of tensor-core layer l as the stage's kernels use them, row-major
+ * [dims[l+1]][dims[l]] element codes (bf16 bit patterns for GEMM_BF16, e4m3
+ * codes for GEMM_FP8) written to host memory `out` of `bytes` bytes (exactly
+ * rows x columns x element size), and (nullable) the weight scale s_w (1 for
+ * bf16).  Errors: EINVAL (not a tensor-core stage, bad layer or size), ECUDA. */
+camelot_status camelot_stage_export_weights(const camelot_stage* st, int layer, void* out, size_t bytes,
+                                            float* weight_scale);
 
 /* Row sizes in bytes of one query's input and output for the stage (output
  * bytes are 0 for a final stage), and the device scratch bytes a direct launch

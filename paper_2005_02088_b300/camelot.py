@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, ECUDA, ESTATE, EINFEASIBLE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EAGAIN", "ETIMEDOUT", "ECUDA", "ESTATE", "EINFEASIBLE"]
 
 STAGE_NORMALIZE_U8, STAGE_NORM_POOL2_BF16, STAGE_MLP_FP32, STAGE_GEMM_BF16 = 1, 2, 3, 4
+STAGE_GEMM_FP8, STAGE_NORMALIZE_U8_E4M3 = 5, 6
 ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
 HANDOFF_GLOBAL, HANDOFF_HOST_STAGED = 0, 1
 POLICY_MAX_PEAK, POLICY_MIN_SM = 0, 1
@@ -34,7 +35,7 @@ class CamelotError(RuntimeError):
 class StageDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
                 ("act", C.c_int32 * MAX_LAYERS), ("top_k", C.c_int32), ("max_batch", C.c_int32),
-                ("weights", C.c_void_p * MAX_LAYERS)]
+                ("weights", C.c_void_p * MAX_LAYERS), ("scales", C.c_float * (MAX_LAYERS + 1))]
 
 
 class Alloc(C.Structure):
@@ -86,6 +87,7 @@ _SIGS = {
     "camelot_stage_prepare": (C.c_int, [P, P]),
     "camelot_stage_release": (C.c_int, [P]),
     "camelot_stage_info": (C.c_int, [P, P, P, C.c_uint32, P]),
+    "camelot_stage_export_weights": (C.c_int, [P, C.c_int, P, C.c_size_t, P]),
     "camelot_stage_launch": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P]),
     "camelot_stage_launch_noalloc": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P]),
     "camelot_stage_time": (C.c_int, [P, C.c_int, P, C.c_uint32, P, P, P, P, P, C.c_size_t, P,
@@ -177,6 +179,16 @@ def camelot_stage_info(st: int, n: int = 1):
     a, b, s = C.c_size_t(), C.c_size_t(), C.c_size_t()
     _check(load().camelot_stage_info(st, C.byref(a), C.byref(b), n, C.byref(s)))
     return a.value, b.value, s.value
+
+
+def camelot_stage_export_weights(st: int, layer: int, rows: int, cols: int, esz: int):
+    """Layer weights as the kernels use them: numpy uint16 (bf16 bits) or
+    uint8 (e4m3 codes) [rows, cols], and the weight scale."""
+    import numpy as np
+    out = np.empty((rows, cols), np.uint16 if esz == 2 else np.uint8)
+    sc = C.c_float()
+    _check(load().camelot_stage_export_weights(st, layer, out.ctypes.data, out.nbytes, C.byref(sc)))
+    return out, sc.value
 
 
 def camelot_stage_launch(st: int, n_ctas: int, inp, n: int, out=None, out_idx=None, out_val=None,

@@ -1,7 +1,8 @@
-// GEMM_BF16 stage body: dense layers on the 5th-generation tensor cores.
+// GEMM_BF16 / GEMM_FP8 stage body: dense layers on the 5th-generation tensor
+// cores, bf16 (kind::f16) or e4m3 (kind::f8f6f4) operands, f32 accumulation.
 //
-// Each layer computes y[q][m] = act(sum_k W[m][k] x[q][k]) for a batch of at
-// most 32 queries.  The batch is small, so the operands are swapped: the
+// Each layer computes y[q][m] = act(vscale * sum_k W[m][k] x[q][k]) for a batch
+// of at most 32 queries.  The batch is small, so the operands are swapped: the
 // weights are the M = 128 operand (128 x 64 tiles, stored pre-tiled and
 // pre-swizzled as contiguous 16 KB blocks and streamed by 1-D bulk copies
 // through a shared-memory ring) and the queries are the N = 32
@@ -14,6 +15,7 @@
 // result is the same whatever the number of CTAs.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "device_sync.cuh"
 #include "stage_params.h"
@@ -25,8 +27,8 @@ namespace camelot {
 constexpr int kGemmStages = 5;                   // ring depth
 constexpr int kKbPerStage = 2;                   // k-blocks per stage: one 32 KB weight copy
 constexpr int kGemmN = 32;                       // queries per MMA (N)
-constexpr uint32_t kATileBytes = 128 * 64 * 2;   // one 128 x 64 bf16 weight tile
-constexpr uint32_t kBTileBytes = kGemmN * 64 * 2;   // the matching 32 x 64 query tile
+constexpr uint32_t kATileBytes = 128 * 128;      // one weight tile: 128 rows x 128 bytes
+constexpr uint32_t kBTileBytes = kGemmN * 128;   // the matching query tile: 32 rows x 128 bytes
 constexpr uint32_t kStageBytes = kKbPerStage * (kATileBytes + kBTileBytes);   // 40 KB
 constexpr int kIssuers = 2;                      // MMA-issuing warps
 constexpr uint32_t kTmemCols = 2 * kIssuers * kGemmN;   // two 32-column accumulators per issuer
@@ -119,15 +121,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
-// Output of one layer: bf16 rows (hidden / next stage) or f32 rows (logits).
+// Output of one layer: bf16 rows, f32 rows (logits) or e4m3 rows.
+enum OutFmt : int { OUT_BF16 = 0, OUT_F32 = 1, OUT_E4M3 = 2 };
 struct LayerOut {
     RowRef rows;
-    int f32;
+    int fmt;
+    int act;
+    float vscale;   // accumulator scale
+    float qscale;   // e4m3: the stored code is e4m3(value / qscale)
 };
 
-__device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float v) {
-    if (o.f32) reinterpret_cast<float*>(o.rows.row(q))[m] = v;
-    else reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = __float2bfloat16_rn(v);
+__device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float acc) {
+    const float v = apply_act(acc * o.vscale, o.act);
+    if (o.fmt == OUT_F32) {
+        reinterpret_cast<float*>(o.rows.row(q))[m] = v;
+    } else if (o.fmt == OUT_BF16) {
+        reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = __float2bfloat16_rn(v);
+    } else {
+        reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(q))[m] =
+            __nv_cvt_float_to_fp8(v / o.qscale, __NV_SATFINITE, __NV_E4M3);
+    }
 }
 
 // The order in which a CTA's ring stages carry its units: units are taken in
@@ -172,7 +185,9 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
 #pragma unroll
     for (int w = 0; w < kIssuers; ++w) accb[w] = g.acc_it[w];
     const uint32_t tmem = *g.tmem_slot;
-    auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) / 64; };
+    // k-blocks are 128 bytes wide: 64 bf16 or 128 e4m3 columns
+    auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) * L.esz / 128; };
+    const size_t kc_bytes = (size_t)L.KC * L.esz;
     auto stages_of = [&](int u) { return (chunk_kb(u / MT) + kKbPerStage - 1) / kKbPerStage; };
     // accumulator of the unit that is issuer w's k-th (counting all its
     // earlier units): two per issuer, alternating
@@ -184,7 +199,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             // tiles (mt, kb) and (mt, kb+1) are adjacent in memory: one bulk copy
             const uint64_t pol = l2_policy_evict_last();
             const char* wt = reinterpret_cast<const char*>(L.w);
-            const int KB = L.K / 64;                     // weight tiles per 128-row block
+            const int KB = L.K * L.esz / 128;            // weight tiles per 128-row block
             for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
                 const int c = u / MT, mt = u - c * MT;
                 const int kb = j * kKbPerStage;
@@ -195,7 +210,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                     return false;
                 mbar_arrive_expect_tx(&g.full[s], nk * kATileBytes);
                 bulk_load_hint(g.ring + s * kStageBytes,
-                               wt + ((size_t)mt * KB + c * (L.KC / 64) + kb) * kATileBytes,
+                               wt + ((size_t)mt * KB + c * (kc_bytes / 128) + kb) * kATileBytes,
                                nk * kATileBytes, &g.full[s], pol);
                 return true;
             });
@@ -227,7 +242,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
                 for (int t = 0; t < nk; ++t) {
                     char* dst = dstb + t * kBTileBytes;
-                    const size_t k_off = (size_t)(c * L.KC + (kb + t) * 64) * 2;
+                    const size_t k_off = (size_t)c * kc_bytes + (size_t)(kb + t) * 128;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) cp_async16_zfill(dst + dst_off[i], src_row[i] + k_off, src_bytes[i]);
                 }
@@ -235,7 +250,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 return true;
             });
         } else if (iw >= 0 && lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(128, kGemmN);
+            const bool f8 = L.esz == 1;
+            const uint32_t idesc = f8 ? idesc_e4m3_f32(128, kGemmN) : idesc_bf16_f32(128, kGemmN);
             uint32_t k = accb[iw];
             for_each_stage(u0, u1, ring0, stages_of, [&](int u, int r, int j, uint32_t gi) {
                 if ((r & 1) != iw) return true;
@@ -260,7 +276,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
                 const uint64_t da = sw128_desc(sbase);
                 const uint64_t db = sw128_desc(sbase + kKbPerStage * kATileBytes);
-                if (nk == kKbPerStage) {
+                if (nk == kKbPerStage && !f8) {
 #pragma unroll
                     for (int t = 0; t < kKbPerStage; ++t)
 #pragma unroll
@@ -268,6 +284,13 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                             tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
                                        db + (t * kBTileBytes + 32 * kk) / 16, idesc,
                                        (kb + t > 0 || kk > 0) ? 1u : 0u);
+                } else if (f8) {
+                    for (int t = 0; t < nk; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_f8(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
+                                      db + (t * kBTileBytes + 32 * kk) / 16, idesc,
+                                      (kb + t > 0 || kk > 0) ? 1u : 0u);
                 } else {
                     for (int t = 0; t < nk; ++t)
 #pragma unroll
@@ -311,7 +334,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                     for (int j = 0; j < 32; ++j) {
                         if (j < n) {
                             const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                            if (L.C == 1) store_out(direct, j, m, apply_act(v, L.act));
+                            if (L.C == 1) store_out(direct, j, m, v);
                             else __stcg(Pbuf + ((size_t)c * n + j) * L.Npad + m, v);
                         }
                     }
@@ -373,25 +396,31 @@ static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int
             const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (m + i < L.N) store_out(o, q, m + i, apply_act(vv[i], L.act));
+                if (m + i < L.N) store_out(o, q, m + i, vv[i]);
         }
     }
 }
 
-// The whole GEMM_BF16 stage.
+// The whole GEMM_BF16 / GEMM_FP8 stage.  Hidden rows and the rows handed to
+// the next stage are bf16 (GEMM_BF16) or e4m3 codes (GEMM_FP8); a final stage
+// keeps its logits in f32.
 static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                  RowRef out, const FinalOut& fo) {
     RowRef x = in;
+    const int hfmt = P.kind == KIND_GEMM_FP8 ? OUT_E4M3 : OUT_BF16;
+    const size_t hsz = P.kind == KIND_GEMM_FP8 ? 1 : 2;
     for (int l = 0; l < P.n_layers; ++l) {
         const LayerParams& L = P.layer[l];
         const bool last = (l == P.n_layers - 1);
         LayerOut o;
         if (last && P.top_k == 0) {
-            o = LayerOut{out, 0};
+            o = LayerOut{out, hfmt, L.act, L.vscale, L.qscale};
         } else if (last) {
-            o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * sizeof(float)}, 1};
+            o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * sizeof(float)}, OUT_F32, L.act,
+                         L.vscale, 0.f};
         } else {
-            o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * 2}, 0};
+            o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * hsz}, hfmt, L.act, L.vscale,
+                         L.qscale};
         }
         float* Pbuf = reinterpret_cast<float*>(cx.scratch + L.p_off);
         if (!gemm_layer_tasks(cx, L, x, n, Pbuf, o)) return false;

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     __shared__ unsigned long long sh_in, sh_first, sh_out;
     __shared__ long long sh_tb;
     LeaderState ls{~0ull, 0, gtime()};
-    const bool tensor_stage = (SP.kind == KIND_GEMM_BF16);
+    const bool tensor_stage = is_tensor_kind(SP.kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
 
     for (;;) {
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     StageCtx cx{(int)blockIdx.x, (int)gridDim.x, gs, ctl, (uint64_t)limit_ns, 0u, scratch,
                 reinterpret_cast<float*>(smem4)};
     FinalOut fo{idx, val, logits};
-    const bool tensor_stage = (sp->kind == KIND_GEMM_BF16);
+    const bool tensor_stage = is_tensor_kind(sp->kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
     stage_body(cx, *sp, in, n, out, fo);
     if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));

@@ -84,8 +84,8 @@ extern "C" camelot_status camelot_stage_launch_noalloc(const camelot_stage* st, 
                                                        float* out_logits, void* stream) {
     if (!st) return camelot_internal_fail(CAMELOT_EINVAL, "null stage");
     StageParams sp = *camelot_internal_stage_params(st);
-    if (sp.kind == KIND_GEMM_BF16)
-        return camelot_internal_fail(CAMELOT_EINVAL, "GEMM_BF16 stages need camelot_stage_launch");
+    if (is_tensor_kind(sp.kind))
+        return camelot_internal_fail(CAMELOT_EINVAL, "tensor-core stages need camelot_stage_launch");
     if (n == 0 || (int)n > sp.max_batch)
         return camelot_internal_fail(CAMELOT_EINVAL, "n outside 1..max_batch");
     if (n_ctas < 1 || n_ctas > camelot_internal_sm_count())

@@ -86,11 +86,14 @@ static camelot_status ensure_configured() {
 // ---------------------------------------------------------------------------
 struct camelot_stage {
     camelot_stage_desc desc;
+    float wscale[kMaxLayers] = {1.f, 1.f, 1.f, 1.f};   // tensor-core layers: weight scale s_w
     StageParams sp;            // host copy (device pointers inside)
     StageParams* d_sp = nullptr;
     std::vector<void*> allocs; // device buffers owned by the stage
     int device = 0;
 };
+
+camelot_status camelot_internal_quantize_e4m3(const float* w, int N, int K, int Npad, void** out, float* scale);
 
 static void stage_free(camelot_stage* st) {
     for (void* p : st->allocs) cudaFree(p);
@@ -98,7 +101,8 @@ static void stage_free(camelot_stage* st) {
     delete st;
 }
 
-// K-chunk of a tensor-core layer: 1024 for long K, else 256 (multiples of 64).
+// K-chunk of a tensor-core layer: 1024 columns for long K, else 256 (whole
+// 128-byte k-blocks for bf16 and e4m3 alike).
 static int choose_kc_gemm(int K) { return std::min(K, K >= 8192 ? 1024 : 256); }
 
 // K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, kMaxKC].
@@ -114,7 +118,7 @@ static size_t layout_scratch(StageParams& sp, int B) {
     size_t p_bytes = 0, h_bytes = 0;
     for (int l = 0; l < sp.n_layers; ++l) {
         LayerParams& L = sp.layer[l];
-        if (sp.kind == KIND_GEMM_BF16) {
+        if (is_tensor_kind(sp.kind)) {
             if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * B * L.Npad * sizeof(float));
             h_bytes = std::max(h_bytes, (size_t)B * L.Npad * sizeof(float));
             continue;
@@ -159,16 +163,17 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
 
     switch (d->kind) {
         case CAMELOT_STAGE_NORMALIZE_U8:
+        case CAMELOT_STAGE_NORMALIZE_U8_E4M3:
         case CAMELOT_STAGE_NORM_POOL2_BF16: {
             const int H = d->dims[0], W = d->dims[1], C = d->dims[2];
             if (H <= 0 || W <= 0 || C <= 0) return bail(fail(CAMELOT_EINVAL, "image dims must be > 0"));
             if (d->top_k != 0) return bail(fail(CAMELOT_EINVAL, "image stages cannot be final"));
             sp.H = H; sp.W = W; sp.C = C;
             sp.in_row_bytes = (size_t)H * W * C;
-            if (d->kind == CAMELOT_STAGE_NORMALIZE_U8) {
+            if (d->kind == CAMELOT_STAGE_NORMALIZE_U8 || d->kind == CAMELOT_STAGE_NORMALIZE_U8_E4M3) {
                 if (sp.in_row_bytes % 16)
                     return bail(fail(CAMELOT_EINVAL, "H*W*C must be a multiple of 16"));
-                sp.out_row_bytes = sp.in_row_bytes * 4;
+                sp.out_row_bytes = sp.in_row_bytes * (d->kind == CAMELOT_STAGE_NORMALIZE_U8 ? 4 : 1);
             } else {
                 if (H % 2 || W % 2) return bail(fail(CAMELOT_EINVAL, "H and W must be even"));
                 if ((2 * W * C) % 16 || 2 * W * C > 8192)
@@ -228,14 +233,23 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             sp.scratch_bytes = layout_scratch(sp, d->max_batch);
             break;
         }
-        case CAMELOT_STAGE_GEMM_BF16: {
+        case CAMELOT_STAGE_GEMM_BF16:
+        case CAMELOT_STAGE_GEMM_FP8: {
+            const bool f8 = d->kind == CAMELOT_STAGE_GEMM_FP8;
+            const int esz = f8 ? 1 : 2;
             const int L = d->n_layers;
             if (L < 1 || L > kMaxLayers) return bail(fail(CAMELOT_EINVAL, "n_layers %d outside 1..4", L));
-            if (d->max_batch > 32) return bail(fail(CAMELOT_EINVAL, "GEMM_BF16 stages take batches of at most 32"));
+            if (d->max_batch > 32) return bail(fail(CAMELOT_EINVAL, "tensor-core stages take batches of at most 32"));
             for (int l = 0; l <= L; ++l)
                 if (d->dims[l] <= 0) return bail(fail(CAMELOT_EINVAL, "dims[%d] must be > 0", l));
+            if (f8)
+                for (int l = 0; l <= (d->top_k ? L - 1 : L); ++l)
+                    if (!(d->scales[l] > 0.f) || !std::isfinite(d->scales[l]))
+                        return bail(fail(CAMELOT_EINVAL, "scales[%d] must be finite and > 0", l));
             for (int l = 0; l < L; ++l) {
-                if (d->dims[l] % 64) return bail(fail(CAMELOT_EINVAL, "layer input width dims[%d]=%d must be a multiple of 64", l, d->dims[l]));
+                if ((d->dims[l] * esz) % 128)
+                    return bail(fail(CAMELOT_EINVAL, "layer input width dims[%d]=%d must be a multiple of %d", l,
+                                     d->dims[l], 128 / esz));
                 if (!d->weights[l]) return bail(fail(CAMELOT_EINVAL, "weights[%d] is null", l));
                 if (d->act[l] < 0 || d->act[l] > 2) return bail(fail(CAMELOT_EINVAL, "act[%d] invalid", l));
             }
@@ -243,8 +257,8 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             if (!d->top_k && d->dims[L] % 8)
                 return bail(fail(CAMELOT_EINVAL, "an intermediate stage's output width must be a multiple of 8"));
             sp.n_layers = L;
-            sp.in_row_bytes = (size_t)d->dims[0] * 2;
-            sp.out_row_bytes = d->top_k ? 0 : (size_t)d->dims[L] * 2;
+            sp.in_row_bytes = (size_t)d->dims[0] * esz;
+            sp.out_row_bytes = d->top_k ? 0 : (size_t)d->dims[L] * esz;
             sp.out_width = d->dims[L];
             for (int l = 0; l < L; ++l) {
                 LayerParams& Lp = sp.layer[l];
@@ -253,6 +267,23 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                 Lp.Npad = (N + 127) / 128 * 128;
                 Lp.KC = choose_kc_gemm(K);
                 Lp.C = (K + Lp.KC - 1) / Lp.KC;
+                Lp.esz = esz;
+                Lp.vscale = 1.f;
+                Lp.qscale = 0.f;
+                if (f8) {
+                    void* q = nullptr;
+                    float sw = 0.f;
+                    const camelot_status qs = camelot_internal_quantize_e4m3((const float*)d->weights[l], N, K,
+                                                                             Lp.Npad, &q, &sw);
+                    if (qs != CAMELOT_OK) return bail(qs);
+                    st->allocs.push_back(q);
+                    st->wscale[l] = sw;
+                    Lp.w = (const float*)q;
+                    Lp.vscale = sw * d->scales[l];
+                    const bool out_codes = l < L - 1 || d->top_k == 0;
+                    Lp.qscale = out_codes ? d->scales[l + 1] : 0.f;
+                    continue;
+                }
                 std::vector<uint16_t> w((size_t)N * K);
                 if (cudaMemcpy(w.data(), d->weights[l], w.size() * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
                     return bail(fail(CAMELOT_EINVAL, "weights[%d] is not readable device memory", l));
@@ -305,7 +336,7 @@ static const size_t kDirectHeader = align_up(sizeof(Ctl), 256) + align_up(sizeof
 // Internal helpers shared with noalloc.cu (not part of the C ABI).
 const StageParams* camelot_internal_stage_params(const camelot_stage* st) { return &st->sp; }
 size_t camelot_internal_layout_scratch(StageParams& sp, int B) {
-    return (sp.kind == KIND_MLP_FP32 || sp.kind == KIND_GEMM_BF16) ? layout_scratch(sp, B) : 0;
+    return (sp.kind == KIND_MLP_FP32 || is_tensor_kind(sp.kind)) ? layout_scratch(sp, B) : 0;
 }
 int camelot_internal_sm_count() { return sm_count(); }
 camelot_status camelot_internal_fail(camelot_status st, const char* msg) { return fail(st, "%s", msg); }
@@ -320,6 +351,35 @@ extern "C" camelot_status camelot_stage_info(const camelot_stage* st, size_t* in
     return CAMELOT_OK;
 }
 
+
+extern "C" camelot_status camelot_stage_export_weights(const camelot_stage* st, int layer, void* out,
+                                                       size_t bytes, float* weight_scale) {
+    if (!st || !out) return fail(CAMELOT_EINVAL, "null argument");
+    if (!is_tensor_kind(st->sp.kind)) return fail(CAMELOT_EINVAL, "not a tensor-core stage");
+    if (layer < 0 || layer >= st->sp.n_layers) return fail(CAMELOT_EINVAL, "layer %d outside 0..%d", layer,
+                                                           st->sp.n_layers - 1);
+    const LayerParams& L = st->sp.layer[layer];
+    const size_t rowb = (size_t)L.K * L.esz;
+    if (bytes != (size_t)L.N * rowb)
+        return fail(CAMELOT_EINVAL, "%zu bytes given, %zu needed", bytes, (size_t)L.N * rowb);
+    std::vector<unsigned char> t((size_t)L.Npad * rowb);
+    if (cudaMemcpy(t.data(), L.w, t.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CAMELOT_ECUDA, "weight read-back failed");
+    // undo the tiling: tile (mt, kb) holds rows 128 mt.. and bytes 128 kb.. of
+    // each row, row r's 16-byte piece j at r * 128 + (j ^ (r % 8)) * 16
+    const size_t KB = rowb / 128;
+    unsigned char* o = (unsigned char*)out;
+    for (int row = 0; row < L.N; ++row) {
+        const int mt = row / 128, r = row % 128;
+        for (size_t kb = 0; kb < KB; ++kb) {
+            const unsigned char* tile = t.data() + ((size_t)mt * KB + kb) * 16384;
+            for (int j = 0; j < 8; ++j)
+                memcpy(o + (size_t)row * rowb + kb * 128 + 16 * j, tile + r * 128 + ((j ^ (r & 7)) * 16), 16);
+        }
+    }
+    if (weight_scale) *weight_scale = st->wscale[layer];
+    return CAMELOT_OK;
+}
 
 extern "C" camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const void* in,
                                                uint32_t n, void* out, int32_t* out_idx,
@@ -671,7 +731,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     if (per_sm < 1 || total > per_sm * sms)
         return fail(CAMELOT_EINVAL, "allocation needs %d SMs, the device offers %d", total, sms * per_sm);
     if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32 &&
-        stages[n_stages - 1]->sp.kind != KIND_GEMM_BF16)
+        !is_tensor_kind(stages[n_stages - 1]->sp.kind))
         return fail(CAMELOT_EINVAL, "logits_sink needs a dense final stage");
 
     auto* p = new camelot_pipeline();
@@ -709,7 +769,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         hp.inst_begin[s] = inst;
         hp.st[s] = stages[s]->sp;
         StageParams tmp = stages[s]->sp;
-        const bool dense = tmp.kind == KIND_MLP_FP32 || tmp.kind == KIND_GEMM_BF16;
+        const bool dense = tmp.kind == KIND_MLP_FP32 || is_tensor_kind(tmp.kind);
         const size_t per = dense ? align_up(layout_scratch(tmp, B), 256) : 0;
         hp.st[s] = tmp;   // scratch offsets laid out for batch B
         hp.inst_scratch[s] = per;

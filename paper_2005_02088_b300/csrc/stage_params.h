@@ -19,7 +19,8 @@ constexpr size_t kSmemBytes = 216 * 1024;  // dynamic shared memory per CTA: > h
                                            // so exactly one CTA fits on an SM
 
 enum StageKind : int32_t { KIND_NORMALIZE_U8 = 1, KIND_NORM_POOL2_BF16 = 2, KIND_MLP_FP32 = 3,
-                           KIND_GEMM_BF16 = 4 };
+                           KIND_GEMM_BF16 = 4, KIND_GEMM_FP8 = 5, KIND_NORMALIZE_U8_E4M3 = 6 };
+__host__ __device__ inline bool is_tensor_kind(int32_t k) { return k == KIND_GEMM_BF16 || k == KIND_GEMM_FP8; }
 enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
 
 // One dense layer in kernel layout.
@@ -29,18 +30,25 @@ enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
 //    whose partial sums are reduced over chunks in chunk order.
 //  - "head" layer (last layer of a final stage with N <= 32): weights row-major
 //    [N][K]; one warp computes a whole query.
-//  - tensor-core layers (GEMM_BF16): weights bf16 in 128 x 64 tiles, tile
-//    (mt, kb) a contiguous 16 KB block at ((mt * K/64) + kb) * 16 KB holding rows
-//    128 mt.. and columns 64 kb.. in the 128-byte-swizzle layout (row r's
-//    16-byte piece j at r * 128 + (j ^ (r % 8)) * 16); rows >= N are zero and
-//    Npad = N rounded up to 128.  K is cut into chunks of KC (a multiple of 64)
-//    whose fp32 partials are reduced in chunk order.
+//  - tensor-core layers (GEMM_BF16, GEMM_FP8): weights bf16 or e4m3 in tiles of
+//    128 rows x 128 bytes (64 bf16 or 128 e4m3 columns); tile (mt, kb) is a
+//    contiguous 16 KB block at ((mt * KB) + kb) * 16 KB, KB = K * esz / 128,
+//    holding rows 128 mt.. and the kb-th 128-byte column block in the
+//    128-byte-swizzle layout (row r's 16-byte piece j at r * 128 + (j ^ (r % 8))
+//    * 16); rows >= N are zero and Npad = N rounded up to 128.  K is cut into
+//    chunks of KC (128 / esz columns at least) whose fp32 partials are reduced
+//    in chunk order.  An output value is act(acc * vscale); FP8 hidden outputs
+//    are stored as e4m3(value / qscale).
 struct LayerParams {
     const float* w;     // device, kernel layout (see above)
     int32_t K, N, Npad;
-    int32_t KC, C;      // K-chunk (multiple of 4) and number of chunks
+    int32_t KC, C;      // K-chunk and number of chunks
     int32_t act;
     int32_t head;       // 1 = head layer
+    int32_t esz;        // tensor-core layers: bytes per element (2 bf16, 1 e4m3)
+    float vscale;       // tensor-core layers: accumulator scale (1 for bf16)
+    float qscale;       // FP8 layers: scale of the output codes (0 = f32 / bf16 output)
+    int32_t pad_;
     size_t p_off;       // scratch offset of this layer's partial sums (task layers)
     size_t h_off;       // scratch offset of its output rows (hidden layers / logits)
 };

@@ -7,6 +7,7 @@
 // the stage is prepared), never by p, so the result of a query is bit-identical
 // whatever the SM quota, the number of instances or the batch it travels in.
 #pragma once
+#include <cuda_fp8.h>
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -90,6 +91,49 @@ static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, 
                 for (int j = 0; j < 4; ++j)
                     __stcg(o + j, make_float4(norm_u8(w[j] & 0xff), norm_u8((w[j] >> 8) & 0xff),
                                               norm_u8((w[j] >> 16) & 0xff), norm_u8(w[j] >> 24)));
+            }
+        }
+    }
+}
+
+// FP8 arm of the normalisation stage: the code of 128 y, y = (x - 127.5) / 64,
+// i.e. e4m3(2 x - 255) (exact in f32, then rounded to nearest even e4m3).  The
+// next stage reads the codes with scale 1/128.  16 input bytes -> 16 codes.
+static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                                           RowRef out) {
+    const uint64_t chunks = P.in_row_bytes / 16;
+    const uint64_t total = (uint64_t)n * chunks;
+    const uint64_t stride = (uint64_t)cx.nctas * kThreads;
+    constexpr int U = 4;
+    for (uint64_t base = (uint64_t)cx.rank * kThreads + threadIdx.x; base < total;
+         base += stride * U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t e = base + u * stride;
+            if (e < total) {
+                const uint64_t q = e / chunks, c = e - q * chunks;
+                v[u] = __ldcs(reinterpret_cast<const uint4*>(in.row(q)) + c);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t e = base + u * stride;
+            if (e < total) {
+                const uint64_t q = e / chunks, c = e - q * chunks;
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                uint32_t o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t packed = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float y128 = ((float)((w[j] >> (8 * b)) & 0xffu) - 127.5f) * 2.0f;
+                        packed |= (uint32_t)__nv_cvt_float_to_fp8(y128, __NV_SATFINITE, __NV_E4M3) << (8 * b);
+                    }
+                    o[j] = packed;
+                }
+                __stcg(reinterpret_cast<uint4*>(out.row(q)) + c, make_uint4(o[0], o[1], o[2], o[3]));
             }
         }
     }
