@@ -65,6 +65,13 @@ WORKLOADS = {
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
+    "fp8-2stage": dict(
+        desc=("plain 2-stage pipeline, FP8 arm: 64x64x3 u8 images -> normalize to e4m3 codes (scale "
+              "1/128) -> MLP 12288-512-256-10 on e4m3 weights and activations (per-tensor scales, f32 "
+              "accumulation, tcgen05 kind::f8f6f4) -> argmax; Poisson arrivals; p99 QoS 20 ms"),
+        batch=16, row=12288, even=([1, 1], [72, 72]), profile_alloc=([2, 16], [8, 8]),
+        flop=2 * (12288 * 512 + 512 * 256 + 256 * 10),
+        bytes=12288 + 2 * 12288, weight_bytes=(12288 * 512 + 512 * 256 + 256 * 10)),
 }
 
 
@@ -202,7 +209,7 @@ COMP_DTYPE = np.dtype({
 class Workload:
     """Stages, device-resident trace data and measurement helpers of one pipeline."""
 
-    def __init__(self, name: str, device: int, n_rows: int = Q_STEP):
+    def __init__(self, name: str, device: int, n_rows: int = Q_STEP, device_rows: int = 0):
         import torch
 
         import synth
@@ -222,6 +229,18 @@ class Workload:
             self.stages.append(pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], top_k=1,
                                               max_batch=32))
             self.io = [(12288, "u8"), (12288 * 4, "f32")]
+        elif name == "fp8-2stage":
+            x, ws = synth.cfg1_inputs(0, n_queries=1024)
+            rows = np.arange(n_rows) % 1024
+            self.xq_host = np.ascontiguousarray(x[rows].reshape(n_rows, -1))
+            wd = [torch.from_numpy(w).cuda() for w in ws]
+            xc = synth.images_u8(0, 64, 64, 64, 3, tag="cfg5.calibration")
+            self.act_scales = pl.calibrate_fp8_scales(wd, xc)
+            scales = [1.0 / 128] + self.act_scales
+            self.stages = [pl.stage_normalize_e4m3(64, 64, 3, max_batch=32),
+                           pl.stage_fp8(wd, [1, 1, 0], scales, top_k=1, max_batch=32)]
+            self.io = [(12288, "u8"), (12288, "e4m3")]
+            self.base_rows = torch.from_numpy(np.ascontiguousarray(x.reshape(1024, -1))).cuda()
         else:
             x, ws = synth.cfg2_inputs(0, n_queries=256)
             rows = np.arange(n_rows) % 256
@@ -238,6 +257,11 @@ class Workload:
         self.xq_pinned = pinned
         self.xq_host = pinned.numpy()
         self.xq = torch.from_numpy(self.xq_host).cuda()        # larger than L2
+        if device_rows:
+            # a long device-resident query buffer: the base images repeated on the device
+            base = self.xq[: min(1024, self.xq.shape[0])]
+            reps = (device_rows + base.shape[0] - 1) // base.shape[0]
+            self.xq = base.repeat(reps, 1)[:device_rows].contiguous()
         self.buf = (cm.Completion * 8192)()
         self._last_total = {}      # per pipeline: summed launch ms already accounted
         torch.cuda.synchronize()
@@ -246,10 +270,10 @@ class Workload:
         for s in self.stages:
             self.cm.camelot_stage_release(s)
 
-    def pipeline(self, mode, inst, quota, data_slots=0, device_data=0):
-        o = self.pl.options(exit_after_trace=1, query_slots=65536, idle_exit_ns=20_000_000,
+    def pipeline(self, mode, inst, quota, data_slots=0, device_data=0, batch=0, query_slots=65536):
+        o = self.pl.options(exit_after_trace=1, query_slots=query_slots, idle_exit_ns=20_000_000,
                             data_slots=data_slots, device_data=device_data)
-        p = self.cm.camelot_pipeline_create(self.stages, self.pl.alloc(inst, quota, self.B), mode, o)
+        p = self.cm.camelot_pipeline_create(self.stages, self.pl.alloc(inst, quota, batch or self.B), mode, o)
         self._last_total[p] = 0.0
         return p
 
@@ -289,10 +313,10 @@ class Workload:
         lat = (comps["t_done"] - comps["t_arrival"])[skip:]
         return float(np.percentile(lat, 99)), float(np.percentile(lat, 50))
 
-    def peak(self, mode, inst, quota, iters=9, seed=1):
+    def peak(self, mode, inst, quota, iters=9, seed=1, batch=0):
         """Bisection on the Poisson rate; returns (rate, pipeline, saturation)."""
         import synth
-        p = self.pipeline(mode, inst, quota)
+        p = self.pipeline(mode, inst, quota, batch=batch)
         comps, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
         sat = {"qps": Q_STEP / (ms * 1e-3), "launch_ms": ms, "queries": Q_STEP,
                "p50_ms": self.p99(comps)[1] * 1e-6}
@@ -434,6 +458,59 @@ class Workload:
                               0.0, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
         a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
         return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)], obj
+
+
+    def profile_batches(self, batches, runs=20):
+        """Solo-run p99 duration (s) of one batch of every stage at every 8-SM
+        quota and batch size: [n_batches][n_stages][n_levels], by
+        camelot_stage_time (CUDA events between back-to-back launches)."""
+        torch, cm = self.torch, self.cm
+        levels = list(range(8, (self.sms // 8) * 8 + 1, 8))
+        Bmax = max(batches)
+        bufs = [torch.zeros(Bmax * nb, dtype=torch.uint8, device="cuda") for (nb, _) in self.io[1:]]
+        idx = torch.empty((Bmax, 5), dtype=torch.int32, device="cuda")
+        val = torch.empty((Bmax, 5), dtype=torch.float32, device="cuda")
+        dur = np.zeros((len(batches), len(self.stages), len(levels)))
+        stream = torch.cuda.current_stream().cuda_stream
+        for si, st in enumerate(self.stages):
+            _, _, sb = cm.camelot_stage_info(st, Bmax)
+            scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+            inp = self.xq if si == 0 else bufs[si - 1]
+            last = si == len(self.stages) - 1
+            out = None if last else bufs[si]
+            for bi, B in enumerate(batches):
+                for li, pq in enumerate(levels):
+                    args = (st, pq, inp, B, out, idx if last else None, val if last else None, None, scr, sb,
+                            stream)
+                    cm.camelot_stage_time(*args, runs=2)
+                    ms = cm.camelot_stage_time(*args, runs=runs)
+                    dur[bi, si, li] = float(np.percentile(ms, 99)) * 1e-3
+        return levels, dur
+
+    def alloc_table(self, levels, batches, dur):
+        """camelot_profile of Table 2 quantities from a duration table."""
+        cm = self.cm
+        n, L, nb = len(self.stages), len(levels), len(batches)
+        Bv = np.array(batches, np.float64)[:, None, None]
+        f = np.ascontiguousarray(Bv / dur, np.float64)
+        by = np.array([[B * (self.io[si][0] + (self.io[si + 1][0] if si + 1 < len(self.io) else 40))
+                        for si in range(n)] for B in batches], np.float64)[:, :, None]
+        bw = np.ascontiguousarray(by / dur / 1e9, np.float64)
+        d = np.ascontiguousarray(dur, np.float64)
+        mem = np.ascontiguousarray(np.full((nb, n), 64e6), np.float64)
+        bs = np.array(batches, np.int32)
+        keep = (f, bw, d, mem, bs)
+        pr = cm.Profile(n, L, nb, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, d.ctypes.data,
+                        mem.ctypes.data)
+        return pr, keep
+
+    def solve(self, pr, policy, load=0.0, qos_s=QOS_NS * 1e-9):
+        cm = self.cm
+        cons = cm.Constraints(self.sms, self.sms // 8, _peaks().get("hbm_gbs", 6400.0), 200e9, qos_s,
+                              load, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
+        a, obj = cm.camelot_allocate(pr, policy, cons)
+        n = len(self.stages)
+        return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)], a.batch, obj
 
 
 def measure_workload(name, args, local, headline: bool):
@@ -627,6 +704,121 @@ def run_predictor(args):
     return 0
 
 
+def run_diurnal(args):
+    """Low-load resource minimisation (Eq. 3, Sec. 8.2-8.3) on the FP8 arm of the
+    plain 2-stage pipeline: a diurnal day of sinusoidal Poisson arrivals from 10 %
+    to 100 % of the measured peak, compressed into `--diurnal` seconds and cut
+    into 60 windows; per window camelot_allocate (MIN_SM) picks the fewest SMs
+    whose profiled throughput, scaled by the measured efficiency of the peak
+    allocation, covers the window's highest rate with 15 % headroom; the pipeline
+    is rebuilt when the allocation changes and the window's arrivals replay on
+    the device clock.  The same windows replay on the static peak allocation
+    (Eq. 1).  value = 1 - SM-time(Eq. 3) / SM-time(static)."""
+    import torch
+    import synth
+    T = float(args.diurnal)
+    nwin = 60
+    W = T / nwin
+    cm = None
+    wl = Workload("fp8-2stage", 0)
+    cm = wl.cm
+    try:
+        batches = [8, 16, 32]
+        levels, dur = wl.profile_batches(batches)
+        pr, keep = wl.alloc_table(levels, batches, dur)
+        inst_p, quota_p, B_p, obj_p = wl.solve(pr, cm.POLICY_MAX_PEAK)
+        lam_peak, p, sat = wl.peak(0, inst_p, quota_p, batch=B_p)
+        cm.camelot_pipeline_destroy(p)
+        lam_hs, p, _ = wl.peak(1, inst_p, quota_p, batch=B_p)
+        cm.camelot_pipeline_destroy(p)
+        eff = lam_peak / obj_p
+        arrivals = synth.diurnal_arrivals_ns(7, lam_peak, T)
+        edges = (np.arange(nwin + 1) * W * 1e9).astype(np.int64)
+        counts = np.diff(np.searchsorted(arrivals, edges))
+        rows = int(counts.max()) + 64
+        slots = 1 << max(16, int(np.ceil(np.log2(rows))))
+        base = wl.xq[:1024]
+        wl.xq = base.repeat((rows + 1023) // 1024, 1)[:rows].contiguous()
+        torch.cuda.synchronize()
+
+        def rate(t):
+            return lam_peak * (0.55 - 0.45 * np.cos(2 * np.pi * t / T))
+
+        def replay(choose):
+            out, cur, p = [], None, None
+            try:
+                for w in range(nwin):
+                    inst, quota, B = choose(w)
+                    if (inst, quota, B) != cur:
+                        if p is not None:
+                            cm.camelot_pipeline_destroy(p)
+                        # trace replays only: a minimal host data ring
+                        p = wl.pipeline(0, inst, quota, batch=B, query_slots=slots, data_slots=64)
+                        cur = (inst, quota, B)
+                    seg = arrivals[(arrivals >= edges[w]) & (arrivals < edges[w + 1])] - edges[w]
+                    if len(seg) == 0:
+                        out.append({"window": w, "queries": 0, "sms": sum(i * q for i, q in zip(inst, quota))})
+                        continue
+                    comps, ms = wl.trace(p, seg)
+                    lat = comps["t_done"] - comps["t_arrival"]
+                    out.append({"window": w, "queries": int(len(seg)), "offered_qps": len(seg) / W,
+                                "sms": sum(i * q for i, q in zip(inst, quota)), "batch": B,
+                                "instances": inst, "sm_quota": quota,
+                                "p99_ms": float(np.percentile(lat, 99)) * 1e-6,
+                                "p50_ms": float(np.percentile(lat, 50)) * 1e-6})
+            finally:
+                if p is not None:
+                    cm.camelot_pipeline_destroy(p)
+            return out
+
+        def dynamic(w):
+            t0, t1 = w * W, (w + 1) * W
+            lam = max(rate(t0), rate(t1), rate(min(max(T / 2, t0), t1)))
+            load = lam * 1.15 / eff
+            if load >= obj_p:
+                return inst_p, quota_p, B_p       # the peak windows keep the peak allocation
+            try:
+                inst, quota, B, _ = wl.solve(pr, cm.POLICY_MIN_SM, load)
+            except cm.CamelotError:
+                return inst_p, quota_p, B_p
+            return inst, quota, B
+
+        with ClockSampler(0) as clk:
+            dyn = replay(dynamic)
+            stat = replay(lambda w: (inst_p, quota_p, B_p))
+    finally:
+        wl.close()
+    sm_dyn = sum(r["sms"] for r in dyn) * W
+    sm_stat = sum(r["sms"] for r in stat) * W
+    viol_d = sum(1 for r in dyn if r.get("p99_ms", 0) > QOS_NS * 1e-6)
+    viol_s = sum(1 for r in stat if r.get("p99_ms", 0) > QOS_NS * 1e-6)
+    line = {
+        "metric": "SM-time saved by the Eq. 3 low-load allocation vs the static Eq. 1 peak allocation, "
+                  "diurnal load at p99<=QoS (FP8 2-stage pipeline)",
+        "value": 1.0 - sm_dyn / sm_stat, "unit": "fraction of the static allocation's SM-seconds",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "e4m3", "data": "synthetic",
+        "config": {"workload": WORKLOADS["fp8-2stage"]["desc"],
+                   "load": f"rate peak*(0.55-0.45cos(2 pi t/{T:g} s)): 10%..100% of the measured peak, "
+                           f"{nwin} windows of {W:g} s (the paper's 600 s day and 10 s windows, "
+                           f"compressed {600 / T:g}x)",
+                   "qos_p99_ms": QOS_NS / 1e6, "batches": batches},
+        "peak_qps": lam_peak, "peak_qps_host_staged": lam_hs, "saturation_qps": sat["qps"],
+        "static_alloc": {"instances": inst_p, "sm_quota": quota_p, "batch": B_p,
+                         "predicted_min_thr_qps": obj_p},
+        "allocator_efficiency": eff,
+        "sm_seconds": {"eq3": sm_dyn, "static": sm_stat},
+        "qos_violating_windows": {"eq3": viol_d, "static": viol_s},
+        "p99_ms_max": {"eq3": max(r.get("p99_ms", 0) for r in dyn),
+                       "static": max(r.get("p99_ms", 0) for r in stat)},
+        "queries": int(sum(r["queries"] for r in dyn)),
+        "windows_eq3": dyn, "windows_static": stat,
+        "profile_p99_ms": {"levels": levels, "batches": batches, "stage_batch_ms": (dur * 1e3).round(4).tolist()},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Small self-contained case for ncu: two saturated 2,000-query launches."""
     wl = Workload(args.workload, 0, n_rows=2000)
@@ -653,6 +845,8 @@ def main():
                     help="run the latency-predictor study (profiling, GPU training, allocation) instead")
     ap.add_argument("--pred-samples", type=int, default=20000)
     ap.add_argument("--pred-runs", type=int, default=100)
+    ap.add_argument("--diurnal", type=float, default=0.0,
+                    help="run the diurnal low-load study over this many seconds (60 = the compressed day)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -662,6 +856,8 @@ def main():
         return run_profile_case(args)
     if args.predictor:
         return run_predictor(args)
+    if args.diurnal > 0:
+        return run_diurnal(args)
     dist = None
     if world > 1:
         import torch

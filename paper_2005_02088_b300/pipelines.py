@@ -47,6 +47,70 @@ def stage_dense(kind: int, weights, acts, top_k: int, max_batch: int) -> int:
     return cm.camelot_stage_prepare(d)
 
 
+def stage_normalize_e4m3(H: int, W: int, Cc: int, max_batch: int) -> int:
+    d = cm.StageDesc()
+    d.kind = cm.STAGE_NORMALIZE_U8_E4M3
+    d.dims[0], d.dims[1], d.dims[2] = H, W, Cc
+    d.max_batch = max_batch
+    return cm.camelot_stage_prepare(d)
+
+
+def stage_fp8(weights, acts, scales, top_k: int, max_batch: int) -> int:
+    """GEMM_FP8 chain from f32 device tensors ``weights[l]`` [out, in] (quantised
+    to e4m3 by the library); ``scales[l]`` is layer l's input scale and, for an
+    intermediate stage, ``scales[n_layers]`` its output scale."""
+    d = cm.StageDesc()
+    d.kind = cm.STAGE_GEMM_FP8
+    d.n_layers = len(weights)
+    d.dims[0] = weights[0].shape[1]
+    for i, w in enumerate(weights):
+        assert w.is_cuda and w.is_contiguous() and w.dtype == torch.float32
+        d.dims[i + 1] = w.shape[0]
+        d.act[i] = acts[i]
+        d.weights[i] = w.data_ptr()
+    for i, sc in enumerate(scales):
+        d.scales[i] = float(sc)
+    d.top_k = top_k
+    d.max_batch = max_batch
+    torch.cuda.synchronize()
+    return cm.camelot_stage_prepare(d)
+
+
+def calibrate_fp8_scales(weights, images_u8: np.ndarray, n_ctas: int = 16) -> list:
+    """Static activation scales of the FP8 arm for a ReLU MLP behind the u8
+    normalisation: max |input of layer l| / 448 (l >= 1) over calibration images,
+    with the activations computed by the library's FP32 stages, one layer at a
+    time.  Returns [s_1, ..., s_{L-1}]."""
+    n = images_u8.shape[0]
+    H, W, Cc = images_u8.shape[1:4]
+    x = torch.from_numpy(np.ascontiguousarray(images_u8.reshape(n, -1))).cuda()
+    s0 = stage_normalize(H, W, Cc, n)
+    stages = [s0]
+    try:
+        y = torch.empty((n, H * W * Cc), dtype=torch.float32, device="cuda")
+        _run_stage(s0, x, n, y, n_ctas)
+        scales = []
+        for w in weights[:-1]:
+            st = stage_dense(cm.STAGE_MLP_FP32, [w], [cm.ACT_RELU], top_k=0, max_batch=n)
+            stages.append(st)
+            h = torch.empty((n, w.shape[0]), dtype=torch.float32, device="cuda")
+            _run_stage(st, y, n, h, n_ctas)
+            torch.cuda.synchronize()
+            scales.append(float(np.float32(np.abs(h.cpu().numpy()).max() / 448.0)))
+            y = h
+        return scales
+    finally:
+        for st in stages:
+            cm.camelot_stage_release(st)
+
+
+def _run_stage(st: int, inp, n: int, out, n_ctas: int) -> None:
+    _, _, sb = cm.camelot_stage_info(st, n)
+    scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+    cm.camelot_stage_launch(st, n_ctas, inp, n, out, None, None, None, scr, sb, None)
+    torch.cuda.synchronize()
+
+
 def alloc(instances, quotas, batch: int) -> cm.Alloc:
     a = cm.Alloc()
     a.n_stages = len(instances)
