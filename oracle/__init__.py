@@ -65,6 +65,7 @@ def _declare(L):
         "orc_bf16_bits": (None, [P, I64, P]),
         "orc_round_e4m3": (None, [P, I64, P]),
         "orc_e4m3_decode": (None, [P, I64, P]),
+        "orc_embed_gather": (None, [P, I64, P, C.c_int, C.c_int, P]),
         "orc_quantize_e4m3": (C.c_double, [P, I64, P]),
         "orc_linear_fp8": (None, [P, I64, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_double, P, P, P]),
         "orc_pipeline_mlp": (None, [P, I64, P, P, P, P, P, P, C.c_int]),
@@ -235,6 +236,34 @@ def pipeline_fp8(x_u8: np.ndarray, ws, act_scales):
             return y, argmax(y), hidden, sws
         hidden.append(yq)
         xq = yq
+
+
+def embed_gather(tokens, E) -> np.ndarray:
+    """Rows E[token] (zero rows for padding / out-of-range IDs); tokens [..., T]."""
+    t = np.ascontiguousarray(tokens, dtype=np.int32)
+    E = _f64(E)
+    out = np.empty(t.shape + (E.shape[1],), np.float64)
+    lib().orc_embed_gather(_p(t), t.size, _p(E), E.shape[0], E.shape[1], _p(out))
+    return out
+
+
+def pipeline_text(tokens, E, ws, emulate_bf16: bool = False):
+    """Text-tagging pipeline on padded token queries [n, T]: e = E[tok],
+    h = gelu(W1 e), g = W2 h, z = W3 g, tag = argmax of z per token.  With
+    emulate_bf16 the embedding table and weights are rounded to bfloat16 and so
+    are h and g (the logits stay unrounded), as the BF16 GEMM stages round.
+    Returns (logits [n, T, 64], tags [n, T])."""
+    t = np.ascontiguousarray(tokens, dtype=np.int32)
+    n, T = t.shape
+    r = (lambda a: round_bf16(a)) if emulate_bf16 else (lambda a: _f64(a))
+    e = embed_gather(t, r(E)).reshape(n * T, -1)
+    w1, w2, w3 = (r(w) for w in ws)
+    h = linear(e, w1, ACT_GELU)
+    h = r(h) if emulate_bf16 else h
+    g = linear(h, w2, ACT_NONE)
+    g = r(g) if emulate_bf16 else g
+    z = linear(g, w3, ACT_NONE)
+    return z.reshape(n, T, -1), argmax(z).reshape(n, T)
 
 
 def pipeline_mlp(x_u8: np.ndarray, ws, nthreads: int = 0):

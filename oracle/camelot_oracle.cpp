@@ -244,6 +244,15 @@ void orc_linear_fp8(const double* xq, int64_t nq, int K, const double* wq, int N
         }
 }
 
+// Embedding gather of the text-tagging microservice: row t of query q is
+// E[tok[q, t]] for 0 <= tok < V, and a zero row for padding (any other ID).
+void orc_embed_gather(const int32_t* tok, int64_t n_rows, const double* E, int V, int D, double* out) {
+    for (int64_t r = 0; r < n_rows; ++r) {
+        const int32_t t = tok[r];
+        for (int d = 0; d < D; ++d) out[r * D + d] = (t >= 0 && t < V) ? E[(int64_t)t * D + d] : 0.0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 2. Whole-pipeline references
 // ---------------------------------------------------------------------------

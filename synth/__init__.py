@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "rng", "images_u8", "dense_weights", "mlp_weights", "zipf_tokens",
-    "poisson_arrivals_ns", "diurnal_arrivals_ns", "CFG1", "CFG2", "CFG3", "CFG4",
+    "poisson_arrivals_ns", "diurnal_arrivals_ns", "CFG1", "CFG2", "CFG3", "CFG4", "cfg4_inputs",
     "cfg1_inputs", "cfg2_inputs",
 ]
 
@@ -111,3 +111,20 @@ def cfg2_inputs(seed: int = 0, n_queries: int = 64):
     x = images_u8(seed, n_queries, CFG2["H"], CFG2["W"], CFG2["C"], tag="cfg2.images")
     ws = mlp_weights(seed, CFG2["dims"], tag="cfg2")
     return x, ws
+
+
+def cfg4_inputs(seed: int = 0, n_queries: int = 64, seq_max: int = 128):
+    """Text-tagging pipeline inputs: token queries padded to ``seq_max`` int32
+    IDs (-1 = padding; Zipf s = 1.1 over 32000 IDs, lengths uniform in 16..128),
+    their lengths, the embedding table [32000, 512] N(0, 1) and the three weight
+    matrices 512->2048->512->64 N(0, 1/fan_in), all float32."""
+    c = CFG4
+    toks = zipf_tokens(seed, n_queries, c["vocab"], c["zipf_s"], c["seq"][0], c["seq"][1],
+                       tag="cfg4.tokens")
+    padded = np.full((n_queries, seq_max), -1, np.int32)
+    lens = np.array([len(t) for t in toks], np.int32)
+    for i, t in enumerate(toks):
+        padded[i, : len(t)] = t
+    E = rng(seed, "cfg4.embedding").standard_normal((c["vocab"], c["d_model"])).astype(np.float32)
+    ws = mlp_weights(seed, (c["d_model"], c["d_ff"], c["d_model"], c["n_tags"]), tag="cfg4")
+    return padded, lens, E, ws
