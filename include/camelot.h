@@ -85,14 +85,24 @@ int camelot_version(void);
  *                    for the last layer of a final stage.  Widths dims[0..L-1]
  *                    multiples of 128; batches of at most 32.
  *   NORMALIZE_U8_E4M3: u8 image -> e4m3 codes of 128 y (y as NORMALIZE_U8), i.e.
- *                    e4m3(2 x - 255): the next stage reads them with scale 1/128. */
+ *                    e4m3(2 x - 255): the next stage reads them with scale 1/128.
+ *   EMBED_GATHER   : int32 token IDs [T] -> bf16 rows [T][D], row t = E[tok[t]] for
+ *                    0 <= tok < V and zero for any other ID (padding).  dims =
+ *                    {V, D, T}, D a multiple of 8; weights[0] = E, bf16 [V][D].
+ * Token-level tensor-core stages: a GEMM_BF16 / GEMM_FP8 stage with
+ * rows_per_query T > 1 treats each query as T rows (its input row is T x
+ * dims[0] elements) and runs the dense chain on every row; a final such stage
+ * must have top_k = 1 and emits the argmax of every row (a tag per token):
+ * result arrays hold the tags and maxima of the first min(T, 5) rows, and the
+ * logits output / logits_sink row of a query holds its T tags as int32. */
 typedef enum {
     CAMELOT_STAGE_NORMALIZE_U8 = 1,
     CAMELOT_STAGE_NORM_POOL2_BF16 = 2,
     CAMELOT_STAGE_MLP_FP32 = 3,
     CAMELOT_STAGE_GEMM_BF16 = 4,
     CAMELOT_STAGE_GEMM_FP8 = 5,
-    CAMELOT_STAGE_NORMALIZE_U8_E4M3 = 6
+    CAMELOT_STAGE_NORMALIZE_U8_E4M3 = 6,
+    CAMELOT_STAGE_EMBED_GATHER = 7
 } camelot_stage_kind;
 
 typedef enum { CAMELOT_ACT_NONE = 0, CAMELOT_ACT_RELU = 1, CAMELOT_ACT_GELU = 2 } camelot_act;
@@ -118,6 +128,8 @@ typedef struct {
                                            layer l's input codes; scales[n_layers] that of
                                            an intermediate stage's output codes (static
                                            scales, calibrated by the caller) */
+    int32_t rows_per_query;             /* tensor-core kinds: rows per query (0 or 1 = one;
+                                           T > 1 = token-level, see above); else 0 */
 } camelot_stage_desc;
 
 /* A prepared stage: validated descriptor plus the library's own copy of its
@@ -151,10 +163,12 @@ camelot_status camelot_stage_info(const camelot_stage* st, size_t* in_row_bytes,
  * stream).
  *   in      device, n * in_row_bytes, rows contiguous.
  *   out     device, n * out_row_bytes (intermediate stages), else may be NULL.
- *   out_idx device int32 [n][top_k] (final stages), else NULL.
- *   out_val device f32   [n][top_k] (final stages), else NULL.
+ *   out_idx device int32 [n][k] (final stages), else NULL; k = top_k, or
+ *           min(T, 5) for a token-level stage.
+ *   out_val device f32   [n][k] (final stages), else NULL.
  *   out_logits device f32 [n][dims[n_layers]] or NULL: the final layer's
- *           output before top-k (dense kinds only).
+ *           output before top-k (dense kinds only); int32 [n][T] tags for a
+ *           token-level stage.
  *   scratch device, >= camelot_stage_info(...) bytes, 256-byte aligned; the
  *           call clears what must start at zero.
  * Errors: EINVAL (n = 0 or > max_batch, n_ctas outside 1..SM count, missing

@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, ECUDA, ESTATE, EINFEASIBLE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EAGAIN", "ETIMEDOUT", "ECUDA", "ESTATE", "EINFEASIBLE"]
 
 STAGE_NORMALIZE_U8, STAGE_NORM_POOL2_BF16, STAGE_MLP_FP32, STAGE_GEMM_BF16 = 1, 2, 3, 4
-STAGE_GEMM_FP8, STAGE_NORMALIZE_U8_E4M3 = 5, 6
+STAGE_GEMM_FP8, STAGE_NORMALIZE_U8_E4M3, STAGE_EMBED_GATHER = 5, 6, 7
 ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
 HANDOFF_GLOBAL, HANDOFF_HOST_STAGED = 0, 1
 POLICY_MAX_PEAK, POLICY_MIN_SM = 0, 1
@@ -35,7 +35,8 @@ class CamelotError(RuntimeError):
 class StageDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
                 ("act", C.c_int32 * MAX_LAYERS), ("top_k", C.c_int32), ("max_batch", C.c_int32),
-                ("weights", C.c_void_p * MAX_LAYERS), ("scales", C.c_float * (MAX_LAYERS + 1))]
+                ("weights", C.c_void_p * MAX_LAYERS), ("scales", C.c_float * (MAX_LAYERS + 1)),
+                ("rows_per_query", C.c_int32)]
 
 
 class Alloc(C.Structure):

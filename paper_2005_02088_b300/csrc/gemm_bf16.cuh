@@ -164,20 +164,23 @@ __device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, S
     return true;
 }
 
-// One layer.  Work units u = (chunk c, 128-row tile mt) in chunk-major order
-// (u = c * MT + mt); CTA r takes the contiguous units [r U / p, (r+1) U / p).
+// One layer over `rows` input rows (queries, or tokens of a token-level
+// stage), taken 32 at a time.  Work units u = (row tile rt, chunk c, 128-row
+// weight tile mt) in that order (u = (rt * C + c) * MT + mt); CTA r takes the
+// contiguous units [r U / p, (r+1) U / p).
 // Every unit accumulates the same K range in the same MMA order, issued by
 // one thread into one accumulator, whichever CTA or issuer runs it.  Each ring
 // stage carries two consecutive weight tiles (one 32 KB bulk copy: the copy
 // engine's cost is per operation, so larger copies stream faster; kept in L2
 // with the evict-last policy) and the matching query tiles (cp.async by the
 // loader warp, 128-byte swizzle).
-static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
+static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int rows,
                                         float* Pbuf, const LayerOut& direct) {
     const GemmSmem g = gemm_smem(cx.smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int MT = L.Npad / 128;
-    const int U = MT * L.C;
+    const int CM = MT * L.C;                        // units per row tile
+    const int U = CM * ((rows + kGemmN - 1) / kGemmN);
     const int u0 = (int)((long long)cx.rank * U / cx.nctas);
     const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
     const uint32_t ring0 = *g.ring_it;
@@ -188,7 +191,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     // k-blocks are 128 bytes wide: 64 bf16 or 128 e4m3 columns
     auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) * L.esz / 128; };
     const size_t kc_bytes = (size_t)L.KC * L.esz;
-    auto stages_of = [&](int u) { return (chunk_kb(u / MT) + kKbPerStage - 1) / kKbPerStage; };
+    auto chunk_of = [&](int u) { return (u % CM) / MT; };
+    auto stages_of = [&](int u) { return (chunk_kb(chunk_of(u)) + kKbPerStage - 1) / kKbPerStage; };
     // accumulator of the unit that is issuer w's k-th (counting all its
     // earlier units): two per issuer, alternating
     auto acc_of = [&](int w, uint32_t k) { return 2 * w + (int)(k & 1u); };
@@ -201,7 +205,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             const char* wt = reinterpret_cast<const char*>(L.w);
             const int KB = L.K * L.esz / 128;            // weight tiles per 128-row block
             for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
-                const int c = u / MT, mt = u - c * MT;
+                const int c = chunk_of(u), mt = u % MT;
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, chunk_kb(c) - kb);
                 const int s = gi % kGemmStages;
@@ -217,28 +221,34 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
         } else if (warp == kWarpB) {
             // query tiles: 32 rows x 128 bytes, 16-byte piece j of row r at
             // r * 128 + ((j ^ (r & 7)) * 16).  Lane l always copies piece
-            // j = l % 8 of rows r = l / 8 + 4 i (i < 8): its source rows and
-            // destination offsets are fixed for the layer.  Each lane's cp.async
-            // completion arrives on the stage's full barrier by itself, so the
-            // loader runs as far ahead as the ring allows.
+            // j = l % 8 of rows r = l / 8 + 4 i (i < 8) of the unit's row tile.
+            // Each lane's cp.async completion arrives on the stage's full
+            // barrier by itself, so the loader runs as far ahead as the ring
+            // allows.
             const int jj = lane & 7;
-            const char* src_row[8];
-            uint32_t dst_off[8], src_bytes[8];
+            uint32_t dst_off[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = (lane >> 3) + 4 * i;
-                src_row[i] = x.row(r < n ? r : 0) + 16 * jj;
-                src_bytes[i] = r < n ? 16u : 0u;
                 dst_off[i] = (uint32_t)(r * 128 + ((jj ^ (r & 7)) << 4));
             }
             for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
-                const int c = u / MT;
+                const int c = chunk_of(u);
+                const int row0 = (u / CM) * kGemmN;
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, chunk_kb(c) - kb);
                 const int s = gi % kGemmStages;
                 if (gi >= (uint32_t)kGemmStages &&
                     !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 2))
                     return false;
+                const char* src_row[8];
+                uint32_t src_bytes[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = row0 + (lane >> 3) + 4 * i;
+                    src_row[i] = x.row(r < rows ? r : 0) + 16 * jj;
+                    src_bytes[i] = r < rows ? 16u : 0u;
+                }
                 char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
                 for (int t = 0; t < nk; ++t) {
                     char* dst = dstb + t * kBTileBytes;
@@ -259,7 +269,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const int ns = stages_of(u);
                 if (j == 0 && k >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((k >> 1) - 1) & 1, cx, 4))
                     return false;
-                const int c = u / MT;
+                const int c = chunk_of(u);
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, chunk_kb(c) - kb);
                 const int s = gi % kGemmStages;
@@ -316,7 +326,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             for (int u = u0; u < u1; ++u) {
                 const int w = (u - u0) & 1;
                 const uint32_t k = kw[w]++;
-                const int c = u / MT, mt = u - c * MT;
+                const int c = chunk_of(u), mt = u % MT;
+                const int row0 = (u / CM) * kGemmN;
                 const int acc = acc_of(w, k);
                 if (!mbar_wait_bounded(&g.tfull[acc], (k >> 1) & 1, cx, 6)) break;
                 tc_fence_after();
@@ -332,10 +343,10 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 if (m < L.N) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        if (j < n) {
+                        if (row0 + j < rows) {
                             const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                            if (L.C == 1) store_out(direct, j, m, v);
-                            else __stcg(Pbuf + ((size_t)c * n + j) * L.Npad + m, v);
+                            if (L.C == 1) store_out(direct, row0 + j, m, v);
+                            else __stcg(Pbuf + ((size_t)c * rows + row0 + j) * L.Npad + m, v);
                         }
                     }
                 }
@@ -404,9 +415,18 @@ static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int
 // The whole GEMM_BF16 / GEMM_FP8 stage.  Hidden rows and the rows handed to
 // the next stage are bf16 (GEMM_BF16) or e4m3 codes (GEMM_FP8); a final stage
 // keeps its logits in f32.
+// Rows of a token-level stage: the T rows of query q follow each other in its
+// query row, so row r of a contiguous batch is at base + r * (stride / T).
+__device__ __forceinline__ RowRef token_rows(const RowRef& q, int T) {
+    return RowRef{q.base + q.first * q.stride, 0, ~0ull, q.stride / (size_t)T};
+}
+
 static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                  RowRef out, const FinalOut& fo) {
-    RowRef x = in;
+    const int T = P.rows;
+    const int rows = n * T;
+    RowRef x = T > 1 ? token_rows(in, T) : in;
+    if (T > 1 && out.base != nullptr) out = token_rows(out, T);
     const int hfmt = P.kind == KIND_GEMM_FP8 ? OUT_E4M3 : OUT_BF16;
     const size_t hsz = P.kind == KIND_GEMM_FP8 ? 1 : 2;
     for (int l = 0; l < P.n_layers; ++l) {
@@ -423,14 +443,17 @@ static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRe
                          L.qscale};
         }
         float* Pbuf = reinterpret_cast<float*>(cx.scratch + L.p_off);
-        if (!gemm_layer_tasks(cx, L, x, n, Pbuf, o)) return false;
+        if (!gemm_layer_tasks(cx, L, x, rows, Pbuf, o)) return false;
         if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         if (L.C > 1) {
-            gemm_reduce(cx, L, n, Pbuf, o);
+            gemm_reduce(cx, L, rows, Pbuf, o);
             if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         }
         x = o.rows;
-        if (last && P.top_k > 0) topk_rows(cx, x, n, L.N, P.top_k, fo);
+        if (last && P.top_k > 0) {
+            if (T > 1) token_argmax(cx, x, n, T, L.N, P.res_k, fo);
+            else topk_rows(cx, x, n, L.N, P.top_k, fo);
+        }
     }
     return true;
 }

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                 __shared__ long long sh_done;
                 if (threadIdx.x == 0) sh_done = (long long)gtime();
                 __syncthreads();
-                const int k = SP.top_k;
+                const int k = SP.res_k;
                 for (int q = threadIdx.x; q < n; q += kThreads) {
                     CompSlot& cs = P.comp[(first + q) & P.cmask];
                     for (int r = 0; r < kMaxTopK; ++r) {

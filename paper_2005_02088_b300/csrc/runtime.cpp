@@ -119,8 +119,9 @@ static size_t layout_scratch(StageParams& sp, int B) {
     for (int l = 0; l < sp.n_layers; ++l) {
         LayerParams& L = sp.layer[l];
         if (is_tensor_kind(sp.kind)) {
-            if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * B * L.Npad * sizeof(float));
-            h_bytes = std::max(h_bytes, (size_t)B * L.Npad * sizeof(float));
+            const size_t rows = (size_t)B * std::max(1, sp.rows);
+            if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * rows * L.Npad * sizeof(float));
+            h_bytes = std::max(h_bytes, rows * L.Npad * sizeof(float));
             continue;
         }
         const size_t G = (L.C + kWarps - 1) / kWarps;    // chunk groups
@@ -156,6 +157,8 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
     sp.kind = d->kind;
     sp.top_k = d->top_k;
     sp.max_batch = d->max_batch;
+    sp.rows = 1;
+    sp.res_k = d->top_k;
     auto* st = new camelot_stage();
     st->desc = *d;
     cudaGetDevice(&st->device);
@@ -238,6 +241,13 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             const bool f8 = d->kind == CAMELOT_STAGE_GEMM_FP8;
             const int esz = f8 ? 1 : 2;
             const int L = d->n_layers;
+            const int T = std::max(1, d->rows_per_query);
+            if (T > 1 && d->top_k > 1)
+                return bail(fail(CAMELOT_EINVAL, "a token-level final stage emits argmax tags: top_k must be 1"));
+            if ((size_t)T * d->max_batch > 8192)
+                return bail(fail(CAMELOT_EINVAL, "rows_per_query x max_batch exceeds 8192 rows"));
+            sp.rows = T;
+            sp.res_k = T > 1 && d->top_k ? std::min(T, kMaxTopK) : d->top_k;
             if (L < 1 || L > kMaxLayers) return bail(fail(CAMELOT_EINVAL, "n_layers %d outside 1..4", L));
             if (d->max_batch > 32) return bail(fail(CAMELOT_EINVAL, "tensor-core stages take batches of at most 32"));
             for (int l = 0; l <= L; ++l)
@@ -257,15 +267,16 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             if (!d->top_k && d->dims[L] % 8)
                 return bail(fail(CAMELOT_EINVAL, "an intermediate stage's output width must be a multiple of 8"));
             sp.n_layers = L;
-            sp.in_row_bytes = (size_t)d->dims[0] * esz;
-            sp.out_row_bytes = d->top_k ? 0 : (size_t)d->dims[L] * esz;
-            sp.out_width = d->dims[L];
+            sp.in_row_bytes = (size_t)T * d->dims[0] * esz;
+            sp.out_row_bytes = d->top_k ? 0 : (size_t)T * d->dims[L] * esz;
+            sp.out_width = T > 1 ? T : d->dims[L];   // token-level: the sink row holds T tags
             for (int l = 0; l < L; ++l) {
                 LayerParams& Lp = sp.layer[l];
                 const int K = d->dims[l], N = d->dims[l + 1];
                 Lp.K = K; Lp.N = N; Lp.act = d->act[l]; Lp.head = 0;
                 Lp.Npad = (N + 127) / 128 * 128;
-                Lp.KC = choose_kc_gemm(K);
+                // token-level stages have row tiles enough to fill the SMs: no split-K
+                Lp.KC = T > 1 ? K : choose_kc_gemm(K);
                 Lp.C = (K + Lp.KC - 1) / Lp.KC;
                 Lp.esz = esz;
                 Lp.vscale = 1.f;
@@ -311,6 +322,25 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                 Lp.w = (const float*)dp;
             }
             sp.scratch_bytes = layout_scratch(sp, d->max_batch);
+            break;
+        }
+        case CAMELOT_STAGE_EMBED_GATHER: {
+            const int V = d->dims[0], D = d->dims[1], T = d->dims[2];
+            if (V <= 0 || D <= 0 || T <= 0 || D % 8)
+                return bail(fail(CAMELOT_EINVAL, "EMBED_GATHER dims {V, D, T}: positive, D a multiple of 8"));
+            if (d->top_k != 0) return bail(fail(CAMELOT_EINVAL, "an embedding stage cannot be final"));
+            if (!d->weights[0]) return bail(fail(CAMELOT_EINVAL, "weights[0] (the table) is null"));
+            sp.H = V; sp.W = D; sp.rows = T;
+            sp.in_row_bytes = (size_t)T * 4;
+            sp.out_row_bytes = (size_t)T * D * 2;
+            void* tab = nullptr;
+            if (cudaMalloc(&tab, (size_t)V * D * 2) != cudaSuccess)
+                return bail(fail(CAMELOT_ENOMEM, "table copy allocation failed"));
+            st->allocs.push_back(tab);
+            if (cudaMemcpy(tab, d->weights[0], (size_t)V * D * 2, cudaMemcpyDeviceToDevice) != cudaSuccess)
+                return bail(fail(CAMELOT_EINVAL, "weights[0] is not readable device memory"));
+            sp.layer[0].w = (const float*)tab;
+            sp.scratch_bytes = 0;
             break;
         }
         default:
@@ -730,6 +760,8 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     const int sms = sm_count();
     if (per_sm < 1 || total > per_sm * sms)
         return fail(CAMELOT_EINVAL, "allocation needs %d SMs, the device offers %d", total, sms * per_sm);
+    if (is_tensor_kind(stages[0]->sp.kind) && stages[0]->sp.rows > 1)
+        return fail(CAMELOT_EINVAL, "a token-level tensor-core stage cannot be the first stage");
     if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32 &&
         !is_tensor_kind(stages[n_stages - 1]->sp.kind))
         return fail(CAMELOT_EINVAL, "logits_sink needs a dense final stage");

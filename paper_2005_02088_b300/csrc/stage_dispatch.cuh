@@ -14,6 +14,7 @@ static __device__ bool stage_body(const StageCtx& cx, const StageParams& P, RowR
         case KIND_GEMM_BF16:
         case KIND_GEMM_FP8: return gemm_body(cx, P, in, n, out, fo);
         case KIND_NORMALIZE_U8_E4M3: normalize_e4m3_body(cx, P, in, n, out); return true;
+        case KIND_EMBED_GATHER: embed_body(cx, P, in, n, out); return true;
         default: return false;
     }
 }

@@ -99,6 +99,25 @@ static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, 
 // FP8 arm of the normalisation stage: the code of 128 y, y = (x - 127.5) / 64,
 // i.e. e4m3(2 x - 255) (exact in f32, then rounded to nearest even e4m3).  The
 // next stage reads the codes with scale 1/128.  16 input bytes -> 16 codes.
+// Embedding gather of the text-tagging microservice: out row t of query q =
+// E[tok] (bf16, D columns) for 0 <= tok < V, zero otherwise; 16-byte pieces.
+static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out) {
+    const int V = P.H, D = P.W, T = P.rows;
+    const __nv_bfloat16* E = reinterpret_cast<const __nv_bfloat16*>(P.layer[0].w);
+    const uint64_t pieces = (uint64_t)D * 2 / 16;
+    const uint64_t per_q = (uint64_t)T * pieces;
+    const uint64_t total = (uint64_t)n * per_q;
+    const uint64_t stride = (uint64_t)cx.nctas * kThreads;
+    for (uint64_t e = (uint64_t)cx.rank * kThreads + threadIdx.x; e < total; e += stride) {
+        const uint64_t q = e / per_q, rem = e - q * per_q;
+        const uint64_t t = rem / pieces, c = rem - t * pieces;
+        const int32_t tok = reinterpret_cast<const int32_t*>(in.row(q))[t];
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (tok >= 0 && tok < V) v = __ldg(reinterpret_cast<const uint4*>(E + (size_t)tok * D) + c);
+        __stcg(reinterpret_cast<uint4*>(out.row(q) + t * (uint64_t)D * 2) + c, v);
+    }
+}
+
 static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                            RowRef out) {
     const uint64_t chunks = P.in_row_bytes / 16;
@@ -415,6 +434,32 @@ static __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int
                 bv[kMaxTopK - 1] = -INFINITY;
                 bi[kMaxTopK - 1] = 0x7fffffff;
             }
+        }
+    }
+}
+
+// Token-level final stage: the argmax (lowest index among equal maxima) of
+// each of the T rows of every query; the tags of the first res_k rows go to
+// the result arrays, all T tags (int32) to the logits rows when wanted.
+static __device__ void token_argmax(const StageCtx& cx, RowRef z, int n, int T, int N, int res_k,
+                                    const FinalOut& fo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = cx.rank * kWarps + warp; r < n * T; r += cx.nctas * kWarps) {
+        const float* zr = reinterpret_cast<const float*>(z.row(r));
+        float bv = -INFINITY;
+        int bi = 0x7fffffff;
+        for (int j = lane; j < N; j += 32) {
+            const float v = __ldcg(zr + j);
+            if (v > bv || bi == 0x7fffffff) { bv = v; bi = j; }
+        }
+        warp_best(bv, bi);
+        if (lane == 0) {
+            const int q = r / T, t = r - q * T;
+            if (t < res_k) {
+                fo.idx[(size_t)q * res_k + t] = bi;
+                fo.val[(size_t)q * res_k + t] = bv;
+            }
+            if (fo.logits.base != nullptr) reinterpret_cast<int32_t*>(fo.logits.row(q))[t] = bi;
         }
     }
 }
