@@ -405,6 +405,60 @@ camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);
  * free every resource.  Completions not yet polled are dropped. */
 camelot_status camelot_pipeline_destroy(camelot_pipeline* p);
 
+/* -------------------------------------------------------- serving loop */
+/* A serving loop over several pipelines sharing the GPU, with admission by
+ * device memory (Sec. 5.1: a query is started only once the memory it needs is
+ * free; services are co-located, Sec. 4.2).  camelot_server_submit queues
+ * queries per pipeline in pinned host memory and returns at once; one server
+ * thread admits them in FIFO order per pipeline, round robin over pipelines, at
+ * most max_admit at a time, while the query bytes in flight on the device (all
+ * pipelines) stay within device_bytes_budget and the pipeline has ring room,
+ * by camelot_submit (so each pipeline should use device_data = 1: the admitted
+ * bytes then live in its device data ring); it polls every pipeline and keeps
+ * the completions for camelot_server_poll.  Batching happens on the device, per
+ * pipeline, over whatever has been admitted.  The server is the only thread
+ * that may submit to or poll its pipelines while it exists; the pipelines
+ * (caller-owned) must outlive it. */
+#define CAMELOT_MAX_SERVER_PIPELINES 16
+typedef struct camelot_server camelot_server;
+typedef struct {
+    uint64_t device_bytes_budget;  /* query bytes in flight on the device, all pipelines
+                                      (0 = no limit beyond the rings)               */
+    uint32_t host_queue_queries;   /* host queue capacity per pipeline (default 4096)  */
+    uint32_t max_admit;            /* queries admitted per pipeline per round (64)     */
+} camelot_server_options;
+typedef struct {
+    uint64_t submitted, admitted, completed;  /* queries                               */
+    uint64_t waiting;                         /* in the host queue, not yet admitted   */
+    uint64_t deferred;                        /* admission rounds that found no room   */
+    uint64_t inflight_bytes;                  /* this pipeline's query bytes on device */
+    uint64_t peak_inflight_bytes;
+    uint64_t total_inflight_bytes;            /* all pipelines                         */
+    int32_t status;                           /* camelot_status of the pipeline        */
+    int32_t pad_;
+} camelot_lane_stats;
+
+void camelot_server_options_default(camelot_server_options* o);
+/* Errors: EINVAL (n outside 1..16, null pipeline, budget below one query),
+ * ENOMEM. */
+camelot_status camelot_server_create(camelot_pipeline* const* pipelines, int n,
+                                     const camelot_server_options* opts, camelot_server** out);
+/* Copy n queries (host, rows contiguous, the pipeline's stage-0 row bytes each)
+ * into pipeline `pipeline`'s host queue with their arrival stamps (host
+ * CLOCK_MONOTONIC ns; NULL = now).  All or nothing: EAGAIN if the host queue
+ * lacks room; ESTATE if the pipeline failed. */
+camelot_status camelot_server_submit(camelot_server* s, int pipeline, uint32_t stream_id,
+                                     const void* queries, uint32_t n, const int64_t* arrival_ns);
+/* Up to max completions of `pipeline`, in query-ID order; waits up to
+ * timeout_us for the first (0 = no wait, < 0 = no bound).  ETIMEDOUT if
+ * timeout_us > 0 passed with nothing; ESTATE if the pipeline failed. */
+camelot_status camelot_server_poll(camelot_server* s, int pipeline, camelot_completion* out,
+                                   uint32_t max, uint32_t* n_out, int64_t timeout_us);
+camelot_status camelot_server_stats(camelot_server* s, int pipeline, camelot_lane_stats* out);
+/* Stop the server thread and free the queues (queued, unadmitted queries are
+ * dropped; admitted ones stay in their pipelines). */
+camelot_status camelot_server_destroy(camelot_server* s);
+
 /* ------------------------------------------------------------ allocator */
 typedef enum {
     CAMELOT_POLICY_MAX_PEAK = 0,  /* Eq. 1: maximise min_i N_i f_i(p_i)                   */

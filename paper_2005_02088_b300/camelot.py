@@ -67,6 +67,18 @@ class Stats(C.Structure):
                 ("total_launch_ms", C.c_double)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("device_bytes_budget", C.c_uint64), ("host_queue_queries", C.c_uint32),
+                ("max_admit", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("waiting", C.c_uint64), ("deferred", C.c_uint64), ("inflight_bytes", C.c_uint64),
+                ("peak_inflight_bytes", C.c_uint64), ("total_inflight_bytes", C.c_uint64),
+                ("status", C.c_int32), ("pad_", C.c_int32)]
+
+
 class Profile(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("n_levels", C.c_int32), ("n_batches", C.c_int32),
                 ("unit", C.c_int32), ("batch_sizes", C.c_void_p), ("thr_qps", C.c_void_p),
@@ -111,6 +123,12 @@ _SIGS = {
     "camelot_pipeline_stats": (C.c_int, [P, P]),
     "camelot_pipeline_destroy": (C.c_int, [P]),
     "camelot_allocate": (C.c_int, [P, C.c_int, P, P, P]),
+    "camelot_server_options_default": (None, [P]),
+    "camelot_server_create": (C.c_int, [P, C.c_int, P, P]),
+    "camelot_server_submit": (C.c_int, [P, C.c_int, C.c_uint32, P, C.c_uint32, P]),
+    "camelot_server_poll": (C.c_int, [P, C.c_int, P, C.c_uint32, P, C.c_int64]),
+    "camelot_server_stats": (C.c_int, [P, C.c_int, P]),
+    "camelot_server_destroy": (C.c_int, [P]),
 }
 
 _lib = None
@@ -333,3 +351,41 @@ def camelot_allocate(prof: Profile, policy: int, cons: Constraints):
     obj = C.c_double()
     _check(load().camelot_allocate(C.byref(prof), policy, C.byref(cons), C.byref(a), C.byref(obj)))
     return a, obj.value
+
+
+def camelot_server_options_default() -> ServerOptions:
+    o = ServerOptions()
+    load().camelot_server_options_default(C.byref(o))
+    return o
+
+
+def camelot_server_create(pipelines, opts: ServerOptions | None = None) -> int:
+    arr = (C.c_void_p * len(pipelines))(*pipelines)
+    h = C.c_void_p()
+    _check(load().camelot_server_create(arr, len(pipelines), C.byref(opts) if opts is not None else None,
+                                        C.byref(h)))
+    return h.value
+
+
+def camelot_server_submit(s: int, pipeline: int, stream_id: int, queries, n: int, arrival_ns=None,
+                          allow_eagain: bool = False) -> bool:
+    """True if queued, False on EAGAIN when ``allow_eagain``."""
+    st = _check(load().camelot_server_submit(s, pipeline, stream_id, _ptr(queries), n, _ptr(arrival_ns)),
+                allow=(EAGAIN,) if allow_eagain else ())
+    return st == OK
+
+
+def camelot_server_poll(s: int, pipeline: int, buf, timeout_us: int = 0) -> int:
+    n = C.c_uint32()
+    _check(load().camelot_server_poll(s, pipeline, buf, len(buf), C.byref(n), timeout_us), allow=(ETIMEDOUT,))
+    return n.value
+
+
+def camelot_server_stats(s: int, pipeline: int) -> ServerStats:
+    st = ServerStats()
+    _check(load().camelot_server_stats(s, pipeline, C.byref(st)))
+    return st
+
+
+def camelot_server_destroy(s: int) -> None:
+    _check(load().camelot_server_destroy(s))

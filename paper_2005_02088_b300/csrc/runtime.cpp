@@ -370,6 +370,7 @@ size_t camelot_internal_layout_scratch(StageParams& sp, int B) {
 }
 int camelot_internal_sm_count() { return sm_count(); }
 camelot_status camelot_internal_fail(camelot_status st, const char* msg) { return fail(st, "%s", msg); }
+size_t camelot_internal_query_bytes(const camelot_pipeline* p);
 
 extern "C" camelot_status camelot_stage_info(const camelot_stage* st, size_t* in_row,
                                              size_t* out_row, uint32_t n, size_t* scratch) {
@@ -1082,3 +1083,5 @@ extern "C" camelot_status camelot_pipeline_destroy(camelot_pipeline* p) {
     if (e != cudaSuccess) return fail(CAMELOT_ECUDA, "persistent kernel ended with: %s", cudaGetErrorString(e));
     return CAMELOT_OK;
 }
+
+size_t camelot_internal_query_bytes(const camelot_pipeline* p) { return p->hp.q_row; }
