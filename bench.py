@@ -65,6 +65,13 @@ WORKLOADS = {
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
+    "text-2stage": dict(
+        desc=("text tagging: int32 token queries (Zipf s=1.1 over 32000, length 16..128, padded to 128) -> "
+              "embedding gather 32000x512 bf16 -> token-level GEMMs 512-2048 GELU-512-64 (bf16, tcgen05) -> "
+              "per-token argmax; batch 8"),
+        batch=8, row=512, even=([1, 1], [72, 72]), profile_alloc=([1, 2], [8, 16]),
+        flop=2 * 128 * (512 * 2048 + 2048 * 512 + 512 * 64),
+        bytes=512 + 2 * 128 * 512 * 2, weight_bytes=2 * (512 * 2048 + 2048 * 512 + 512 * 64)),
     "fp8-2stage": dict(
         desc=("plain 2-stage pipeline, FP8 arm: 64x64x3 u8 images -> normalize to e4m3 codes (scale "
               "1/128) -> MLP 12288-512-256-10 on e4m3 weights and activations (per-tensor scales, f32 "
@@ -229,6 +236,29 @@ class Workload:
             self.stages.append(pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], top_k=1,
                                               max_batch=32))
             self.io = [(12288, "u8"), (12288 * 4, "f32")]
+        elif name == "text-2stage":
+            tok, _, E, ws = synth.cfg4_inputs(0, n_queries=1024)
+            rows = np.arange(n_rows) % 1024
+            self.xq_host = np.ascontiguousarray(tok[rows]).view(np.uint8).reshape(n_rows, -1)
+            bfz = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).cuda()
+            self._keep = [bfz(E)] + [bfz(w) for w in ws]
+            d = cm.StageDesc()
+            d.kind = cm.STAGE_EMBED_GATHER
+            d.dims[0], d.dims[1], d.dims[2] = 32000, 512, 128
+            d.weights[0] = self._keep[0].data_ptr()
+            d.max_batch = 8
+            torch.cuda.synchronize()
+            s0 = cm.camelot_stage_prepare(d)
+            d = cm.StageDesc()
+            d.kind = cm.STAGE_GEMM_BF16
+            d.n_layers = 3
+            d.dims[0], d.dims[1], d.dims[2], d.dims[3] = 512, 2048, 512, 64
+            for i in range(3):
+                d.weights[i] = self._keep[1 + i].data_ptr()
+            d.act[0] = cm.ACT_GELU
+            d.top_k, d.max_batch, d.rows_per_query = 1, 8, 128
+            self.stages = [s0, cm.camelot_stage_prepare(d)]
+            self.io = [(512, "i32"), (128 * 512 * 2, "bf16")]
         elif name == "fp8-2stage":
             x, ws = synth.cfg1_inputs(0, n_queries=1024)
             rows = np.arange(n_rows) % 1024
@@ -819,6 +849,163 @@ def run_diurnal(args):
     return 0
 
 
+def run_serving(args):
+    """The serving loop of four pipelines of uneven size sharing one GPU (plain
+    FP32 2-stage, text tagging, 3-stage BF16, FP8 2-stage), Poisson arrivals
+    mixed 1:1:1:1.  SM shares: each pipeline first gets an Eq. 1 allocation
+    inside 32 SMs and its saturation rate there is measured; the 144 SMs are then
+    shared in inverse proportion to those rates (multiples of 8, at least 8 per
+    stage), Eq. 1 again inside each share.  Measured: the largest total rate at
+    which all four hold p99 <= QoS replaying concurrent device-resident traces
+    (bisection), each pipeline's p50/p99 there, the same rate with each pipeline
+    alone, and the host-submitted mix through camelot_server (device-memory
+    admission) at a fraction of that rate."""
+    import torch
+    import synth
+    names = ["fp32-2stage", "text-2stage", "bf16-3stage", "fp8-2stage"]
+    wls = [Workload(nm, 0, n_rows=8192) for nm in names]
+    cm = wls[0].cm
+    total = (wls[0].sms // 8) * 8
+    q_n = 8000
+    out = {"pipelines": names}
+    try:
+        def alloc_in(wl, sms):
+            levels, dur = wl.profile_batches([wl.B], runs=10)
+            pr, keep = wl.alloc_table(levels, [wl.B], dur)
+            cons = cm.Constraints(sms, sms // 8, _peaks().get("hbm_gbs", 6400.0), 200e9, QOS_NS * 1e-9, 0.0,
+                                  cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
+            a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
+            n = len(wl.stages)
+            return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)]
+
+        sat = []
+        for wl in wls:
+            inst, quota = alloc_in(wl, 32)
+            p = wl.pipeline(0, inst, quota)
+            comps, ms = wl.trace(p, np.zeros(q_n, np.int64))
+            cm.camelot_pipeline_destroy(p)
+            sat.append(q_n / (ms * 1e-3))
+        inv = np.array([1.0 / r for r in sat])
+        mins = np.array([8 * len(wl.stages) for wl in wls])
+        share = np.maximum(mins, np.floor(inv / inv.sum() * total / 8) * 8).astype(int)
+        while share.sum() > total:
+            share[np.argmax(share - mins)] -= 8
+        allocs = [alloc_in(wl, int(sh)) for wl, sh in zip(wls, share)]
+        out["saturation_in_32_sms_qps"] = sat
+        out["sm_share"] = share.tolist()
+        out["allocations"] = [{"instances": a[0], "sm_quota": a[1]} for a in allocs]
+
+        pipes = [wl.pipeline(0, a[0], a[1]) for wl, a in zip(wls, allocs)]
+
+        def mix(lam_total, seed, only=None):
+            """Concurrent device-resident traces at lam_total / 4 each."""
+            offs = [synth.poisson_arrivals_ns(seed + i, q_n, lam_total / 4) for i in range(4)]
+            use = range(4) if only is None else [only]
+            for i in use:
+                off = torch.from_numpy(offs[i]).cuda()
+                wls[i]._off = off
+            torch.cuda.synchronize()
+            for i in use:
+                cm.camelot_submit_trace(pipes[i], 0, wls[i].xq, q_n, wls[i]._off)
+            res = {}
+            for i in use:
+                comps = wls[i]._drain(pipes[i], q_n)
+                lat = (comps["t_done"] - comps["t_arrival"])[Q_WARM:]
+                res[names[i]] = {"p99_ms": float(np.percentile(lat, 99)) * 1e-6,
+                                 "p50_ms": float(np.percentile(lat, 50)) * 1e-6,
+                                 "qps": q_n / ((comps["t_done"].max() - comps["t_arrival"].min()) * 1e-9)}
+            for i in use:   # let each launch end (exit_after_trace) before the next trace
+                t_end = time.time() + 10
+                while cm.camelot_pipeline_stats(pipes[i]).total_launch_ms <= wls[i]._last_total[pipes[i]]:
+                    if time.time() > t_end:
+                        break
+                    time.sleep(0.0005)
+                wls[i]._last_total[pipes[i]] = cm.camelot_pipeline_stats(pipes[i]).total_launch_ms
+            return res
+
+        try:
+            with ClockSampler(0) as clk:
+                hi = 4 * min(r * sh / 32 for r, sh in zip(sat, share)) * 1.5
+                lo, best = hi * 0.05, None
+                for it in range(8):
+                    lam = lo if it == 0 else (lo * hi) ** 0.5
+                    r = mix(lam, 10 + it)
+                    ok = all(v["p99_ms"] <= QOS_NS * 1e-6 for v in r.values())
+                    if ok:
+                        best, lo = (lam, r), lam
+                    else:
+                        hi = lam
+                    if it == 0 and not ok:
+                        break
+                lam_best, res_mix = best if best else (0.0, {})
+                alone = {}
+                if lam_best:
+                    for i in range(4):
+                        alone.update(mix(lam_best, 99, only=i))
+        finally:
+            for p in pipes:
+                cm.camelot_pipeline_destroy(p)
+        out["mix_peak_total_qps"] = lam_best
+        out["mix"] = res_mix
+        out["alone_at_same_rate"] = alone
+
+        # host-submitted mix through camelot_server at 30 % of that rate
+        lam_h = 0.3 * lam_best
+        pipes = [wl.pipeline(0, a[0], a[1], data_slots=1024, device_data=1) for wl, a in zip(wls, allocs)]
+        opts = cm.camelot_server_options_default()
+        opts.device_bytes_budget = 256 << 20
+        srv = cm.camelot_server_create(pipes, opts)
+        try:
+            nq = 4000
+            arr = [synth.poisson_arrivals_ns(50 + i, nq, lam_h / 4) for i in range(4)]
+            t0 = time.monotonic_ns() + 2_000_000
+            arr = [(a + t0).astype(np.int64) for a in arr]
+            sent, done, got = [0] * 4, [[] for _ in range(4)], [0] * 4
+            buf = (cm.Completion * 4096)()
+            deadline = time.time() + 120
+            while any(g < nq for g in got):
+                now = time.monotonic_ns()
+                for i in range(4):
+                    if sent[i] < nq and arr[i][sent[i]] <= now:
+                        m = min(int(np.searchsorted(arr[i], now, side="right")) - sent[i], 256)
+                        if cm.camelot_server_submit(srv, i, 1, wls[i].xq_host[sent[i]:sent[i] + m], m,
+                                                    arr[i][sent[i]:sent[i] + m], allow_eagain=True):
+                            sent[i] += m
+                    k = cm.camelot_server_poll(srv, i, buf, 0)
+                    if k:
+                        done[i].append(np.frombuffer(buf, dtype=COMP_DTYPE, count=k).copy())
+                        got[i] += k
+                if time.time() > deadline:
+                    raise TimeoutError("host-submitted mix")
+            host = {}
+            for i in range(4):
+                c = np.concatenate(done[i])
+                lat = (c["t_poll"] - c["t_arrival"])[500:]
+                st = cm.camelot_server_stats(srv, i)
+                host[names[i]] = {"p99_ms": float(np.percentile(lat, 99)) * 1e-6,
+                                  "p50_ms": float(np.percentile(lat, 50)) * 1e-6,
+                                  "peak_inflight_bytes": st.peak_inflight_bytes, "deferred": st.deferred}
+        finally:
+            cm.camelot_server_destroy(srv)
+            for p in pipes:
+                cm.camelot_pipeline_destroy(p)
+        out["host_submitted"] = {"total_offered_qps": lam_h, "budget_bytes": 256 << 20, "per_pipeline": host}
+    finally:
+        for wl in wls:
+            wl.close()
+    line = {
+        "metric": "serving loop: largest total Poisson rate (mixed 1:1:1:1) at which four co-located "
+                  "pipelines all hold p99 <= QoS on 1 B300, with p50/p99 per pipeline",
+        "value": out["mix_peak_total_qps"], "unit": "queries/s (all four pipelines)", "higher_is_better": True,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": {nm: WORKLOADS[nm]["desc"] for nm in names}, "qos_p99_ms": QOS_NS / 1e6,
+                   "queries_per_trace_per_pipeline": q_n},
+        "serving": out, "clocks": clk.summary(),
+    }
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Small self-contained case for ncu: two saturated 2,000-query launches."""
     wl = Workload(args.workload, 0, n_rows=2000)
@@ -845,6 +1032,7 @@ def main():
                     help="run the latency-predictor study (profiling, GPU training, allocation) instead")
     ap.add_argument("--pred-samples", type=int, default=20000)
     ap.add_argument("--pred-runs", type=int, default=100)
+    ap.add_argument("--serving", action="store_true", help="run the four-pipeline serving study instead")
     ap.add_argument("--diurnal", type=float, default=0.0,
                     help="run the diurnal low-load study over this many seconds (60 = the compressed day)")
     args = ap.parse_args()
@@ -858,6 +1046,8 @@ def main():
         return run_predictor(args)
     if args.diurnal > 0:
         return run_diurnal(args)
+    if args.serving:
+        return run_serving(args)
     dist = None
     if world > 1:
         import torch
