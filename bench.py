@@ -61,7 +61,7 @@ WORKLOADS = {
               "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
               "arrivals; p99 QoS 20 ms"),
         batch=32, row=224 * 224 * 3, even=([1, 1, 1], [48, 48, 48]),
-        profile_alloc=([4, 11, 3], [8, 8, 8]),
+        profile_alloc=([5, 10, 3], [8, 8, 8]),
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
@@ -69,17 +69,37 @@ WORKLOADS = {
         desc=("text tagging: int32 token queries (Zipf s=1.1 over 32000, length 16..128, padded to 128) -> "
               "embedding gather 32000x512 bf16 -> token-level GEMMs 512-2048 GELU-512-64 (bf16, tcgen05) -> "
               "per-token argmax; batch 8"),
-        batch=8, row=512, even=([1, 1], [72, 72]), profile_alloc=([1, 2], [8, 16]),
+        batch=8, row=512, even=([1, 1], [72, 72]), profile_alloc=([1, 10], [8, 8]),
         flop=2 * 128 * (512 * 2048 + 2048 * 512 + 512 * 64),
         bytes=512 + 2 * 128 * 512 * 2, weight_bytes=2 * (512 * 2048 + 2048 * 512 + 512 * 64)),
     "fp8-2stage": dict(
         desc=("plain 2-stage pipeline, FP8 arm: 64x64x3 u8 images -> normalize to e4m3 codes (scale "
               "1/128) -> MLP 12288-512-256-10 on e4m3 weights and activations (per-tensor scales, f32 "
               "accumulation, tcgen05 kind::f8f6f4) -> argmax; Poisson arrivals; p99 QoS 20 ms"),
-        batch=16, row=12288, even=([1, 1], [72, 72]), profile_alloc=([2, 16], [8, 8]),
+        batch=16, row=12288, even=([1, 1], [72, 72]), profile_alloc=([3, 15], [8, 8]),
         flop=2 * (12288 * 512 + 512 * 256 + 256 * 10),
         bytes=12288 + 2 * 12288, weight_bytes=(12288 * 512 + 512 * 256 + 256 * 10)),
 }
+
+
+def _measured_traffic_per_query():
+    """DRAM bytes per query of the headline pipeline kernel from the committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
+    import glob
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2005_02088_b300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "pipeline_kernel_bf16_3stage.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_per_query_bytes: (\d+); csrc_sha256: ([0-9a-f]+)", txt)
+    if not m or m.group(2) != h.hexdigest()[:16]:
+        return None
+    return int(m.group(1))
 
 
 def _peaks():
@@ -617,6 +637,7 @@ def run_gpu(args, rank: int, world: int, dist):
     achieved = bytes_q * sat_qps / 1e9
     hbm = peaks.get("hbm_gbs", 6400.0)
     value = world * Q_STEP / (ms_step * 1e-3)
+    tpq = _measured_traffic_per_query()
     cpu_v, cores, sample = cpu_oracle_rate(HEADLINE)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -631,10 +652,12 @@ def run_gpu(args, rank: int, world: int, dist):
         "headline_detail": head,
         "fp32_2stage": side,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "pipeline_kernel",
+                     "frac": achieved / hbm, "traffic": tpq * Q_STEP if tpq else None,
+                     "kernel": "pipeline_kernel",
                      "basis": (f"{bytes_q:.0f} algorithmic bytes/query (image, bf16 handoffs, "
                                f"weights/{w['batch']}) x saturated {sat_qps:.0f} queries/s; peak = "
-                               "measured HBM copy bandwidth")},
+                               "measured HBM copy bandwidth; traffic = ncu DRAM bytes per query of a "
+                               "2,000-query capture x the queries of one launch")},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": e2e["qps"], "unit": UNIT, "p99_ms": e2e["p99_ms"],
