@@ -3,14 +3,13 @@
 //
 // Each layer computes y[q][m] = act(vscale * sum_k W[m][k] x[q][k]) for a batch
 // of at most 32 queries.  The batch is small, so the operands are swapped: the
-// weights are the M = 128 operand (128 x 64 tiles, stored pre-tiled and
-// pre-swizzled as contiguous 16 KB blocks and streamed by 1-D bulk copies
-// through a shared-memory ring) and the queries are the N = 32
-// operand (32 x 64 tiles staged with cp.async in the same swizzled layout, in
-// the same ring stage as the weight tile they multiply).  The CTA's warps
-// specialise: one streams weight tiles, one stages query tiles, one thread
-// issues tcgen05.mma (M=128, N=32, K=16) into one of two TMEM accumulators,
-// four warps drain the other accumulator.  A unit is
+// weights are the M = 128 operand (128-row x 128-byte tiles, stored pre-tiled
+// and pre-swizzled as contiguous 16 KB blocks) and the queries are the N = 32
+// operand (32-row x 128-byte tiles: each layer first rewrites its input rows in
+// that tiled, swizzled form, 4 KB per tile).  One warp streams both operands
+// with 1-D bulk copies through a shared-memory ring; one thread in each of two
+// warps issues tcgen05.mma (M=128, N=32) into its own pair of TMEM
+// accumulators; four warps drain finished accumulators.  A unit is
 // (K-chunk, 128-row tile); chunk partials are added in chunk order, so the
 // result is the same whatever the number of CTAs.
 #pragma once
@@ -34,8 +33,7 @@ constexpr int kIssuers = 2;                      // MMA-issuing warps
 constexpr uint32_t kTmemCols = 2 * kIssuers * kGemmN;   // two 32-column accumulators per issuer
 
 // Warp roles inside a CTA running tensor-core layers.
-constexpr int kWarpTma = 0;     // weight tiles, bulk copies
-constexpr int kWarpB = 2;       // query tiles, cp.async
+constexpr int kWarpTma = 0;     // weight and query tiles, bulk copies
 constexpr int kWarpEpi0 = 4;    // warps 4..7 read the accumulators
 // warps 1 and 3 issue tcgen05.mma (one thread each): issuer 0 takes the
 // CTA's even units, issuer 1 the odd ones
@@ -43,7 +41,7 @@ __device__ __forceinline__ int issuer_of_warp(int warp) { return warp == 1 ? 0 :
 
 struct GemmSmem {
     char* ring;            // kGemmStages x (2 weight tiles, 32 KB, then 2 query tiles, 8 KB)
-    uint64_t* full;        // [kGemmStages] both tiles landed (1 copy arrival + tx, 32 cp.async arrivals)
+    uint64_t* full;        // [kGemmStages] both operands landed (1 arrival + tx bytes)
     uint64_t* empty;       // [kGemmStages] MMAs reading the stage are done
     uint64_t* tfull;       // [2 * kIssuers] accumulator complete
     uint64_t* tfree;       // [2 * kIssuers] accumulator read out (4 arrivals: epilogue warps)
@@ -73,7 +71,7 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
     GemmSmem g = gemm_smem(smem);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGemmStages; ++s) {
-            mbar_init(&g.full[s], 1 + 32);
+            mbar_init(&g.full[s], 1);
             mbar_init(&g.empty[s], 1);
         }
         for (int b = 0; b < 2 * kIssuers; ++b) {
@@ -129,6 +127,8 @@ struct LayerOut {
     int act;
     float vscale;   // accumulator scale
     float qscale;   // e4m3: the stored code is e4m3(value / qscale)
+    int tiled;      // bf16 / e4m3 rows in the tiled layout (the next layer's operand), from rows.base
+    size_t rowb;    // bytes per row (tiled)
 };
 
 __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float acc) {
@@ -136,29 +136,39 @@ __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float
     if (o.fmt == OUT_F32) {
         reinterpret_cast<float*>(o.rows.row(q))[m] = v;
     } else if (o.fmt == OUT_BF16) {
-        reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = __float2bfloat16_rn(v);
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        if (o.tiled) *reinterpret_cast<__nv_bfloat16*>(o.rows.base + tiled_offset(q, (size_t)m * 2, o.rowb)) = b;
+        else reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = b;
     } else {
-        reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(q))[m] =
-            __nv_cvt_float_to_fp8(v / o.qscale, __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v / o.qscale, __NV_SATFINITE, __NV_E4M3);
+        if (o.tiled) *reinterpret_cast<__nv_fp8_storage_t*>(o.rows.base + tiled_offset(q, (size_t)m, o.rowb)) = c;
+        else reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(q))[m] = c;
     }
 }
+
+// What a stage needs to know about its unit, worked out once per unit.
+struct UnitInfo {
+    int c, mt, row0;   // K-chunk, weight tile, first input row
+    int nkb, ns;       // 128-byte k-blocks in the chunk, ring stages of the unit
+};
 
 // The order in which a CTA's ring stages carry its units: units are taken in
 // pairs (r, r + 1) relative to the CTA's first unit, and the stages of a pair
 // alternate between its two units, so both issuers always have stages in the
-// ring.  f(u, r, j, gi) is called for stage j of unit u0 + r at ring position
-// gi, in ring order; it returns false to stop.
-template <class StagesOf, class F>
-__device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, StagesOf stages_of, F f) {
+// ring.  f(info, r, j, gi) is called for stage j of unit u0 + r at ring
+// position gi, in ring order; it returns false to stop.
+template <class Info, class F>
+__device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, Info info, F&& f) {
     uint32_t gi = ring0;
     for (int r = 0; u0 + r < u1; r += 2) {
         const int ua = u0 + r;
         const bool pair = ua + 1 < u1;
-        const int na = stages_of(ua), nb = pair ? stages_of(ua + 1) : 0;
-        const int nmax = na > nb ? na : nb;
+        const UnitInfo a = info(ua);
+        const UnitInfo b = pair ? info(ua + 1) : UnitInfo{0, 0, 0, 0, 0};
+        const int nmax = a.ns > b.ns ? a.ns : b.ns;
         for (int j = 0; j < nmax; ++j) {
-            if (j < na && !f(ua, r, j, gi++)) return false;
-            if (j < nb && !f(ua + 1, r + 1, j, gi++)) return false;
+            if (j < a.ns && !f(a, r, j, gi++)) return false;
+            if (j < b.ns && !f(b, r + 1, j, gi++)) return false;
         }
     }
     return true;
@@ -172,9 +182,12 @@ __device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, S
 // one thread into one accumulator, whichever CTA or issuer runs it.  Each ring
 // stage carries two consecutive weight tiles (one 32 KB bulk copy: the copy
 // engine's cost is per operation, so larger copies stream faster; kept in L2
-// with the evict-last policy) and the matching query tiles (cp.async by the
-// loader warp, 128-byte swizzle).
-static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int rows,
+// with the evict-last policy) and the matching two query tiles of xt (one
+// 8 KB bulk copy).
+// ESZ = bytes per operand element (2: bf16 / kind::f16, 1: e4m3 / kind::f8f6f4),
+// a template parameter so that each instantiation's MMA loop holds one kind.
+template <int ESZ>
+static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, const char* xt, int rows,
                                         float* Pbuf, const LayerOut& direct) {
     const GemmSmem g = gemm_smem(cx.smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -189,13 +202,25 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     for (int w = 0; w < kIssuers; ++w) accb[w] = g.acc_it[w];
     const uint32_t tmem = *g.tmem_slot;
     // k-blocks are 128 bytes wide: 64 bf16 or 128 e4m3 columns
-    auto chunk_kb = [&](int c) { return min(L.KC, L.K - c * L.KC) * L.esz / 128; };
-    const size_t kc_bytes = (size_t)L.KC * L.esz;
-    auto chunk_of = [&](int u) { return (u % CM) / MT; };
-    auto stages_of = [&](int u) { return (chunk_kb(chunk_of(u)) + kKbPerStage - 1) / kKbPerStage; };
+    // layer constants in registers: the lambdas below capture by value, so the
+    // asm statements' memory clobbers do not force reloads
+    const int K = L.K, KC = L.KC, N = L.N, Npad = L.Npad, C = L.C;
+    constexpr int esz = ESZ;
+    auto chunk_kb = [=](int c) { return min(KC, K - c * KC) * esz / 128; };
+    const size_t kc_bytes = (size_t)KC * esz;
+    auto info = [=](int u) {
+        UnitInfo ui;
+        const int rt = u / CM, v = u - rt * CM;
+        ui.c = v / MT;
+        ui.mt = v - ui.c * MT;
+        ui.row0 = rt * kGemmN;
+        ui.nkb = chunk_kb(ui.c);
+        ui.ns = (ui.nkb + kKbPerStage - 1) / kKbPerStage;
+        return ui;
+    };
     // accumulator of the unit that is issuer w's k-th (counting all its
     // earlier units): two per issuer, alternating
-    auto acc_of = [&](int w, uint32_t k) { return 2 * w + (int)(k & 1u); };
+    auto acc_of = [](int w, uint32_t k) { return 2 * w + (int)(k & 1u); };
     const int iw = issuer_of_warp(warp);
 
     if (u0 < u1) {
@@ -203,80 +228,37 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             // tiles (mt, kb) and (mt, kb+1) are adjacent in memory: one bulk copy
             const uint64_t pol = l2_policy_evict_last();
             const char* wt = reinterpret_cast<const char*>(L.w);
-            const int KB = L.K * L.esz / 128;            // weight tiles per 128-row block
-            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
-                const int c = chunk_of(u), mt = u % MT;
+            const int KB = K * esz / 128;                // weight tiles per 128-row block
+            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int, int j, uint32_t gi) {
                 const int kb = j * kKbPerStage;
-                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
+                const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
                 if (gi >= (uint32_t)kGemmStages &&
                     !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
                     return false;
-                mbar_arrive_expect_tx(&g.full[s], nk * kATileBytes);
-                bulk_load_hint(g.ring + s * kStageBytes,
-                               wt + ((size_t)mt * KB + c * (kc_bytes / 128) + kb) * kATileBytes,
+                const size_t kbg = ui.c * (kc_bytes / 128) + kb;   // first k-block of the stage
+                mbar_arrive_expect_tx(&g.full[s], nk * (kATileBytes + kBTileBytes));
+                bulk_load_hint(g.ring + s * kStageBytes, wt + ((size_t)ui.mt * KB + kbg) * kATileBytes,
                                nk * kATileBytes, &g.full[s], pol);
-                return true;
-            });
-        } else if (warp == kWarpB) {
-            // query tiles: 32 rows x 128 bytes, 16-byte piece j of row r at
-            // r * 128 + ((j ^ (r & 7)) * 16).  Lane l always copies piece
-            // j = l % 8 of rows r = l / 8 + 4 i (i < 8) of the unit's row tile.
-            // Each lane's cp.async completion arrives on the stage's full
-            // barrier by itself, so the loader runs as far ahead as the ring
-            // allows.
-            const int jj = lane & 7;
-            uint32_t dst_off[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = (lane >> 3) + 4 * i;
-                dst_off[i] = (uint32_t)(r * 128 + ((jj ^ (r & 7)) << 4));
-            }
-            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int, int j, uint32_t gi) {
-                const int c = chunk_of(u);
-                const int row0 = (u / CM) * kGemmN;
-                const int kb = j * kKbPerStage;
-                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
-                const int s = gi % kGemmStages;
-                if (gi >= (uint32_t)kGemmStages &&
-                    !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 2))
-                    return false;
-                const char* src_row[8];
-                uint32_t src_bytes[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = row0 + (lane >> 3) + 4 * i;
-                    src_row[i] = x.row(r < rows ? r : 0) + 16 * jj;
-                    src_bytes[i] = r < rows ? 16u : 0u;
-                }
-                char* dstb = g.ring + s * kStageBytes + kKbPerStage * kATileBytes;
-                for (int t = 0; t < nk; ++t) {
-                    char* dst = dstb + t * kBTileBytes;
-                    const size_t k_off = (size_t)c * kc_bytes + (size_t)(kb + t) * 128;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) cp_async16_zfill(dst + dst_off[i], src_row[i] + k_off, src_bytes[i]);
-                }
-                cp_async_mbar_arrive_noinc(&g.full[s]);
+                bulk_load_hint(g.ring + s * kStageBytes + kKbPerStage * kATileBytes,
+                               xt + ((size_t)(ui.row0 / kGemmN) * KB + kbg) * kBTileBytes, nk * kBTileBytes,
+                               &g.full[s], pol);
                 return true;
             });
         } else if (iw >= 0 && lane == 0) {
-            const bool f8 = L.esz == 1;
-            const uint32_t idesc = f8 ? idesc_e4m3_f32(128, kGemmN) : idesc_bf16_f32(128, kGemmN);
+            constexpr bool f8 = ESZ == 1;
+            constexpr uint32_t idesc = f8 ? idesc_e4m3_f32(128, kGemmN) : idesc_bf16_f32(128, kGemmN);
             uint32_t k = accb[iw];
-            for_each_stage(u0, u1, ring0, stages_of, [&](int u, int r, int j, uint32_t gi) {
+            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) mutable {
                 if ((r & 1) != iw) return true;
                 const int acc = acc_of(iw, k);
-                const int ns = stages_of(u);
+                const int ns = ui.ns;
                 if (j == 0 && k >= 2 && !mbar_wait_bounded(&g.tfree[acc], ((k >> 1) - 1) & 1, cx, 4))
                     return false;
-                const int c = chunk_of(u);
                 const int kb = j * kKbPerStage;
-                const int nk = min(kKbPerStage, chunk_kb(c) - kb);
+                const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
                 if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) return false;
-                // the query tiles were written by cp.async (generic proxy):
-                // order them before the tensor core's reads
-                fence_proxy_async_smem();
                 tc_fence_after();
                 // descriptors of the stage's first A and B slices; a slice 32
                 // bytes further along is the start field + 2 (the field is
@@ -286,28 +268,22 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const uint32_t sbase = smem_u32(g.ring + s * kStageBytes);
                 const uint64_t da = sw128_desc(sbase);
                 const uint64_t db = sw128_desc(sbase + kKbPerStage * kATileBytes);
-                if (nk == kKbPerStage && !f8) {
+                auto mma = [&](int t, int kk) {
+                    const uint64_t a = da + (t * kATileBytes + 32 * kk) / 16;
+                    const uint64_t b = db + (t * kBTileBytes + 32 * kk) / 16;
+                    const uint32_t accum = (kb + t > 0 || kk > 0) ? 1u : 0u;
+                    if constexpr (f8) tc_mma_f8(d_tmem, a, b, idesc, accum);
+                    else tc_mma_f16(d_tmem, a, b, idesc, accum);
+                };
+                if (nk == kKbPerStage) {
 #pragma unroll
                     for (int t = 0; t < kKbPerStage; ++t)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
-                                       db + (t * kBTileBytes + 32 * kk) / 16, idesc,
-                                       (kb + t > 0 || kk > 0) ? 1u : 0u);
-                } else if (f8) {
-                    for (int t = 0; t < nk; ++t)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f8(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
-                                      db + (t * kBTileBytes + 32 * kk) / 16, idesc,
-                                      (kb + t > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) mma(t, kk);
                 } else {
                     for (int t = 0; t < nk; ++t)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f16(d_tmem, da + (t * kATileBytes + 32 * kk) / 16,
-                                       db + (t * kBTileBytes + 32 * kk) / 16, idesc,
-                                       (kb + t > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) mma(t, kk);
                 }
                 tc_commit(&g.empty[s]);
                 if (j == ns - 1) {
@@ -326,8 +302,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             for (int u = u0; u < u1; ++u) {
                 const int w = (u - u0) & 1;
                 const uint32_t k = kw[w]++;
-                const int c = chunk_of(u), mt = u % MT;
-                const int row0 = (u / CM) * kGemmN;
+                const UnitInfo ui = info(u);
+                const int c = ui.c, mt = ui.mt, row0 = ui.row0;
                 const int acc = acc_of(w, k);
                 if (!mbar_wait_bounded(&g.tfull[acc], (k >> 1) & 1, cx, 6)) break;
                 tc_fence_after();
@@ -340,24 +316,25 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&g.tfree[acc]);
                 const int m = mt * 128 + 32 * sub + lane;
-                if (m < L.N) {
+                if (m < N) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         if (row0 + j < rows) {
                             const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                            if (L.C == 1) store_out(direct, row0 + j, m, v);
-                            else __stcg(Pbuf + ((size_t)c * rows + row0 + j) * L.Npad + m, v);
+                            if (C == 1) store_out(direct, row0 + j, m, v);
+                            else __stcg(Pbuf + ((size_t)c * rows + row0 + j) * Npad + m, v);
                         }
                     }
                 }
             }
         }
     }
-    cp_async_wait<0>();   // nothing of this layer still lands in the ring (error paths)
+    // direct (C == 1) outputs may be the next layer's bulk-copied operand
+    fence_proxy_async_global();
     __syncthreads();
     if (threadIdx.x == 0 && u0 < u1) {
         uint32_t stages = 0;
-        for (int u = u0; u < u1; ++u) stages += stages_of(u);
+        for (int u = u0; u < u1; ++u) stages += info(u).ns;
         *g.ring_it = ring0 + stages;
         const uint32_t cnt = (uint32_t)(u1 - u0);
         g.acc_it[0] = accb[0] + (cnt + 1) / 2;
@@ -410,11 +387,50 @@ static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int
                 if (m + i < L.N) store_out(o, q, m + i, vv[i]);
         }
     }
+    fence_proxy_async_global();   // the outputs may be the next layer's bulk-copied operand
 }
 
 // The whole GEMM_BF16 / GEMM_FP8 stage.  Hidden rows and the rows handed to
 // the next stage are bf16 (GEMM_BF16) or e4m3 codes (GEMM_FP8); a final stage
 // keeps its logits in f32.
+// Rewrite `rows` input rows of `rowb` bytes (x) as 32-row x 128-byte tiles:
+// tile (rt, kb) at (rt * rowb / 128 + kb) * 4 KB, row r's 16-byte piece j at
+// r * 128 + (j ^ (r % 8)) * 16, the layout the MMA reads; rows past `rows` in
+// the last tile are zero.  All CTAs of the instance share the work; the
+// writes are fenced for the bulk copies that read them after the next barrier.
+static __device__ void retile_rows(const StageCtx& cx, RowRef x, int rows, size_t rowb, char* xt) {
+    const size_t pieces = rowb / 16;
+    const size_t KB = rowb / 128;
+    const size_t total = (size_t)((rows + kGemmN - 1) / kGemmN) * kGemmN * pieces;
+    const size_t stride = (size_t)cx.nctas * kThreads;
+    constexpr int U = 8;                             // loads in flight per thread
+    for (size_t base = (size_t)cx.rank * kThreads + threadIdx.x; base < total; base += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = base + u * stride;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (e < total) {
+                const int r = (int)(e / pieces);
+                if (r < rows) v[u] = __ldcg(reinterpret_cast<const uint4*>(x.row(r)) + (e - (size_t)r * pieces));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = base + u * stride;
+            if (e < total) {
+                const int r = (int)(e / pieces);
+                const size_t p = e - (size_t)r * pieces;
+                const int rt = r / kGemmN, rr = r % kGemmN;
+                const size_t kb = p / 8, j = p % 8;
+                char* dst = xt + ((size_t)rt * KB + kb) * kBTileBytes + rr * 128 + ((j ^ (size_t)(rr & 7)) << 4);
+                *reinterpret_cast<uint4*>(dst) = v[u];
+            }
+        }
+    }
+    fence_proxy_async_global();
+}
+
 // Rows of a token-level stage: the T rows of query q follow each other in its
 // query row, so row r of a contiguous batch is at base + r * (stride / T).
 __device__ __forceinline__ RowRef token_rows(const RowRef& q, int T) {
@@ -426,29 +442,41 @@ static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRe
     const int T = P.rows;
     const int rows = n * T;
     RowRef x = T > 1 ? token_rows(in, T) : in;
-    if (T > 1 && out.base != nullptr) out = token_rows(out, T);
+    if (T > 1 && out.base != nullptr && !P.out_tiled) out = token_rows(out, T);
     const int hfmt = P.kind == KIND_GEMM_FP8 ? OUT_E4M3 : OUT_BF16;
     const size_t hsz = P.kind == KIND_GEMM_FP8 ? 1 : 2;
+    // the first layer's operand: the input slot itself when the producer wrote
+    // it tiled, else a tiled copy
+    const char* xt = P.in_tiled ? in.base + in.first * in.stride : nullptr;
     for (int l = 0; l < P.n_layers; ++l) {
         const LayerParams& L = P.layer[l];
         const bool last = (l == P.n_layers - 1);
         LayerOut o;
         if (last && P.top_k == 0) {
-            o = LayerOut{out, hfmt, L.act, L.vscale, L.qscale};
+            o = LayerOut{out, hfmt, L.act, L.vscale, L.qscale, P.out_tiled, (size_t)L.N * hsz};
         } else if (last) {
             o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * sizeof(float)}, OUT_F32, L.act,
-                         L.vscale, 0.f};
-        } else {
+                         L.vscale, 0.f, 0, 0};
+        } else {   // hidden rows, tiled for the next layer
             o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * hsz}, hfmt, L.act, L.vscale,
-                         L.qscale};
+                         L.qscale, 1, (size_t)L.N * hsz};
         }
         float* Pbuf = reinterpret_cast<float*>(cx.scratch + L.p_off);
-        if (!gemm_layer_tasks(cx, L, x, rows, Pbuf, o)) return false;
+        if (xt == nullptr) {
+            char* buf = cx.scratch + P.tile_off;
+            retile_rows(cx, x, rows, (size_t)L.K * L.esz, buf);
+            if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+            xt = buf;
+        }
+        const bool ok = L.esz == 1 ? gemm_layer_tasks<1>(cx, L, xt, rows, Pbuf, o)
+                                   : gemm_layer_tasks<2>(cx, L, xt, rows, Pbuf, o);
+        if (!ok) return false;
         if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         if (L.C > 1) {
             gemm_reduce(cx, L, rows, Pbuf, o);
             if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         }
+        if (!last) xt = cx.scratch + L.h_off;   // written (and fenced) before the barriers above
         x = o.rows;
         if (last && P.top_k > 0) {
             if (T > 1) token_argmax(cx, x, n, T, L.N, P.res_k, fo);

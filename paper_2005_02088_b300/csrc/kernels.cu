@@ -168,6 +168,7 @@ __device__ unsigned int stageN_acquire(const PipeParams& P, int s, LeaderState& 
     }
 }
 
+template <uint32_t KINDS>
 __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams* __restrict__ pp) {
     extern __shared__ float4 smem4[];
     const PipeParams& P = *pp;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                     RowRef{reinterpret_cast<char*>(P.sink), first, P.cmask, P.sink_ld * sizeof(float)}};
         if (P.sink == nullptr) fo.logits.base = nullptr;
 
-        if (!stage_body(cx, SP, in, n, out, fo)) break;
+        if (!stage_body<KINDS>(cx, SP, in, n, out, fo)) break;
         if (!group_barrier(gs, cx.nctas, P.ctl, P.limit_ns, 300 + s)) break;
 
         // ---- the leader publishes the result and releases the input
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
 }
 
 // Direct launch of one stage over one batch: the whole grid is one instance.
+template <uint32_t KINDS>
 __global__ void __launch_bounds__(kThreads, 1)
     stage_direct_kernel(const StageParams* __restrict__ sp, RowRef in, int n, RowRef out,
                         int32_t* idx, float* val, RowRef logits, char* scratch, GroupSync* gs,
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     FinalOut fo{idx, val, logits};
     const bool tensor_stage = is_tensor_kind(sp->kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
-    stage_body(cx, *sp, in, n, out, fo);
+    stage_body<KINDS>(cx, *sp, in, n, out, fo);
     if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));
 }
 
@@ -341,30 +343,67 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Host-callable launch helpers (used by the runtime in runtime.cpp).
 namespace camelot {
-cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream) {
-    void* args[] = {(void*)&dparams};
-    return cudaLaunchCooperativeKernel((const void*)pipeline_kernel, dim3(grid), dim3(kThreads),
-                                       args, kSmemBytes, stream);
+
+// The instantiations: the four pipeline shapes of the workloads, every kind on
+// its own (direct launches), and all kinds together (any other pipeline).
+constexpr uint32_t kKindSets[] = {
+    kind_bit(KIND_NORMALIZE_U8), kind_bit(KIND_NORM_POOL2_BF16), kind_bit(KIND_MLP_FP32),
+    kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8), kind_bit(KIND_NORMALIZE_U8_E4M3),
+    kind_bit(KIND_EMBED_GATHER),
+    kind_bit(KIND_NORMALIZE_U8) | kind_bit(KIND_MLP_FP32),
+    kind_bit(KIND_NORM_POOL2_BF16) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
+    kind_bit(KIND_NORMALIZE_U8_E4M3) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
+    kind_bit(KIND_EMBED_GATHER) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
+    kAllKinds};
+constexpr int kNumSets = sizeof(kKindSets) / sizeof(kKindSets[0]);
+
+template <int... I>
+struct SetTable {
+    static const void* const pipe[sizeof...(I)];
+    static const void* const direct[sizeof...(I)];
+};
+template <int... I>
+const void* const SetTable<I...>::pipe[sizeof...(I)] = {(const void*)pipeline_kernel<kKindSets[I]>...};
+template <int... I>
+const void* const SetTable<I...>::direct[sizeof...(I)] = {(const void*)stage_direct_kernel<kKindSets[I]>...};
+using Table = SetTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10>;
+static_assert(kNumSets == 11, "instantiation table");
+
+// The first (narrowest) instantiation holding every kind in `kinds`.
+static int pick(uint32_t kinds) {
+    for (int i = 0; i < kNumSets; ++i)
+        if ((kKindSets[i] & kinds) == kinds) return i;
+    return kNumSets - 1;
 }
 
-cudaError_t launch_stage_direct(const StageParams* dsp, RowRef in, int n, RowRef out, int32_t* idx,
+cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream, uint32_t kinds) {
+    void* args[] = {(void*)&dparams};
+    return cudaLaunchCooperativeKernel(Table::pipe[pick(kinds)], dim3(grid), dim3(kThreads), args, kSmemBytes,
+                                       stream);
+}
+
+cudaError_t launch_stage_direct(const StageParams* dsp, int kind, RowRef in, int n, RowRef out, int32_t* idx,
                                 float* val, RowRef logits, char* scratch, GroupSync* gs, Ctl* ctl,
                                 long long limit_ns, int grid, cudaStream_t stream) {
     void* args[] = {(void*)&dsp, &in, &n, &out, &idx, &val, &logits, &scratch, &gs, &ctl, &limit_ns};
-    return cudaLaunchCooperativeKernel((const void*)stage_direct_kernel, dim3(grid), dim3(kThreads),
-                                       args, kSmemBytes, stream);
+    return cudaLaunchCooperativeKernel(Table::direct[pick(kind_bit(kind))], dim3(grid), dim3(kThreads), args,
+                                       kSmemBytes, stream);
 }
 
 cudaError_t configure_kernels() {
-    cudaError_t e = cudaFuncSetAttribute((const void*)pipeline_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)stage_direct_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    for (int i = 0; i < kNumSets; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(Table::pipe[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(Table::direct[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t max_coresident_ctas(int* per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)pipeline_kernel,
-                                                         kThreads, kSmemBytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, Table::pipe[kNumSets - 1], kThreads,
+                                                         kSmemBytes);
 }
 }  // namespace camelot

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     StageCtx cx{(int)blockIdx.x, (int)gridDim.x, gs, ctl, (uint64_t)limit_ns, 0u, base + header,
                 reinterpret_cast<float*>(smem4)};
     FinalOut fo{idx, val, logits};
-    stage_body(cx, sp, in, n, out, fo);
+    stage_body<kAllKinds & ~(kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8))>(cx, sp, in, n, out, fo);
 }
 
 }  // namespace camelot

@@ -20,8 +20,8 @@
 #include "pipeline_params.h"
 
 namespace camelot {
-cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream);
-cudaError_t launch_stage_direct(const StageParams* dsp, RowRef in, int n, RowRef out, int32_t* idx,
+cudaError_t launch_pipeline_kernel(const PipeParams* dparams, int grid, cudaStream_t stream, uint32_t kinds);
+cudaError_t launch_stage_direct(const StageParams* dsp, int kind, RowRef in, int n, RowRef out, int32_t* idx,
                                 float* val, RowRef logits, char* scratch, GroupSync* gs, Ctl* ctl,
                                 long long limit_ns, int grid, cudaStream_t stream);
 cudaError_t configure_kernels();
@@ -115,13 +115,15 @@ static int choose_kc(int K) {
 
 // Scratch layout of one instance for batches of up to B rows.
 static size_t layout_scratch(StageParams& sp, int B) {
-    size_t p_bytes = 0, h_bytes = 0;
+    size_t p_bytes = 0, h_bytes = 0, t_bytes = 0;
     for (int l = 0; l < sp.n_layers; ++l) {
         LayerParams& L = sp.layer[l];
         if (is_tensor_kind(sp.kind)) {
             const size_t rows = (size_t)B * std::max(1, sp.rows);
+            const size_t rows_pad = (rows + 31) / 32 * 32;   // hidden rows are kept tiled
             if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * rows * L.Npad * sizeof(float));
-            h_bytes = std::max(h_bytes, rows * L.Npad * sizeof(float));
+            h_bytes = std::max(h_bytes, rows_pad * L.Npad * sizeof(float));
+            t_bytes = std::max(t_bytes, (rows + 31) / 32 * 32 * (size_t)L.K * L.esz);
             continue;
         }
         const size_t G = (L.C + kWarps - 1) / kWarps;    // chunk groups
@@ -141,6 +143,8 @@ static size_t layout_scratch(StageParams& sp, int B) {
     }
     sp.res_off = off;
     off = align_up(off + (size_t)B * kMaxTopK * 8, 256);
+    sp.tile_off = off;
+    off = align_up(off + t_bytes, 256);
     return off;
 }
 
@@ -438,7 +442,7 @@ extern "C" camelot_status camelot_stage_launch(const camelot_stage* st, int n_ct
     RowRef rin{(char*)in, 0, ~0ull, sp.in_row_bytes};
     RowRef rout{(char*)out, 0, ~0ull, sp.out_row_bytes};
     RowRef rlog{(char*)out_logits, 0, ~0ull, sp.out_width * sizeof(float)};
-    CUDA_TRY(launch_stage_direct(st->d_sp, rin, (int)n, rout, out_idx, out_val, rlog,
+    CUDA_TRY(launch_stage_direct(st->d_sp, sp.kind, rin, (int)n, rout, out_idx, out_val, rlog,
                                  base + kDirectHeader, gs, ctl, 2000000000ll, n_ctas, s));
     return CAMELOT_OK;
 }
@@ -480,6 +484,8 @@ struct camelot_pipeline {
     camelot_handoff mode = CAMELOT_HANDOFF_GLOBAL;
     camelot_options opt{};
     int grid = 0;
+    uint32_t kinds = 0;                // bit k: some stage is of kind k
+    bool tiled[kMaxStages] = {};       // boundary s carries tiled rows
     PipeParams hp{};
     PipeParams* dp = nullptr;
     Ctl* ctl = nullptr;
@@ -654,7 +660,7 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
                                               sizeof(GroupSync) * p->hp.inst[p->n_stages - 1],
                                               p->kstream);
     if (e == cudaSuccess) e = cudaEventRecord(p->kstart, p->kstream);
-    if (e == cudaSuccess) e = launch_pipeline_kernel(p->dp, p->grid, p->kstream);
+    if (e == cudaSuccess) e = launch_pipeline_kernel(p->dp, p->grid, p->kstream, p->kinds);
     if (e == cudaSuccess) e = cudaEventRecord(p->kdone, p->kstream);
     if (e != cudaSuccess) {
         char buf[160];
@@ -671,6 +677,31 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
 // the producer's device slot to pinned host memory and from there into the
 // consumer's device slot; the copies run on one D2H and one H2D stream per
 // stage boundary, so consecutive batches overlap.
+// Copy the first `rows` rows of a batch slot: a plain copy of rows x rowb bytes,
+// or, for a tiled slot, the whole 32-row tiles plus, for a partial last tile,
+// the first rows x 128 bytes of each of its 4 KB tiles (one 2-D copy).
+// Returns the bytes moved.
+static size_t copy_batch_rows(char* dst, const char* src, size_t rows, size_t rowb, bool tiled,
+                              cudaMemcpyKind kind, cudaStream_t st, cudaError_t* e) {
+    if (!tiled) {
+        *e = cudaMemcpyAsync(dst, src, rows * rowb, kind, st);
+        return rows * rowb;
+    }
+    const size_t full = rows / 32, part = rows % 32, tile_set = 32 * rowb;   // bytes of one row tile
+    size_t moved = 0;
+    *e = cudaSuccess;
+    if (full) {
+        *e = cudaMemcpyAsync(dst, src, full * tile_set, kind, st);
+        moved += full * tile_set;
+    }
+    if (part && *e == cudaSuccess) {
+        const size_t off = full * tile_set;
+        *e = cudaMemcpy2DAsync(dst + off, 4096, src + off, 4096, part * 128, rowb / 128, kind, st);
+        moved += part * 128 * (rowb / 128);
+    }
+    return moved;
+}
+
 static void relay_main(camelot_pipeline* p) {
     cudaSetDevice(p->device);
     std::vector<uint64_t> cur(p->n_stages, 0);
@@ -686,12 +717,14 @@ static void relay_main(camelot_pipeline* p) {
             if (((volatile unsigned long long*)Bq.note_free)[b] != t) continue;
             std::atomic_thread_fence(std::memory_order_acquire);
             const unsigned n = ((volatile unsigned int*)A.note_n)[a];
-            const size_t bytes = (size_t)n * p->stages[s]->sp.out_row_bytes;
+            const size_t T = (size_t)std::max(1, p->stages[s]->sp.rows);
+            const size_t rowb = p->stages[s]->sp.out_row_bytes / T;
             char* stg = p->r_stage[s] + (size_t)b * A.slot_bytes;
             cudaError_t e = cudaMemcpyAsync(&p->r_hdr[s][b], &A.hdr[a], sizeof(BatchHdr),
                                             cudaMemcpyDeviceToHost, p->r_d2h[s]);
-            if (!e) e = cudaMemcpyAsync(stg, A.data + (size_t)a * A.slot_bytes, bytes,
-                                        cudaMemcpyDeviceToHost, p->r_d2h[s]);
+            size_t bytes = 0;
+            if (!e) bytes = copy_batch_rows(stg, A.data + (size_t)a * A.slot_bytes, (size_t)n * T, rowb, p->tiled[s],
+                                            cudaMemcpyDeviceToHost, p->r_d2h[s], &e);
             p->r_valA[s][a] = t + A.slots;
             if (!e) e = cudaMemcpyAsync(&A.seq[a], &p->r_valA[s][a], 8, cudaMemcpyHostToDevice,
                                         p->r_d2h[s]);
@@ -699,8 +732,8 @@ static void relay_main(camelot_pipeline* p) {
             if (!e) e = cudaStreamWaitEvent(p->r_h2d[s], p->r_ev[s][b], 0);
             if (!e) e = cudaMemcpyAsync(&Bq.hdr[b], &p->r_hdr[s][b], sizeof(BatchHdr),
                                         cudaMemcpyHostToDevice, p->r_h2d[s]);
-            if (!e) e = cudaMemcpyAsync(Bq.data + (size_t)b * Bq.slot_bytes, stg, bytes,
-                                        cudaMemcpyHostToDevice, p->r_h2d[s]);
+            if (!e) copy_batch_rows(Bq.data + (size_t)b * Bq.slot_bytes, stg, (size_t)n * T, rowb, p->tiled[s],
+                                    cudaMemcpyHostToDevice, p->r_h2d[s], &e);
             p->r_valB[s][b] = t + 1;
             if (!e) e = cudaMemcpyAsync(&Bq.seq[b], &p->r_valB[s][b], 8, cudaMemcpyHostToDevice,
                                         p->r_h2d[s]);
@@ -783,6 +816,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     p->mode = mode;
     p->opt = o;
     p->grid = total;
+    for (int s = 0; s < n_stages; ++s) p->kinds |= 1u << stages[s]->sp.kind;
     P_TRY(cudaStreamCreateWithFlags(&p->kstream, cudaStreamNonBlocking));
     P_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     P_TRY(cudaEventCreate(&p->kdone));
@@ -812,6 +846,16 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         inst += alloc->instances[s];
     }
     hp.cta_begin[n_stages] = cta;
+    // boundaries into a tensor-core stage carry the rows in its tiled operand
+    // layout when the producer can write it (no re-tiling pass per batch)
+    for (int s = 0; s + 1 < n_stages; ++s) {
+        const int pk = stages[s]->sp.kind, ck = stages[s + 1]->sp.kind;
+        const bool producer_can = pk == KIND_NORM_POOL2_BF16 || pk == KIND_NORMALIZE_U8_E4M3 ||
+                                  pk == KIND_EMBED_GATHER || is_tensor_kind(pk);
+        p->tiled[s] = is_tensor_kind(ck) && producer_can;
+        hp.st[s].out_tiled = p->tiled[s] ? 1 : 0;
+        hp.st[s + 1].in_tiled = p->tiled[s] ? 1 : 0;
+    }
     P_TRY(cudaMalloc(&p->ctl, sizeof(Ctl)));
     P_TRY(cudaMemset(p->ctl, 0, sizeof(Ctl)));
     P_TRY(cudaMalloc(&p->groups, sizeof(GroupSync) * inst));
@@ -827,7 +871,10 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     hp.scratch = p->scratch;
     // batch rings
     for (int s = 0; s + 1 < n_stages; ++s) {
-        const size_t slot_bytes = align_up((size_t)B * stages[s]->sp.out_row_bytes, 256);
+        const size_t T = (size_t)std::max(1, stages[s]->sp.rows);
+        const size_t slot_bytes = align_up(
+            p->tiled[s] ? tiled_bytes((size_t)B * T, stages[s]->sp.out_row_bytes / T)
+                        : (size_t)B * stages[s]->sp.out_row_bytes, 256);
         const bool staged = (mode == CAMELOT_HANDOFF_HOST_STAGED);
         // every producer and consumer instance of the boundary can hold a slot,
         // with as many again in flight

@@ -63,14 +63,31 @@ struct StageParams {
     int32_t rows;           // rows per query: tokens (EMBED_GATHER, token-level tensor-core stages), else 1
     int32_t res_k;          // results per query in the final-stage result arrays (top_k, or tags of
                             // the first tokens for a token-level stage)
-    int32_t pad_;
+    int32_t in_tiled;       // set per pipeline: the input rows arrive in the tiled layout below
+    int32_t out_tiled;      // set per pipeline: write the output rows in the tiled layout
+    int32_t pad_[3];
     size_t in_row_bytes;
     size_t out_row_bytes;   // 0 for final stages
     size_t out_width;       // final stages: width of the last layer (logits per query)
     size_t scratch_bytes;   // per instance (for max_batch)
     size_t res_off;         // scratch offset of final results: idx [B][5] int32, val [B][5] f32
+    size_t tile_off;        // tensor-core kinds: scratch offset of a layer's input in tiled form
     LayerParams layer[kMaxLayers];
 };
+
+// Tiled row layout read by the tensor-core stages (their MMA operand format):
+// rows of rowb bytes (a multiple of 128) in 32-row x 128-byte tiles; tile
+// (rt, kb) = rows 32 rt.. and bytes 128 kb.. of each row, 4 KB at
+// (rt * rowb / 128 + kb) * 4 KB; row r's 16-byte piece j at r * 128 +
+// (j ^ (r % 8)) * 16 inside it.  Byte `b` of row r:
+__host__ __device__ inline size_t tiled_offset(int r, size_t b, size_t rowb) {
+    const size_t p = b >> 4, kb = p >> 3, j = p & 7;
+    const int rr = r & 31;
+    return ((((size_t)(r >> 5) * (rowb >> 7)) + kb) << 12) + (size_t)rr * 128 + ((j ^ (size_t)(rr & 7)) << 4) +
+           (b & 15);
+}
+// Bytes a tiled batch of `rows` rows occupies (whole row tiles).
+__host__ __device__ inline size_t tiled_bytes(size_t rows, size_t rowb) { return (rows + 31) / 32 * 32 * rowb; }
 
 // Row addressing: row q is at base + ((first + q) & mask) * stride.  Ring
 // slots wrap with mask = slots - 1; contiguous buffers use mask = ~0.

@@ -114,7 +114,10 @@ static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowR
         const int32_t tok = reinterpret_cast<const int32_t*>(in.row(q))[t];
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (tok >= 0 && tok < V) v = __ldg(reinterpret_cast<const uint4*>(E + (size_t)tok * D) + c);
-        __stcg(reinterpret_cast<uint4*>(out.row(q) + t * (uint64_t)D * 2) + c, v);
+        if (P.out_tiled)
+            __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)(q * T + t), c * 16, (size_t)D * 2)), v);
+        else
+            __stcg(reinterpret_cast<uint4*>(out.row(q) + t * (uint64_t)D * 2) + c, v);
     }
 }
 
@@ -152,7 +155,11 @@ static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams
                     }
                     o[j] = packed;
                 }
-                __stcg(reinterpret_cast<uint4*>(out.row(q)) + c, make_uint4(o[0], o[1], o[2], o[3]));
+                const uint4 w4 = make_uint4(o[0], o[1], o[2], o[3]);
+                if (P.out_tiled)
+                    __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)q, c * 16, P.out_row_bytes)), w4);
+                else
+                    __stcg(reinterpret_cast<uint4*>(out.row(q)) + c, w4);
             }
         }
     }
@@ -188,7 +195,12 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
             const int i0 = 2 * w * C + c;
             const uint32_t s = (uint32_t)r0[i0] + r0[i0 + C] + r1[i0] + r1[i0 + C];
             const float y = (static_cast<float>(s) * 0.25f - 127.5f) * 0.015625f;
-            o[m] = __float2bfloat16_rn(y);
+            if (P.out_tiled)
+                *reinterpret_cast<__nv_bfloat16*>(out.base + tiled_offset(q, ((size_t)ho * out_vals + m) * 2,
+                                                                          P.out_row_bytes)) =
+                    __float2bfloat16_rn(y);
+            else
+                o[m] = __float2bfloat16_rn(y);
         }
         __syncwarp();
     }
