@@ -121,11 +121,13 @@ struct alignas(128) GroupSync {
     unsigned int pad0[31];
     unsigned int gen;
     unsigned int pad1[31];
-    // mailbox written by the leader before a barrier, read by all after it
+    unsigned int done;               // running count: batches finished by each non-leader CTA, summed
+    unsigned int pad_d[31];
+    // mailbox: the leader fills it, then releases mb_gen = batch number + 1
     unsigned int cmd;
     unsigned int n;
     unsigned int from_trace;
-    unsigned int pad2;
+    unsigned int mb_gen;
     unsigned long long in_ticket;    // input slot ticket (stage s >= 1)
     unsigned long long out_ticket;   // output slot ticket (non-final stages)
     unsigned long long first;        // first query ticket of the batch
@@ -164,6 +166,29 @@ __device__ __forceinline__ bool group_barrier(GroupSync* g, int nctas, Ctl* ctl,
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Bounded wait (one thread) until the 32-bit word at p equals v, read with
+// acquire semantics; records `err` at `where` and returns false on timeout or
+// on a pipeline error.
+__device__ __forceinline__ bool wait_eq32(const unsigned int* p, unsigned int v, Ctl* ctl, uint64_t limit_ns,
+                                          uint32_t where, uint32_t err) {
+    if (ld_acquire_gpu32(p) == v) return true;
+    Backoff bo(limit_ns);
+    while (ld_acquire_gpu32(p) != v) {
+        if ((bo.sparse() && has_error(ctl)) || !bo.step()) {
+            record_error(ctl, err, where);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 16-byte store of two 8-byte words to pinned host memory; each word is
+// single-copy atomic on its own.
+__device__ __forceinline__ void st_volatile_pair(unsigned long long* p, unsigned long long a,
+                                                 unsigned long long b) {
+    asm volatile("st.volatile.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 
 }  // namespace camelot

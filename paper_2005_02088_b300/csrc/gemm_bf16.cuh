@@ -2,16 +2,17 @@
 // cores, bf16 (kind::f16) or e4m3 (kind::f8f6f4) operands, f32 accumulation.
 //
 // Each layer computes y[q][m] = act(vscale * sum_k W[m][k] x[q][k]) for a batch
-// of at most 32 queries.  The batch is small, so the operands are swapped: the
-// weights are the M = 128 operand (128-row x 128-byte tiles, stored pre-tiled
-// and pre-swizzled as contiguous 16 KB blocks) and the queries are the N = 32
-// operand (32-row x 128-byte tiles: each layer first rewrites its input rows in
-// that tiled, swizzled form, 4 KB per tile).  One warp streams both operands
-// with 1-D bulk copies through a shared-memory ring; one thread in each of two
-// warps issues tcgen05.mma (M=128, N=32) into its own pair of TMEM
-// accumulators; four warps drain finished accumulators.  A unit is
-// (K-chunk, 128-row tile); chunk partials are added in chunk order, so the
-// result is the same whatever the number of CTAs.
+// of at most 32 queries (or of up to 8192 token rows).  The batch is small, so
+// the operands are swapped: the weights are the M = 128 operand (128-row x
+// 128-byte tiles, stored pre-tiled and pre-swizzled as contiguous 16 KB
+// blocks) and the input rows are the N operand (N = 32 for query batches, 128
+// for token-level stages; NT-row x 128-byte tiles in the same swizzled form,
+// written so by the producer or re-tiled once per layer).  One warp streams
+// both operands with 1-D bulk copies through a shared-memory ring; one thread
+// in each of two warps issues tcgen05.mma (M=128, N=NT) into its own pair of
+// TMEM accumulators; four warps drain finished accumulators.  A unit is
+// (row tile, K-chunk, 128-row weight tile); chunk partials are added in chunk
+// order, so the result is the same whatever the number of CTAs.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -23,14 +24,23 @@
 
 namespace camelot {
 
-constexpr int kGemmStages = 5;                   // ring depth
 constexpr int kKbPerStage = 2;                   // k-blocks per stage: one 32 KB weight copy
-constexpr int kGemmN = 32;                       // queries per MMA (N)
 constexpr uint32_t kATileBytes = 128 * 128;      // one weight tile: 128 rows x 128 bytes
-constexpr uint32_t kBTileBytes = kGemmN * 128;   // the matching query tile: 32 rows x 128 bytes
-constexpr uint32_t kStageBytes = kKbPerStage * (kATileBytes + kBTileBytes);   // 40 KB
+constexpr uint32_t kRingBytes = 200 * 1024;      // shared memory of the stage ring
+constexpr int kMaxGemmStages = 5;
 constexpr int kIssuers = 2;                      // MMA-issuing warps
-constexpr uint32_t kTmemCols = 2 * kIssuers * kGemmN;   // two 32-column accumulators per issuer
+constexpr uint32_t kTmemCols = 512;              // two accumulators per issuer, up to 128 columns each
+
+// Ring geometry for NT rows per MMA (N = 32 for batches of queries, 128 for
+// token-level stages): query tiles of NT rows x 128 bytes; stages of two weight
+// and two query tiles (40 KB / 64 KB), as many as fit the ring (5 / 3).
+template <int NT>
+struct RingGeom {
+    static constexpr uint32_t kBTile = NT * 128;
+    static constexpr uint32_t kStage = kKbPerStage * (kATileBytes + kBTile);
+    static constexpr int kStages = (int)(kRingBytes / kStage) < kMaxGemmStages ? (int)(kRingBytes / kStage)
+                                                                                 : kMaxGemmStages;
+};
 
 // Warp roles inside a CTA running tensor-core layers.
 constexpr int kWarpTma = 0;     // weight and query tiles, bulk copies
@@ -40,9 +50,9 @@ constexpr int kWarpEpi0 = 4;    // warps 4..7 read the accumulators
 __device__ __forceinline__ int issuer_of_warp(int warp) { return warp == 1 ? 0 : (warp == 3 ? 1 : -1); }
 
 struct GemmSmem {
-    char* ring;            // kGemmStages x (2 weight tiles, 32 KB, then 2 query tiles, 8 KB)
-    uint64_t* full;        // [kGemmStages] both operands landed (1 arrival + tx bytes)
-    uint64_t* empty;       // [kGemmStages] MMAs reading the stage are done
+    char* ring;            // stages of 2 weight tiles then 2 query tiles (RingGeom)
+    uint64_t* full;        // [stages] both operands landed (1 arrival + tx bytes)
+    uint64_t* empty;       // [stages] MMAs reading the stage are done
     uint64_t* tfull;       // [2 * kIssuers] accumulator complete
     uint64_t* tfree;       // [2 * kIssuers] accumulator read out (4 arrivals: epilogue warps)
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
@@ -55,10 +65,10 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
         (reinterpret_cast<uintptr_t>(smem) + 1023) & ~static_cast<uintptr_t>(1023));
     GemmSmem g;
     g.ring = base;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kGemmStages * kStageBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kRingBytes);
     g.full = bars;
-    g.empty = g.full + kGemmStages;
-    g.tfull = g.empty + kGemmStages;
+    g.empty = g.full + kMaxGemmStages;
+    g.tfull = g.empty + kMaxGemmStages;
     g.tfree = g.tfull + 2 * kIssuers;
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
     g.ring_it = g.tmem_slot + 1;
@@ -70,7 +80,7 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
 __device__ __forceinline__ void gemm_setup(float* smem) {
     GemmSmem g = gemm_smem(smem);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kGemmStages; ++s) {
+        for (int s = 0; s < kMaxGemmStages; ++s) {
             mbar_init(&g.full[s], 1);
             mbar_init(&g.empty[s], 1);
         }
@@ -129,6 +139,7 @@ struct LayerOut {
     float qscale;   // e4m3: the stored code is e4m3(value / qscale)
     int tiled;      // bf16 / e4m3 rows in the tiled layout (the next layer's operand), from rows.base
     size_t rowb;    // bytes per row (tiled)
+    int th;         // rows per tile (tiled)
 };
 
 __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float acc) {
@@ -137,11 +148,11 @@ __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float
         reinterpret_cast<float*>(o.rows.row(q))[m] = v;
     } else if (o.fmt == OUT_BF16) {
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        if (o.tiled) *reinterpret_cast<__nv_bfloat16*>(o.rows.base + tiled_offset(q, (size_t)m * 2, o.rowb)) = b;
+        if (o.tiled) *reinterpret_cast<__nv_bfloat16*>(o.rows.base + tiled_offset(q, (size_t)m * 2, o.rowb, o.th)) = b;
         else reinterpret_cast<__nv_bfloat16*>(o.rows.row(q))[m] = b;
     } else {
         const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v / o.qscale, __NV_SATFINITE, __NV_E4M3);
-        if (o.tiled) *reinterpret_cast<__nv_fp8_storage_t*>(o.rows.base + tiled_offset(q, (size_t)m, o.rowb)) = c;
+        if (o.tiled) *reinterpret_cast<__nv_fp8_storage_t*>(o.rows.base + tiled_offset(q, (size_t)m, o.rowb, o.th)) = c;
         else reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(q))[m] = c;
     }
 }
@@ -186,9 +197,14 @@ __device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, I
 // 8 KB bulk copy).
 // ESZ = bytes per operand element (2: bf16 / kind::f16, 1: e4m3 / kind::f8f6f4),
 // a template parameter so that each instantiation's MMA loop holds one kind.
-template <int ESZ>
+template <int ESZ, int NT>
 static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, const char* xt, int rows,
                                         float* Pbuf, const LayerOut& direct) {
+    using G = RingGeom<NT>;
+    constexpr int kGemmStages = G::kStages;
+    constexpr uint32_t kBTileBytes = G::kBTile;
+    constexpr uint32_t kStageBytes = G::kStage;
+    constexpr int kGemmN = NT;
     const GemmSmem g = gemm_smem(cx.smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int MT = L.Npad / 128;
@@ -225,6 +241,9 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
 
     if (u0 < u1) {
         if (warp == kWarpTma && lane == 0) {
+            // the operands were written by generic stores (other CTAs, other
+            // stages) and are read here by the async proxy
+            fence_proxy_async_global();
             // tiles (mt, kb) and (mt, kb+1) are adjacent in memory: one bulk copy
             const uint64_t pol = l2_policy_evict_last();
             const char* wt = reinterpret_cast<const char*>(L.w);
@@ -247,7 +266,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             });
         } else if (iw >= 0 && lane == 0) {
             constexpr bool f8 = ESZ == 1;
-            constexpr uint32_t idesc = f8 ? idesc_e4m3_f32(128, kGemmN) : idesc_bf16_f32(128, kGemmN);
+            constexpr uint32_t idesc = f8 ? idesc_e4m3_f32(128, NT) : idesc_bf16_f32(128, NT);
             uint32_t k = accb[iw];
             for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) mutable {
                 if ((r & 1) != iw) return true;
@@ -293,8 +312,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 return true;
             });
         } else if (warp >= kWarpEpi0) {
-            // accumulator rows 32 (warp % 4) .. +31, all 32 query columns; units
-            // in order, each from its issuer's accumulator
+            // accumulator rows 32 (warp % 4) .. +31, the NT query columns 32 at
+            // a time; units in order, each from its issuer's accumulator
             const int sub = warp & 3;
             uint32_t kw[kIssuers];
 #pragma unroll
@@ -307,22 +326,28 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const int acc = acc_of(w, k);
                 if (!mbar_wait_bounded(&g.tfull[acc], (k >> 1) & 1, cx, 6)) break;
                 tc_fence_after();
-                uint32_t r0[16], r1[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + acc * kGemmN;
-                tmem_ld16(ta, r0);
-                tmem_ld16(ta + 16, r1);
-                tmem_ld_wait();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&g.tfree[acc]);
                 const int m = mt * 128 + 32 * sub + lane;
-                if (m < N) {
+#pragma unroll 1
+                for (int q0 = 0; q0 < NT; q0 += 32) {
+                    uint32_t r0[16], r1[16];
+                    const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + acc * NT + q0;
+                    tmem_ld16(ta, r0);
+                    tmem_ld16(ta + 16, r1);
+                    tmem_ld_wait();
+                    if (q0 + 32 >= NT) {           // the accumulator has been read out
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&g.tfree[acc]);
+                    }
+                    if (m < N) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (row0 + j < rows) {
-                            const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                            if (C == 1) store_out(direct, row0 + j, m, v);
-                            else __stcg(Pbuf + ((size_t)c * rows + row0 + j) * Npad + m, v);
+                        for (int j = 0; j < 32; ++j) {
+                            const int row = row0 + q0 + j;
+                            if (row < rows) {
+                                const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
+                                if (C == 1) store_out(direct, row, m, v);
+                                else __stcg(Pbuf + ((size_t)c * rows + row) * Npad + m, v);
+                            }
                         }
                     }
                 }
@@ -393,15 +418,17 @@ static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int
 // The whole GEMM_BF16 / GEMM_FP8 stage.  Hidden rows and the rows handed to
 // the next stage are bf16 (GEMM_BF16) or e4m3 codes (GEMM_FP8); a final stage
 // keeps its logits in f32.
-// Rewrite `rows` input rows of `rowb` bytes (x) as 32-row x 128-byte tiles:
-// tile (rt, kb) at (rt * rowb / 128 + kb) * 4 KB, row r's 16-byte piece j at
-// r * 128 + (j ^ (r % 8)) * 16, the layout the MMA reads; rows past `rows` in
-// the last tile are zero.  All CTAs of the instance share the work; the
-// writes are fenced for the bulk copies that read them after the next barrier.
+// Rewrite `rows` input rows of `rowb` bytes (x) as NT-row x 128-byte tiles:
+// tile (rt, kb) at (rt * rowb / 128 + kb) * NT * 128, row r's 16-byte piece j
+// at (r % NT) * 128 + (j ^ (r % 8)) * 16, the layout the MMA reads; rows past
+// `rows` in the last tile are zero.  All CTAs of the instance share the work;
+// the writes are fenced for the bulk copies that read them after the next
+// barrier.
+template <int NT>
 static __device__ void retile_rows(const StageCtx& cx, RowRef x, int rows, size_t rowb, char* xt) {
     const size_t pieces = rowb / 16;
     const size_t KB = rowb / 128;
-    const size_t total = (size_t)((rows + kGemmN - 1) / kGemmN) * kGemmN * pieces;
+    const size_t total = (size_t)((rows + NT - 1) / NT) * NT * pieces;
     const size_t stride = (size_t)cx.nctas * kThreads;
     constexpr int U = 8;                             // loads in flight per thread
     for (size_t base = (size_t)cx.rank * kThreads + threadIdx.x; base < total; base += U * stride) {
@@ -421,9 +448,9 @@ static __device__ void retile_rows(const StageCtx& cx, RowRef x, int rows, size_
             if (e < total) {
                 const int r = (int)(e / pieces);
                 const size_t p = e - (size_t)r * pieces;
-                const int rt = r / kGemmN, rr = r % kGemmN;
+                const int rt = r / NT, rr = r % NT;
                 const size_t kb = p / 8, j = p % 8;
-                char* dst = xt + ((size_t)rt * KB + kb) * kBTileBytes + rr * 128 + ((j ^ (size_t)(rr & 7)) << 4);
+                char* dst = xt + ((size_t)rt * KB + kb) * (NT * 128) + rr * 128 + ((j ^ (size_t)(rr & 7)) << 4);
                 *reinterpret_cast<uint4*>(dst) = v[u];
             }
         }
@@ -437,8 +464,9 @@ __device__ __forceinline__ RowRef token_rows(const RowRef& q, int T) {
     return RowRef{q.base + q.first * q.stride, 0, ~0ull, q.stride / (size_t)T};
 }
 
-static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
-                                 RowRef out, const FinalOut& fo) {
+template <int NT>
+static __device__ bool gemm_body_nt(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                                    RowRef out, const FinalOut& fo) {
     const int T = P.rows;
     const int rows = n * T;
     RowRef x = T > 1 ? token_rows(in, T) : in;
@@ -453,23 +481,23 @@ static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRe
         const bool last = (l == P.n_layers - 1);
         LayerOut o;
         if (last && P.top_k == 0) {
-            o = LayerOut{out, hfmt, L.act, L.vscale, L.qscale, P.out_tiled, (size_t)L.N * hsz};
+            o = LayerOut{out, hfmt, L.act, L.vscale, L.qscale, P.out_tiled, (size_t)L.N * hsz, P.out_tile_h};
         } else if (last) {
             o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * sizeof(float)}, OUT_F32, L.act,
-                         L.vscale, 0.f, 0, 0};
+                         L.vscale, 0.f, 0, 0, NT};
         } else {   // hidden rows, tiled for the next layer
             o = LayerOut{RowRef{cx.scratch + L.h_off, 0, ~0ull, (size_t)L.N * hsz}, hfmt, L.act, L.vscale,
-                         L.qscale, 1, (size_t)L.N * hsz};
+                         L.qscale, 1, (size_t)L.N * hsz, NT};
         }
         float* Pbuf = reinterpret_cast<float*>(cx.scratch + L.p_off);
         if (xt == nullptr) {
             char* buf = cx.scratch + P.tile_off;
-            retile_rows(cx, x, rows, (size_t)L.K * L.esz, buf);
+            retile_rows<NT>(cx, x, rows, (size_t)L.K * L.esz, buf);
             if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
             xt = buf;
         }
-        const bool ok = L.esz == 1 ? gemm_layer_tasks<1>(cx, L, xt, rows, Pbuf, o)
-                                   : gemm_layer_tasks<2>(cx, L, xt, rows, Pbuf, o);
+        const bool ok = L.esz == 1 ? gemm_layer_tasks<1, NT>(cx, L, xt, rows, Pbuf, o)
+                                   : gemm_layer_tasks<2, NT>(cx, L, xt, rows, Pbuf, o);
         if (!ok) return false;
         if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         if (L.C > 1) {
@@ -484,6 +512,13 @@ static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRe
         }
     }
     return true;
+}
+
+// Query-batch stages stream 32-row operand tiles, token-level stages 128-row
+// tiles (four times the work per MMA at about the same issue cost).
+static __device__ bool gemm_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                                 RowRef out, const FinalOut& fo) {
+    return P.tile_h == 128 ? gemm_body_nt<128>(cx, P, in, n, out, fo) : gemm_body_nt<32>(cx, P, in, n, out, fo);
 }
 
 }  // namespace camelot

@@ -15,10 +15,17 @@ struct LeaderState {
     unsigned long long seen_h;   // oldest waiting ticket the trigger has seen ...
     uint64_t seen_t;             // ... and since when (device clock)
     uint64_t idle_since;
+    unsigned int polls;          // acquisition attempts (the host's stop flag is read on every 16th)
 };
 
 __device__ __forceinline__ bool stop_requested(const PipeParams& P) {
     return *P.host_stop != 0ull || has_error(P.ctl);
+}
+// The stop flag lives in host memory (a PCIe round trip per read): the
+// acquisition loops read it on every 16th attempt only, and the device error
+// word on every attempt.
+__device__ __forceinline__ bool stop_check(const PipeParams& P, LeaderState& ls) {
+    return (ls.polls++ & 15u) == 0 ? stop_requested(P) : has_error(P.ctl);
 }
 
 // Claim a free slot of `r` for a new ticket (producer side).  Returns false on
@@ -42,15 +49,15 @@ __device__ bool reserve_out(const PipeParams& P, const RingDev& r, uint32_t wher
 // Stage 0: the wait queue and batch trigger (Sec. 5.2 steps 1-2).  A batch of
 // the oldest waiting tickets leaves when B of them are ready, or when the
 // oldest has waited max_wait_ns.  Executed by warp 0 of the leader CTA; lane 0
-// returns the command.  Writes the per-query metadata of the claimed tickets
-// into their completion slots.
+// returns the command.  Records the arrival time and stream of the claimed
+// tickets for the final stage.
 __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
                                        unsigned long long* first, unsigned int* n_out,
                                        bool* from_trace, long long* t_batch) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         // every decision below is taken on lane 0's view, so the warp stays converged
-        const int stop = __shfl_sync(0xffffffffu, lane == 0 ? (int)stop_requested(P) : 0, 0);
+        const int stop = __shfl_sync(0xffffffffu, lane == 0 ? (int)stop_check(P, ls) : 0, 0);
         if (stop) return CMD_EXIT;
         const unsigned long long h =
             __shfl_sync(0xffffffffu, *(volatile unsigned long long*)&P.ctl->in_head.v, 0);
@@ -111,13 +118,9 @@ __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
         if (got != h) continue;
         // the tickets [h, h + kk) are ours: record their metadata
         if (lane < kk) {
-            camelot_completion& c = P.comp[(h + lane) & P.cmask].c;
-            c.query_id = h + lane;
-            c.stream_id = sid;
-            c.status = 0;
-            c.batch_size = kk;
-            c.t_arrival_ns = arr;
-            c.t_batch_ns = (long long)now;
+            QMeta& m = P.meta[(h + lane) & P.cmask];
+            m.t_arrival = arr;
+            m.stream_id = sid;
         }
         *first = h;
         *n_out = (unsigned)kk;
@@ -136,7 +139,7 @@ __device__ unsigned int stageN_acquire(const PipeParams& P, int s, LeaderState& 
     const unsigned long long* up_tail = P.out_ring[s - 1].tail;
     const uint64_t bound = (uint64_t)P.idle_ns * (uint64_t)(s + 2) + (uint64_t)P.limit_ns;
     for (;;) {
-        if (stop_requested(P)) return CMD_EXIT;
+        if (stop_check(P, ls)) return CMD_EXIT;
         const unsigned long long h = *(volatile unsigned long long*)r.head;
         const unsigned long long sq = ld_acquire_gpu(&r.seq[h % r.slots]);
         if (sq == h + 1) {
@@ -186,53 +189,71 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     const bool final_stage = (s == P.n_stages - 1);
     const bool leader = (rank == 0);
 
-    __shared__ unsigned int sh_cmd, sh_n, sh_trace;
+    __shared__ unsigned int sh_cmd, sh_n, sh_trace, sh_ok;
     __shared__ unsigned long long sh_in, sh_first, sh_out;
     __shared__ long long sh_tb;
-    LeaderState ls{~0ull, 0, gtime()};
+    LeaderState ls{~0ull, 0, gtime(), 0u};
     const bool tensor_stage = is_tensor_kind(SP.kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
+    const bool grouped = cx.nctas > 1;
+    // the other CTAs wait for the leader's post for as long as the leader may idle
+    const uint64_t post_wait = (uint64_t)P.idle_ns * (uint64_t)(P.n_stages + 2) + 2ull * (uint64_t)P.limit_ns;
 
-    for (;;) {
-        // ---- the leader finds work and posts it in the instance's mailbox
-        if (leader && threadIdx.x < 32) {
-            unsigned int cmd, n = 0;
-            unsigned long long in_t = 0, first = 0, out_t = 0;
-            bool tr = false;
-            long long tb = 0;
-            if (s == 0) {
-                cmd = stage0_acquire(P, ls, &first, &n, &tr, &tb);
-                in_t = first;
+    // Per batch: the leader acquires the work and posts it in the instance's
+    // mailbox (releasing mb_gen = k + 1); every other CTA waits for that post,
+    // runs its part of the body and adds one to the done count; the leader,
+    // after its own part, waits for done = (k + 1) (CTAs - 1) and publishes the
+    // batch.  One post and one count per batch, instead of two full barriers.
+    for (unsigned int k = 0;; ++k) {
+        // ---- the leader finds work and posts it
+        if (leader) {
+            if (threadIdx.x < 32) {
+                unsigned int cmd, n = 0;
+                unsigned long long in_t = 0, first = 0, out_t = 0;
+                bool tr = false;
+                long long tb = 0;
+                if (s == 0) {
+                    cmd = stage0_acquire(P, ls, &first, &n, &tr, &tb);
+                    in_t = first;
+                } else {
+                    if (threadIdx.x == 0) cmd = stageN_acquire(P, s, ls, &in_t, &first, &n, &tb);
+                    cmd = __shfl_sync(0xffffffffu, cmd, 0);
+                }
+                if (threadIdx.x == 0) {
+                    if (cmd == CMD_WORK && !final_stage && !reserve_out(P, P.out_ring[s], s, &out_t))
+                        cmd = CMD_EXIT;
+                    sh_cmd = cmd;
+                    sh_n = n;
+                    sh_in = in_t;
+                    sh_out = out_t;
+                    sh_tb = tb;
+                    sh_trace = tr ? 1u : 0u;
+                    sh_first = first;
+                    if (grouped) {
+                        gs->cmd = cmd;
+                        gs->n = n;
+                        gs->in_ticket = in_t;
+                        gs->out_ticket = out_t;
+                        gs->t_batch = tb;
+                        gs->from_trace = tr ? 1u : 0u;
+                        gs->first = first;
+                        st_release_gpu32(&gs->mb_gen, k + 1u);
+                    }
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            if (wait_eq32(&gs->mb_gen, k + 1u, P.ctl, post_wait, 200 + s, DEV_ERR_MAILBOX)) {
+                volatile GroupSync* vg = gs;
+                sh_cmd = vg->cmd;
+                sh_n = vg->n;
+                sh_in = vg->in_ticket;
+                sh_out = vg->out_ticket;
+                sh_tb = vg->t_batch;
+                sh_trace = vg->from_trace;
+                sh_first = vg->first;
             } else {
-                if (threadIdx.x == 0) cmd = stageN_acquire(P, s, ls, &in_t, &first, &n, &tb);
-                cmd = __shfl_sync(0xffffffffu, cmd, 0);
+                sh_cmd = CMD_EXIT;
             }
-            if (threadIdx.x == 0) {
-                if (cmd == CMD_WORK && !final_stage && !reserve_out(P, P.out_ring[s], s, &out_t))
-                    cmd = CMD_EXIT;
-                gs->cmd = cmd;
-                gs->n = n;
-                gs->in_ticket = in_t;
-                gs->out_ticket = out_t;
-                gs->t_batch = tb;
-                gs->from_trace = tr ? 1u : 0u;
-                gs->first = first;
-            }
-        }
-        // ---- broadcast (a group barrier whose wait covers the leader's idle time)
-        if (!group_barrier(gs, cx.nctas, P.ctl, (uint64_t)P.idle_ns * (uint64_t)(P.n_stages + 2) +
-                                                     2ull * (uint64_t)P.limit_ns,
-                           200 + s, DEV_ERR_MAILBOX))
-            break;
-        if (threadIdx.x == 0) {
-            volatile GroupSync* vg = gs;
-            sh_cmd = vg->cmd;
-            sh_n = vg->n;
-            sh_in = vg->in_ticket;
-            sh_out = vg->out_ticket;
-            sh_tb = vg->t_batch;
-            sh_trace = vg->from_trace;
-            sh_first = vg->first;
         }
         __syncthreads();
         if (sh_cmd != CMD_WORK) break;
@@ -264,54 +285,88 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
         if (P.sink == nullptr) fo.logits.base = nullptr;
 
         if (!stage_body<KINDS>(cx, SP, in, n, out, fo)) break;
-        if (!group_barrier(gs, cx.nctas, P.ctl, P.limit_ns, 300 + s)) break;
+
+        // ---- end of the batch: the other CTAs report, the leader collects
+        __syncthreads();
+        if (!leader) {
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&gs->done, 1u);
+            }
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            sh_ok = grouped ? wait_eq32(&gs->done, (k + 1u) * (unsigned)(cx.nctas - 1), P.ctl, P.limit_ns, 300 + s,
+                                        DEV_ERR_GROUP_BARRIER)
+                            : !has_error(P.ctl);
+            __threadfence();
+        }
+        __syncthreads();
+        if (!sh_ok) break;
 
         // ---- the leader publishes the result and releases the input
-        if (leader) {
-            if (final_stage) {
-                __shared__ long long sh_done;
-                if (threadIdx.x == 0) sh_done = (long long)gtime();
-                __syncthreads();
-                const int k = SP.res_k;
-                for (int q = threadIdx.x; q < n; q += kThreads) {
-                    CompSlot& cs = P.comp[(first + q) & P.cmask];
-                    for (int r = 0; r < kMaxTopK; ++r) {
-                        cs.c.idx[r] = r < k ? fo.idx[(size_t)q * k + r] : -1;
-                        cs.c.val[r] = r < k ? fo.val[(size_t)q * k + r] : 0.f;
-                    }
-                    cs.c.t_done_ns = sh_done;
-                    __threadfence_system();
-                    st_release_sys(&cs.seq, first + q + 1);
+        if (final_stage) {
+            // completion records: data and flag in every 8-byte word (no
+            // system-scope fence); the logits rows are ordered before them
+            __shared__ long long sh_done;
+            if (threadIdx.x == 0) sh_done = (long long)gtime();
+            __syncthreads();
+            if (P.sink != nullptr) __threadfence();
+            const int kr = SP.res_k;
+            for (int q = threadIdx.x; q < n; q += kThreads) {
+                const unsigned long long t = first + q;
+                const unsigned long long f = (unsigned long long)(uint32_t)(t + 1ull) << 32;
+                const QMeta m = P.meta[t & P.cmask];
+                uint32_t d[kCompWords];
+                d[CW_STREAM] = m.stream_id;
+                d[CW_STATUS] = 0u;
+                d[CW_BATCH] = (uint32_t)n;
+                d[CW_T_ARR] = (uint32_t)(unsigned long long)m.t_arrival;
+                d[CW_T_ARR_HI] = (uint32_t)((unsigned long long)m.t_arrival >> 32);
+                d[CW_T_BATCH] = (uint32_t)(unsigned long long)sh_tb;
+                d[CW_T_BATCH_HI] = (uint32_t)((unsigned long long)sh_tb >> 32);
+                d[CW_T_DONE] = (uint32_t)(unsigned long long)sh_done;
+                d[CW_T_DONE_HI] = (uint32_t)((unsigned long long)sh_done >> 32);
+#pragma unroll
+                for (int r = 0; r < kMaxTopK; ++r) {
+                    d[CW_IDX + r] = r < kr ? (uint32_t)fo.idx[(size_t)q * kr + r] : 0xffffffffu;
+                    d[CW_VAL + r] = r < kr ? __float_as_uint(fo.val[(size_t)q * kr + r]) : 0u;
                 }
-            } else if (threadIdx.x == 0) {
-                const RingDev& r = P.out_ring[s];
-                const unsigned int slot = (unsigned int)(sh_out % r.slots);
-                BatchHdr& hd = r.hdr[slot];
-                hd.first = first;
-                hd.n = (unsigned)n;
-                hd.t_batch = sh_tb;
-                __threadfence();
-                st_release_gpu(&r.seq[slot], sh_out + 1);
-                if (r.note_pub != nullptr) {
-                    r.note_n[slot] = (unsigned)n;
-                    __threadfence_system();
-                    st_release_sys(&r.note_pub[slot], sh_out + 1);
-                }
+#pragma unroll
+                for (int i = CW_USED; i < kCompWords; ++i) d[i] = 0u;
+                unsigned long long* w = P.comp[t & P.cmask].w;
+#pragma unroll
+                for (int i = 0; i < kCompWords; i += 2) st_volatile_pair(w + i, f | d[i], f | d[i + 1]);
             }
-            if (s == 0) {
-                if (!sh_trace) {
-                    const unsigned long long R = P.qmask + 1;
-                    for (int q = threadIdx.x; q < n; q += kThreads)
-                        st_release_sys(&P.qring[(first + q) & P.qmask].seq, first + q + R);
-                }
-            } else if (threadIdx.x == 0) {
-                const RingDev& r = P.in_ring[s];
-                const unsigned int slot = (unsigned int)(sh_in % r.slots);
-                st_release_gpu(&r.seq[slot], sh_in + r.slots);
-                if (r.note_free != nullptr) st_release_sys(&r.note_free[slot], sh_in + r.slots);
+        } else if (threadIdx.x == 0) {
+            const RingDev& r = P.out_ring[s];
+            const unsigned int slot = (unsigned int)(sh_out % r.slots);
+            BatchHdr& hd = r.hdr[slot];
+            hd.first = first;
+            hd.n = (unsigned)n;
+            hd.t_batch = sh_tb;
+            __threadfence();
+            st_release_gpu(&r.seq[slot], sh_out + 1);
+            if (r.note_pub != nullptr) {
+                r.note_n[slot] = (unsigned)n;
+                __threadfence_system();
+                st_release_sys(&r.note_pub[slot], sh_out + 1);
             }
-            if (threadIdx.x == 0) atomicAdd(&P.ctl->batches[s].v, 1ull);
         }
+        if (s == 0) {
+            if (!sh_trace) {
+                const unsigned long long R = P.qmask + 1;
+                for (int q = threadIdx.x; q < n; q += kThreads)
+                    st_release_sys(&P.qring[(first + q) & P.qmask].seq, first + q + R);
+            }
+        } else if (threadIdx.x == 0) {
+            const RingDev& r = P.in_ring[s];
+            const unsigned int slot = (unsigned int)(sh_in % r.slots);
+            st_release_gpu(&r.seq[slot], sh_in + r.slots);
+            if (r.note_free != nullptr) st_release_sys(&r.note_free[slot], sh_in + r.slots);
+        }
+        if (threadIdx.x == 0) atomicAdd(&P.ctl->batches[s].v, 1ull);
+        __syncthreads();   // the leader's shared mailbox copy is rewritten next
     }
     __syncthreads();
     if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));

@@ -50,10 +50,27 @@ struct QDesc {
     unsigned long long pad2;
 };
 
-// Completion ring entry (pinned, mapped host memory), indexed by ticket.
-struct CompSlot {
-    camelot_completion c;
-    volatile unsigned long long seq;   // ticket + 1 once complete
+// Completion ring entry (pinned, mapped host memory), indexed by ticket t.
+// Every 8-byte word carries 32 bits of the completion in its low half and the
+// flag (t + 1, truncated to 32 bits) in its high half.  Aligned 8-byte stores
+// are single-copy atomic, so the host holds a whole record once every word
+// shows the flag: the device writes data and flags together, with no
+// system-scope fence between them.
+enum CompWord : int {
+    CW_STREAM = 0, CW_STATUS, CW_BATCH, CW_T_ARR, CW_T_ARR_HI, CW_T_BATCH, CW_T_BATCH_HI, CW_T_DONE,
+    CW_T_DONE_HI, CW_IDX, CW_VAL = CW_IDX + kMaxTopK, CW_USED = CW_VAL + kMaxTopK
+};
+constexpr int kCompWords = (CW_USED + 1) / 2 * 2;   // whole 16-byte pairs
+struct alignas(16) CompSlot {
+    unsigned long long w[kCompWords];
+};
+
+// Per-query metadata the batch trigger records for the final stage (device
+// memory, indexed by ticket like the completion ring).
+struct QMeta {
+    long long t_arrival;
+    unsigned int stream_id;
+    unsigned int pad;
 };
 
 // A trace of device-resident queries (device memory).
@@ -93,6 +110,7 @@ struct PipeParams {
     unsigned long long dmask;       // query data ring mask
     size_t q_row;
     CompSlot* comp;
+    QMeta* meta;                // device [cmask + 1]
     unsigned long long cmask;
     float* sink;
     size_t sink_ld;             // floats per sink row

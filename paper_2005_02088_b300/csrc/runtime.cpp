@@ -120,10 +120,11 @@ static size_t layout_scratch(StageParams& sp, int B) {
         LayerParams& L = sp.layer[l];
         if (is_tensor_kind(sp.kind)) {
             const size_t rows = (size_t)B * std::max(1, sp.rows);
-            const size_t rows_pad = (rows + 31) / 32 * 32;   // hidden rows are kept tiled
+            const size_t th = (size_t)sp.tile_h;
+            const size_t rows_pad = (rows + th - 1) / th * th;   // hidden rows are kept tiled
             if (L.C > 1) p_bytes = std::max(p_bytes, (size_t)L.C * rows * L.Npad * sizeof(float));
             h_bytes = std::max(h_bytes, rows_pad * L.Npad * sizeof(float));
-            t_bytes = std::max(t_bytes, (rows + 31) / 32 * 32 * (size_t)L.K * L.esz);
+            t_bytes = std::max(t_bytes, rows_pad * (size_t)L.K * L.esz);
             continue;
         }
         const size_t G = (L.C + kWarps - 1) / kWarps;    // chunk groups
@@ -162,6 +163,8 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
     sp.top_k = d->top_k;
     sp.max_batch = d->max_batch;
     sp.rows = 1;
+    sp.tile_h = 32;
+    sp.out_tile_h = 32;
     sp.res_k = d->top_k;
     auto* st = new camelot_stage();
     st->desc = *d;
@@ -251,6 +254,7 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             if ((size_t)T * d->max_batch > 8192)
                 return bail(fail(CAMELOT_EINVAL, "rows_per_query x max_batch exceeds 8192 rows"));
             sp.rows = T;
+            sp.tile_h = T > 1 ? 128 : 32;
             sp.res_k = T > 1 && d->top_k ? std::min(T, kMaxTopK) : d->top_k;
             if (L < 1 || L > kMaxLayers) return bail(fail(CAMELOT_EINVAL, "n_layers %d outside 1..4", L));
             if (d->max_batch > 32) return bail(fail(CAMELOT_EINVAL, "tensor-core stages take batches of at most 32"));
@@ -499,6 +503,7 @@ struct camelot_pipeline {
     char* qdata = nullptr;             // pinned (device_data = 0) or device memory
     cudaStream_t h2d = nullptr;        // device_data: submit's copies
     CompSlot* comp = nullptr;          // pinned
+    QMeta* meta = nullptr;             // device
     TraceDev* trace = nullptr;         // device
     cudaStream_t kstream = nullptr, side = nullptr;
     cudaEvent_t kdone = nullptr, kstart = nullptr;
@@ -608,6 +613,7 @@ static void pipeline_free(camelot_pipeline* p) {
     }
     if (p->h2d) cudaStreamDestroy(p->h2d);
     if (p->comp) cudaFreeHost(p->comp);
+    if (p->meta) cudaFree(p->meta);
     if (p->kdone) cudaEventDestroy(p->kdone);
     if (p->kstart) cudaEventDestroy(p->kstart);
     if (p->kstream) cudaStreamDestroy(p->kstream);
@@ -678,16 +684,16 @@ static camelot_status check_and_run(camelot_pipeline* p, bool want_running) {
 // consumer's device slot; the copies run on one D2H and one H2D stream per
 // stage boundary, so consecutive batches overlap.
 // Copy the first `rows` rows of a batch slot: a plain copy of rows x rowb bytes,
-// or, for a tiled slot, the whole 32-row tiles plus, for a partial last tile,
-// the first rows x 128 bytes of each of its 4 KB tiles (one 2-D copy).
-// Returns the bytes moved.
-static size_t copy_batch_rows(char* dst, const char* src, size_t rows, size_t rowb, bool tiled,
+// or, for a slot tiled in th-row tiles (th > 0), the whole row tiles plus, for
+// a partial last tile, the first rows x 128 bytes of each of its th x 128-byte
+// tiles (one 2-D copy).  Returns the bytes moved.
+static size_t copy_batch_rows(char* dst, const char* src, size_t rows, size_t rowb, int th,
                               cudaMemcpyKind kind, cudaStream_t st, cudaError_t* e) {
-    if (!tiled) {
+    if (th == 0) {
         *e = cudaMemcpyAsync(dst, src, rows * rowb, kind, st);
         return rows * rowb;
     }
-    const size_t full = rows / 32, part = rows % 32, tile_set = 32 * rowb;   // bytes of one row tile
+    const size_t full = rows / th, part = rows % th, tile_set = (size_t)th * rowb;   // bytes of one row tile
     size_t moved = 0;
     *e = cudaSuccess;
     if (full) {
@@ -695,8 +701,8 @@ static size_t copy_batch_rows(char* dst, const char* src, size_t rows, size_t ro
         moved += full * tile_set;
     }
     if (part && *e == cudaSuccess) {
-        const size_t off = full * tile_set;
-        *e = cudaMemcpy2DAsync(dst + off, 4096, src + off, 4096, part * 128, rowb / 128, kind, st);
+        const size_t off = full * tile_set, pitch = (size_t)th * 128;
+        *e = cudaMemcpy2DAsync(dst + off, pitch, src + off, pitch, part * 128, rowb / 128, kind, st);
         moved += part * 128 * (rowb / 128);
     }
     return moved;
@@ -723,7 +729,8 @@ static void relay_main(camelot_pipeline* p) {
             cudaError_t e = cudaMemcpyAsync(&p->r_hdr[s][b], &A.hdr[a], sizeof(BatchHdr),
                                             cudaMemcpyDeviceToHost, p->r_d2h[s]);
             size_t bytes = 0;
-            if (!e) bytes = copy_batch_rows(stg, A.data + (size_t)a * A.slot_bytes, (size_t)n * T, rowb, p->tiled[s],
+            const int th = p->tiled[s] ? p->stages[s + 1]->sp.tile_h : 0;
+            if (!e) bytes = copy_batch_rows(stg, A.data + (size_t)a * A.slot_bytes, (size_t)n * T, rowb, th,
                                             cudaMemcpyDeviceToHost, p->r_d2h[s], &e);
             p->r_valA[s][a] = t + A.slots;
             if (!e) e = cudaMemcpyAsync(&A.seq[a], &p->r_valA[s][a], 8, cudaMemcpyHostToDevice,
@@ -732,7 +739,7 @@ static void relay_main(camelot_pipeline* p) {
             if (!e) e = cudaStreamWaitEvent(p->r_h2d[s], p->r_ev[s][b], 0);
             if (!e) e = cudaMemcpyAsync(&Bq.hdr[b], &p->r_hdr[s][b], sizeof(BatchHdr),
                                         cudaMemcpyHostToDevice, p->r_h2d[s]);
-            if (!e) copy_batch_rows(Bq.data + (size_t)b * Bq.slot_bytes, stg, (size_t)n * T, rowb, p->tiled[s],
+            if (!e) copy_batch_rows(Bq.data + (size_t)b * Bq.slot_bytes, stg, (size_t)n * T, rowb, th,
                                     cudaMemcpyHostToDevice, p->r_h2d[s], &e);
             p->r_valB[s][b] = t + 1;
             if (!e) e = cudaMemcpyAsync(&Bq.seq[b], &p->r_valB[s][b], 8, cudaMemcpyHostToDevice,
@@ -854,6 +861,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
                                   pk == KIND_EMBED_GATHER || is_tensor_kind(pk);
         p->tiled[s] = is_tensor_kind(ck) && producer_can;
         hp.st[s].out_tiled = p->tiled[s] ? 1 : 0;
+        hp.st[s].out_tile_h = stages[s + 1]->sp.tile_h;
         hp.st[s + 1].in_tiled = p->tiled[s] ? 1 : 0;
     }
     P_TRY(cudaMalloc(&p->ctl, sizeof(Ctl)));
@@ -873,7 +881,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     for (int s = 0; s + 1 < n_stages; ++s) {
         const size_t T = (size_t)std::max(1, stages[s]->sp.rows);
         const size_t slot_bytes = align_up(
-            p->tiled[s] ? tiled_bytes((size_t)B * T, stages[s]->sp.out_row_bytes / T)
+            p->tiled[s] ? tiled_bytes((size_t)B * T, stages[s]->sp.out_row_bytes / T, stages[s + 1]->sp.tile_h)
                         : (size_t)B * stages[s]->sp.out_row_bytes, 256);
         const bool staged = (mode == CAMELOT_HANDOFF_HOST_STAGED);
         // every producer and consumer instance of the boundary can hold a slot,
@@ -921,6 +929,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     P_TRY(cudaHostAlloc((void**)&p->comp, R * sizeof(CompSlot), cudaHostAllocMapped | cudaHostAllocPortable));
     memset((void*)p->qring, 0, R * sizeof(QDesc));
     memset((void*)p->comp, 0, R * sizeof(CompSlot));
+    P_TRY(cudaMalloc(&p->meta, R * sizeof(QMeta)));
     for (size_t i = 0; i < R; ++i) p->qring[i].seq = i;
     hp.qring = p->qring;
     hp.qdata = p->qdata;
@@ -928,6 +937,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     hp.dmask = D - 1;
     hp.q_row = q_row;
     hp.comp = p->comp;
+    hp.meta = p->meta;
     hp.cmask = R - 1;
     hp.sink = o.logits_sink;
     hp.sink_ld = stages[n_stages - 1]->sp.out_width;
@@ -1045,6 +1055,36 @@ extern "C" camelot_status camelot_submit_trace(camelot_pipeline* p, uint32_t str
     return check_and_run(p, true);
 }
 
+// The completion of ticket t, once every word of its slot carries the flag
+// t + 1 (each 8-byte word is written atomically by the device: 32 data bits,
+// 32 flag bits).  Returns false while any word is still missing.
+static bool read_completion(const CompSlot& cs, uint64_t t, camelot_completion* c) {
+    const volatile unsigned long long* w = cs.w;
+    const uint32_t flag = (uint32_t)(t + 1);
+    uint32_t d[kCompWords];
+    for (int i = 0; i < CW_USED; ++i) {
+        const unsigned long long x = w[i];
+        if ((uint32_t)(x >> 32) != flag) return false;
+        d[i] = (uint32_t)x;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    auto u64 = [&](int lo) { return (int64_t)((uint64_t)d[lo] | ((uint64_t)d[lo + 1] << 32)); };
+    memset(c, 0, sizeof(*c));
+    c->query_id = t;
+    c->stream_id = d[CW_STREAM];
+    c->status = (int32_t)d[CW_STATUS];
+    c->batch_size = (int32_t)d[CW_BATCH];
+    c->t_arrival_ns = u64(CW_T_ARR);
+    c->t_batch_ns = u64(CW_T_BATCH);
+    c->t_done_ns = u64(CW_T_DONE);
+    for (int r = 0; r < kMaxTopK; ++r) {
+        c->idx[r] = (int32_t)d[CW_IDX + r];
+        uint32_t v = d[CW_VAL + r];
+        memcpy(&c->val[r], &v, 4);
+    }
+    return true;
+}
+
 extern "C" camelot_status camelot_poll(camelot_pipeline* p, camelot_completion* out, uint32_t max,
                                        uint32_t* n_out, int64_t timeout_us) {
     if (!p || !n_out || (max && !out)) return fail(CAMELOT_EINVAL, "null argument");
@@ -1056,10 +1096,7 @@ extern "C" camelot_status camelot_poll(camelot_pipeline* p, camelot_completion* 
     for (;;) {
         uint64_t t = p->next_poll.load(std::memory_order_relaxed);
         while (got < max) {
-            CompSlot& cs = p->comp[t & mask];
-            if (cs.seq != t + 1) break;
-            std::atomic_thread_fence(std::memory_order_acquire);
-            out[got] = cs.c;
+            if (!read_completion(p->comp[t & mask], t, &out[got])) break;
             out[got].t_poll_ns = host_now_ns();
             ++got;
             ++t;

@@ -65,7 +65,9 @@ struct StageParams {
                             // the first tokens for a token-level stage)
     int32_t in_tiled;       // set per pipeline: the input rows arrive in the tiled layout below
     int32_t out_tiled;      // set per pipeline: write the output rows in the tiled layout
-    int32_t pad_[3];
+    int32_t tile_h;         // tensor-core kinds: rows per operand tile (32; 128 for token-level stages)
+    int32_t out_tile_h;     // set per pipeline: tile height of the consumer's tiled layout
+    int32_t pad_;
     size_t in_row_bytes;
     size_t out_row_bytes;   // 0 for final stages
     size_t out_width;       // final stages: width of the last layer (logits per query)
@@ -76,18 +78,21 @@ struct StageParams {
 };
 
 // Tiled row layout read by the tensor-core stages (their MMA operand format):
-// rows of rowb bytes (a multiple of 128) in 32-row x 128-byte tiles; tile
-// (rt, kb) = rows 32 rt.. and bytes 128 kb.. of each row, 4 KB at
-// (rt * rowb / 128 + kb) * 4 KB; row r's 16-byte piece j at r * 128 +
-// (j ^ (r % 8)) * 16 inside it.  Byte `b` of row r:
-__host__ __device__ inline size_t tiled_offset(int r, size_t b, size_t rowb) {
+// rows of rowb bytes (a multiple of 128) in h-row x 128-byte tiles (h = 32 or
+// 128, nothing else); tile (rt, kb) = rows h rt.. and bytes 128 kb.. of each row, h x 128
+// bytes at (rt * rowb / 128 + kb) * h * 128; row r's 16-byte piece j at
+// (r % h) * 128 + (j ^ (r % 8)) * 16 inside it.  Byte `b` of row r:
+__host__ __device__ inline size_t tiled_offset(int r, size_t b, size_t rowb, int h) {
+    const int lg = h == 128 ? 7 : 5;               // h is 32 or 128
     const size_t p = b >> 4, kb = p >> 3, j = p & 7;
-    const int rr = r & 31;
-    return ((((size_t)(r >> 5) * (rowb >> 7)) + kb) << 12) + (size_t)rr * 128 + ((j ^ (size_t)(rr & 7)) << 4) +
+    const int rt = r >> lg, rr = r & (h - 1);
+    return ((((size_t)rt * (rowb >> 7)) + kb) << (lg + 7)) + (size_t)rr * 128 + ((j ^ (size_t)(rr & 7)) << 4) +
            (b & 15);
 }
-// Bytes a tiled batch of `rows` rows occupies (whole row tiles).
-__host__ __device__ inline size_t tiled_bytes(size_t rows, size_t rowb) { return (rows + 31) / 32 * 32 * rowb; }
+// Bytes a tiled batch of `rows` rows occupies (whole row tiles of h rows).
+__host__ __device__ inline size_t tiled_bytes(size_t rows, size_t rowb, int h) {
+    return (rows + h - 1) / h * h * rowb;
+}
 
 // Row addressing: row q is at base + ((first + q) & mask) * stride.  Ring
 // slots wrap with mask = slots - 1; contiguous buffers use mask = ~0.

@@ -115,7 +115,7 @@ static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowR
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (tok >= 0 && tok < V) v = __ldg(reinterpret_cast<const uint4*>(E + (size_t)tok * D) + c);
         if (P.out_tiled)
-            __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)(q * T + t), c * 16, (size_t)D * 2)), v);
+            __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)(q * T + t), c * 16, (size_t)D * 2, P.out_tile_h)), v);
         else
             __stcg(reinterpret_cast<uint4*>(out.row(q) + t * (uint64_t)D * 2) + c, v);
     }
@@ -157,7 +157,7 @@ static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams
                 }
                 const uint4 w4 = make_uint4(o[0], o[1], o[2], o[3]);
                 if (P.out_tiled)
-                    __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)q, c * 16, P.out_row_bytes)), w4);
+                    __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)q, c * 16, P.out_row_bytes, P.out_tile_h)), w4);
                 else
                     __stcg(reinterpret_cast<uint4*>(out.row(q)) + c, w4);
             }
@@ -166,41 +166,82 @@ static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams
 }
 
 // ---------------------------------------------------------------------------
-// NORM_POOL2_BF16: 2x2 mean, normalise, round to bf16.  One warp per (query,
-// output row): the two input rows (2 * W * C contiguous bytes) are staged in
-// the warp's shared memory with 16-byte loads, then each lane produces output
-// values m = lane, lane + 32, ... of the row.  The FP32 value is exact (an
-// integer sum <= 1020, times 1/4, minus 127.5, times 1/64), so the bf16 result
-// is the round-to-nearest-even of the exact value.
+// NORM_POOL2_BF16: 2x2 mean, normalise, round to bf16.  The FP32 value is exact
+// (an integer sum <= 1020, times 1/4, minus 127.5, times 1/64), so the bf16
+// result is the round-to-nearest-even of the exact value.
+// Work is cut into groups of G consecutive output rows of one query (2G input
+// rows, contiguous in the image).  Each warp streams its groups into two
+// shared-memory buffers with cp.async, the next group's copy in flight while
+// the current one is computed, and each lane produces four consecutive
+// outputs (8 bytes) at a time.  Output value m of an output row reads input
+// bytes i0 = 2 m - (m mod C) and i0 + C of the row pair (pixels 2w and 2w + 1,
+// channel c, with m = w C + c).
 // ---------------------------------------------------------------------------
+constexpr int kPoolBufBytes = 12 * 1024;   // per warp and buffer: 2 x 8 warps x 12 KB = 192 KB
+
 static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
-                              RowRef out) {
+                                     RowRef out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int H = P.H, W = P.W, C = P.C, Ho = H / 2, Wo = W / 2;
-    const int pair_bytes = 2 * W * C;
-    const int out_vals = Wo * C;
-    uint8_t* sm = reinterpret_cast<uint8_t*>(cx.smem) + warp * 8192;   // 8 warps x 8 KB
-    const int units = n * Ho;
-    for (int u = cx.rank * kWarps + warp; u < units; u += cx.nctas * kWarps) {
-        const int q = u / Ho, ho = u - q * Ho;
-        const uint4* src = reinterpret_cast<const uint4*>(in.row(q) + (size_t)2 * ho * W * C);
-        uint4* dst = reinterpret_cast<uint4*>(sm);
-        for (int i = lane; i < pair_bytes / 16; i += 32) dst[i] = __ldcs(src + i);   // read once: evict first
+    const int Ho = P.H / 2, WC = P.W * P.C, C = P.C;
+    const int pair_bytes = 2 * WC;                 // a multiple of 16, at most 8192
+    const int out_vals = (P.W / 2) * C;            // a multiple of 4
+    const int P4 = out_vals / 4;                   // 4-value items per output row
+    const int G = min(8, kPoolBufBytes / pair_bytes);
+    const int gpq = (Ho + G - 1) / G;              // groups per query
+    const int groups = n * gpq;
+    const int d128 = 128 % C;                      // channel step between a lane's items (32 x 4 values)
+    uint8_t* buf = reinterpret_cast<uint8_t*>(cx.smem) + warp * 2 * kPoolBufBytes;
+    auto issue = [&](int g, uint8_t* dst) {
+        const int q = g / gpq, ho0 = (g - q * gpq) * G;
+        const int nv = min(G, Ho - ho0) * pair_bytes / 16;
+        const uint4* src = reinterpret_cast<const uint4*>(in.row(q) + (size_t)ho0 * pair_bytes);
+        for (int i = lane; i < nv; i += 32) cp_async16(dst + 16 * i, src + i);
+        cp_async_commit();
+    };
+    const int gstride = cx.nctas * kWarps;
+    int cur = 0;
+    int g = cx.rank * kWarps + warp;
+    if (g < groups) issue(g, buf);
+    for (; g < groups; g += gstride, cur ^= 1) {
+        if (g + gstride < groups) {
+            issue(g + gstride, buf + (cur ^ 1) * kPoolBufBytes);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncwarp();
-        const uint8_t* r0 = sm;
-        const uint8_t* r1 = sm + W * C;
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out.row(q)) + (size_t)ho * out_vals;
-        for (int m = lane; m < out_vals; m += 32) {
-            const int w = m / C, c = m - w * C;
-            const int i0 = 2 * w * C + c;
-            const uint32_t s = (uint32_t)r0[i0] + r0[i0 + C] + r1[i0] + r1[i0 + C];
-            const float y = (static_cast<float>(s) * 0.25f - 127.5f) * 0.015625f;
-            if (P.out_tiled)
-                *reinterpret_cast<__nv_bfloat16*>(out.base + tiled_offset(q, ((size_t)ho * out_vals + m) * 2,
-                                                                          P.out_row_bytes)) =
-                    __float2bfloat16_rn(y);
-            else
-                o[m] = __float2bfloat16_rn(y);
+        const uint8_t* sm = buf + cur * kPoolBufBytes;
+        const int q = g / gpq, ho0 = (g - q * gpq) * G;
+        const int items = min(G, Ho - ho0) * P4;
+        int r = lane / P4, i = lane - r * P4;      // output row in the group, item in the row
+        int c = (4 * i) % C;                       // channel of the item's first value
+        for (int it = lane; it < items; it += 32) {
+            const uint8_t* r0 = sm + r * pair_bytes;
+            const uint8_t* r1 = r0 + WC;
+            const int m0 = 4 * i;
+            float y[4];
+            int cc = c;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int i0 = 2 * (m0 + t) - cc;
+                const uint32_t s = (uint32_t)r0[i0] + r0[i0 + C] + r1[i0] + r1[i0 + C];
+                y[t] = (static_cast<float>(s) * 0.25f - 127.5f) * 0.015625f;
+                cc = cc + 1 == C ? 0 : cc + 1;
+            }
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(y[0], y[1]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(y[2], y[3]);
+            const uint2 v = make_uint2(*reinterpret_cast<const uint32_t*>(&lo),
+                                       *reinterpret_cast<const uint32_t*>(&hi));
+            const size_t b = ((size_t)(ho0 + r) * out_vals + m0) * 2;   // byte in the query's output row
+            char* dst = P.out_tiled ? out.base + tiled_offset(q, b, P.out_row_bytes, P.out_tile_h)
+                                    : out.row(q) + b;
+            __stcg(reinterpret_cast<uint2*>(dst), v);
+            // next item of this lane: 32 items on (rows of out_vals values are
+            // whole multiples of C, so only the in-row step moves the channel)
+            i += 32;
+            while (i >= P4) { i -= P4; ++r; }
+            c += d128;
+            if (c >= C) c -= C;
         }
         __syncwarp();
     }
