@@ -157,6 +157,63 @@ __device__ __forceinline__ void store_out(const LayerOut& o, int q, int m, float
     }
 }
 
+// Epilogue stores of one 32-row block of an accumulator: this lane holds
+// output column m of rows row0 .. row0 + 31 (r0: the first 16, r1: the rest),
+// of which the first jn are real.  The branches on the output kind sit
+// outside the unrolled row loops, so each path is straight-line code.
+__device__ __forceinline__ float epi_val(const uint32_t (&r0)[16], const uint32_t (&r1)[16], int j) {
+    return __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
+}
+
+// Chunk partials (f32, row stride ld floats), reduced afterwards.
+__device__ __forceinline__ void epi_partials(float* dst, size_t ld, const uint32_t (&r0)[16],
+                                             const uint32_t (&r1)[16], int jn) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j < jn) __stcg(dst + (size_t)j * ld, epi_val(r0, r1, j));
+}
+
+// Final values: act(acc * vscale), stored as o describes.
+__device__ __forceinline__ void epi_direct(const LayerOut& o, int row0, int m, const uint32_t (&r0)[16],
+                                           const uint32_t (&r1)[16], int jn) {
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = epi_val(r0, r1, j) * o.vscale;
+    if (o.act == ACT_GELU) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = apply_act(v[j], ACT_GELU);
+    } else if (o.act == ACT_RELU) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = apply_act(v[j], ACT_RELU);
+    }
+    if (o.fmt == OUT_F32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < jn) reinterpret_cast<float*>(o.rows.row(row0 + j))[m] = v[j];
+    } else if (o.fmt == OUT_BF16) {
+        if (o.tiled) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < jn)
+                    *reinterpret_cast<__nv_bfloat16*>(o.rows.base + tiled_offset(row0 + j, (size_t)m * 2, o.rowb, o.th)) =
+                        __float2bfloat16_rn(v[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < jn) reinterpret_cast<__nv_bfloat16*>(o.rows.row(row0 + j))[m] = __float2bfloat16_rn(v[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < jn) {
+                const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v[j] / o.qscale, __NV_SATFINITE, __NV_E4M3);
+                if (o.tiled) *reinterpret_cast<__nv_fp8_storage_t*>(o.rows.base + tiled_offset(row0 + j, (size_t)m, o.rowb, o.th)) = c;
+                else reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(row0 + j))[m] = c;
+            }
+        }
+    }
+}
+
 // What a stage needs to know about its unit, worked out once per unit.
 struct UnitInfo {
     int c, mt, row0;   // K-chunk, weight tile, first input row
@@ -339,16 +396,10 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&g.tfree[acc]);
                     }
-                    if (m < N) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int row = row0 + q0 + j;
-                            if (row < rows) {
-                                const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
-                                if (C == 1) store_out(direct, row, m, v);
-                                else __stcg(Pbuf + ((size_t)c * rows + row) * Npad + m, v);
-                            }
-                        }
+                    const int jn = min(32, rows - (row0 + q0));   // real rows of this block
+                    if (m < N && jn > 0) {
+                        if (C > 1) epi_partials(Pbuf + ((size_t)c * rows + row0 + q0) * Npad + m, Npad, r0, r1, jn);
+                        else epi_direct(direct, row0 + q0, m, r0, r1, jn);
                     }
                 }
             }
@@ -426,33 +477,29 @@ static __device__ void gemm_reduce(const StageCtx& cx, const LayerParams& L, int
 // barrier.
 template <int NT>
 static __device__ void retile_rows(const StageCtx& cx, RowRef x, int rows, size_t rowb, char* xt) {
-    const size_t pieces = rowb / 16;
-    const size_t KB = rowb / 128;
-    const size_t total = (size_t)((rows + NT - 1) / NT) * NT * pieces;
-    const size_t stride = (size_t)cx.nctas * kThreads;
-    constexpr int U = 8;                             // loads in flight per thread
-    for (size_t base = (size_t)cx.rank * kThreads + threadIdx.x; base < total; base += U * stride) {
-        uint4 v[U];
+    // one warp per (row, run of 256 16-byte pieces): 8 coalesced loads in
+    // flight per lane, then stores of whole 128-byte tile rows
+    const int pieces = (int)(rowb / 16);
+    const int KB = (int)(rowb / 128);
+    const int runs = (pieces + 255) / 256;
+    const int total = (rows + NT - 1) / NT * NT * runs;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int w = cx.rank * kWarps + warp; w < total; w += cx.nctas * kWarps) {
+        const int r = w / runs, p0 = (w - r * runs) * 256;
+        uint4 v[8];
+        const uint4* src = r < rows ? reinterpret_cast<const uint4*>(x.row(r)) : nullptr;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const size_t e = base + u * stride;
-            v[u] = make_uint4(0u, 0u, 0u, 0u);
-            if (e < total) {
-                const int r = (int)(e / pieces);
-                if (r < rows) v[u] = __ldcg(reinterpret_cast<const uint4*>(x.row(r)) + (e - (size_t)r * pieces));
-            }
+        for (int i = 0; i < 8; ++i) {
+            const int p = p0 + 32 * i + lane;
+            v[i] = (src != nullptr && p < pieces) ? __ldcs(src + p) : make_uint4(0u, 0u, 0u, 0u);
         }
+        const int rt = r / NT, rr = r % NT;
+        char* trow = xt + (size_t)rt * KB * (NT * 128) + rr * 128;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const size_t e = base + u * stride;
-            if (e < total) {
-                const int r = (int)(e / pieces);
-                const size_t p = e - (size_t)r * pieces;
-                const int rt = r / NT, rr = r % NT;
-                const size_t kb = p / 8, j = p % 8;
-                char* dst = xt + ((size_t)rt * KB + kb) * (NT * 128) + rr * 128 + ((j ^ (size_t)(rr & 7)) << 4);
-                *reinterpret_cast<uint4*>(dst) = v[u];
-            }
+        for (int i = 0; i < 8; ++i) {
+            const int p = p0 + 32 * i + lane;
+            if (p < pieces)
+                *reinterpret_cast<uint4*>(trow + (size_t)(p >> 3) * (NT * 128) + (((p & 7) ^ (rr & 7)) << 4)) = v[i];
         }
     }
     fence_proxy_async_global();
