@@ -58,7 +58,9 @@ struct GemmSmem {
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
     uint32_t* ring_it;     // stages filled so far (all launches of this CTA)
     uint32_t* acc_it;      // [kIssuers] units finished so far by each issuer
+    char* stage_out;       // [4 epilogue warps][kEpiStageBytes] staging of tiled output blocks
 };
+constexpr uint32_t kEpiStageBytes = 32 * 32 * 2;   // one 32-row x 32-column block of bf16
 
 __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     char* base = reinterpret_cast<char*>(
@@ -73,6 +75,7 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
     g.ring_it = g.tmem_slot + 1;
     g.acc_it = g.ring_it + 1;
+    g.stage_out = base + kRingBytes + 1024;
     return g;
 }
 
@@ -173,9 +176,13 @@ __device__ __forceinline__ void epi_partials(float* dst, size_t ld, const uint32
         if (j < jn) __stcg(dst + (size_t)j * ld, epi_val(r0, r1, j));
 }
 
-// Final values: act(acc * vscale), stored as o describes.
-__device__ __forceinline__ void epi_direct(const LayerOut& o, int row0, int m, const uint32_t (&r0)[16],
-                                           const uint32_t (&r1)[16], int jn) {
+// Final values: act(acc * vscale), stored as o describes; called by all 32
+// lanes of an epilogue warp (lane l holds column m = m0 + l; columns >= N
+// are not stored).  Tiled bf16 outputs (the next layer's operand) pass
+// through the warp's staging block in shared memory, so that the global
+// stores are whole 16-byte pieces of rows (N is a multiple of 8).
+__device__ __forceinline__ void epi_direct(const LayerOut& o, int row0, int m, int N, const uint32_t (&r0)[16],
+                                           const uint32_t (&r1)[16], int jn, char* stg) {
     float v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = epi_val(r0, r1, j) * o.vscale;
@@ -189,23 +196,33 @@ __device__ __forceinline__ void epi_direct(const LayerOut& o, int row0, int m, c
     if (o.fmt == OUT_F32) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (j < jn) reinterpret_cast<float*>(o.rows.row(row0 + j))[m] = v[j];
+            if (j < jn && m < N) reinterpret_cast<float*>(o.rows.row(row0 + j))[m] = v[j];
     } else if (o.fmt == OUT_BF16) {
         if (o.tiled) {
+            const int lane = threadIdx.x & 31, m0 = m - lane;
+            __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(stg);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < jn)
-                    *reinterpret_cast<__nv_bfloat16*>(o.rows.base + tiled_offset(row0 + j, (size_t)m * 2, o.rowb, o.th)) =
-                        __float2bfloat16_rn(v[j]);
+            for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = __float2bfloat16_rn(v[j]);
+            __syncwarp();
+            // 32 rows x 4 pieces of 16 bytes; lane l takes pieces l, l + 32, ...
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int pc = 32 * i + lane, j = pc >> 2, c = pc & 3;
+                if (j < jn && m0 + 8 * c < N)
+                    __stcg(reinterpret_cast<uint4*>(o.rows.base + tiled_offset(row0 + j, (size_t)(m0 + 8 * c) * 2,
+                                                                               o.rowb, o.th)),
+                           *reinterpret_cast<const uint4*>(stg + j * 64 + c * 16));
+            }
+            __syncwarp();
         } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (j < jn) reinterpret_cast<__nv_bfloat16*>(o.rows.row(row0 + j))[m] = __float2bfloat16_rn(v[j]);
+                if (j < jn && m < N) reinterpret_cast<__nv_bfloat16*>(o.rows.row(row0 + j))[m] = __float2bfloat16_rn(v[j]);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            if (j < jn) {
+            if (j < jn && m < N) {
                 const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v[j] / o.qscale, __NV_SATFINITE, __NV_E4M3);
                 if (o.tiled) *reinterpret_cast<__nv_fp8_storage_t*>(o.rows.base + tiled_offset(row0 + j, (size_t)m, o.rowb, o.th)) = c;
                 else reinterpret_cast<__nv_fp8_storage_t*>(o.rows.row(row0 + j))[m] = c;
@@ -397,9 +414,12 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                         if (lane == 0) mbar_arrive(&g.tfree[acc]);
                     }
                     const int jn = min(32, rows - (row0 + q0));   // real rows of this block
-                    if (m < N && jn > 0) {
-                        if (C > 1) epi_partials(Pbuf + ((size_t)c * rows + row0 + q0) * Npad + m, Npad, r0, r1, jn);
-                        else epi_direct(direct, row0 + q0, m, r0, r1, jn);
+                    if (jn > 0) {   // (warp-uniform)
+                        if (C > 1) {
+                            if (m < N) epi_partials(Pbuf + ((size_t)c * rows + row0 + q0) * Npad + m, Npad, r0, r1, jn);
+                        } else {
+                            epi_direct(direct, row0 + q0, m, N, r0, r1, jn, g.stage_out + sub * kEpiStageBytes);
+                        }
                     }
                 }
             }

@@ -96,31 +96,61 @@ static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, 
     }
 }
 
-// FP8 arm of the normalisation stage: the code of 128 y, y = (x - 127.5) / 64,
-// i.e. e4m3(2 x - 255) (exact in f32, then rounded to nearest even e4m3).  The
-// next stage reads the codes with scale 1/128.  16 input bytes -> 16 codes.
 // Embedding gather of the text-tagging microservice: out row t of query q =
-// E[tok] (bf16, D columns) for 0 <= tok < V, zero otherwise; 16-byte pieces.
+// E[tok] (bf16, D columns) for 0 <= tok < V, zero otherwise.  One warp takes
+// 8 consecutive token rows at a time: lanes 0-7 read the 8 token IDs, then
+// every lane loads its 16-byte pieces of all 8 table rows (up to 32 loads in
+// flight) before storing them.
 static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out) {
     const int V = P.H, D = P.W, T = P.rows;
-    const __nv_bfloat16* E = reinterpret_cast<const __nv_bfloat16*>(P.layer[0].w);
-    const uint64_t pieces = (uint64_t)D * 2 / 16;
-    const uint64_t per_q = (uint64_t)T * pieces;
-    const uint64_t total = (uint64_t)n * per_q;
-    const uint64_t stride = (uint64_t)cx.nctas * kThreads;
-    for (uint64_t e = (uint64_t)cx.rank * kThreads + threadIdx.x; e < total; e += stride) {
-        const uint64_t q = e / per_q, rem = e - q * per_q;
-        const uint64_t t = rem / pieces, c = rem - t * pieces;
-        const int32_t tok = reinterpret_cast<const int32_t*>(in.row(q))[t];
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (tok >= 0 && tok < V) v = __ldg(reinterpret_cast<const uint4*>(E + (size_t)tok * D) + c);
-        if (P.out_tiled)
-            __stcg(reinterpret_cast<uint4*>(out.base + tiled_offset((int)(q * T + t), c * 16, (size_t)D * 2, P.out_tile_h)), v);
-        else
-            __stcg(reinterpret_cast<uint4*>(out.row(q) + t * (uint64_t)D * 2) + c, v);
+    const uint4* E = reinterpret_cast<const uint4*>(P.layer[0].w);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pieces = D / 8;                       // 16-byte pieces per row
+    const int rows = n * T;
+    const int groups = (rows + 7) / 8;
+    const size_t rowb = (size_t)D * 2;
+    for (int g = cx.rank * kWarps + warp; g < groups; g += cx.nctas * kWarps) {
+        const int r0 = g * 8;
+        int q = 0, t = 0, tk = -1;
+        if (lane < 8 && r0 + lane < rows) {
+            q = (r0 + lane) / T;
+            t = r0 + lane - q * T;
+            tk = reinterpret_cast<const int32_t*>(in.row(q))[t];
+        }
+        for (int pb = 0; pb < pieces; pb += 128) {
+            uint4 v[8][4];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int tok = __shfl_sync(0xffffffffu, tk, k);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = pb + 32 * i + lane;
+                    v[k][i] = make_uint4(0u, 0u, 0u, 0u);
+                    if (p < pieces && tok >= 0 && tok < V) v[k][i] = __ldg(E + (size_t)tok * pieces + p);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                const int qk = __shfl_sync(0xffffffffu, q, k), tt = __shfl_sync(0xffffffffu, t, k);
+                if (r >= rows) break;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = pb + 32 * i + lane;
+                    if (p < pieces) {
+                        char* dst = P.out_tiled ? out.base + tiled_offset(r, (size_t)p * 16, rowb, P.out_tile_h)
+                                                : out.row(qk) + (size_t)tt * rowb + (size_t)p * 16;
+                        __stcg(reinterpret_cast<uint4*>(dst), v[k][i]);
+                    }
+                }
+            }
+        }
     }
 }
 
+// FP8 arm of the normalisation stage: the code of 128 y, y = (x - 127.5) / 64,
+// i.e. e4m3(2 x - 255) (exact in f32, then rounded to nearest even e4m3).  The
+// next stage reads the codes with scale 1/128.  16 input bytes -> 16 codes.
 static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                            RowRef out) {
     const uint64_t chunks = P.in_row_bytes / 16;
