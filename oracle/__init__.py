@@ -57,6 +57,8 @@ def _declare(L):
         "orc_normalize_u8": (None, [P, I64, P]),
         "orc_norm_pool2": (None, [P, I64, C.c_int, C.c_int, C.c_int, P]),
         "orc_gelu": (C.c_double, [C.c_double]),
+        "orc_compute_synth": (None, [P, I64, C.c_int, P]),
+        "orc_stream_synth": (None, [P, I64, C.c_int, P, I64, C.c_int, P]),
         "orc_linear": (None, [P, I64, C.c_int, P, C.c_int, C.c_int, P, P]),
         "orc_argmax": (None, [P, I64, C.c_int, P]),
         "orc_topk": (None, [P, I64, C.c_int, C.c_int, P, P]),
@@ -236,6 +238,34 @@ def pipeline_fp8(x_u8: np.ndarray, ws, act_scales):
             return y, argmax(y), hidden, sws
         hidden.append(yq)
         xq = yq
+
+
+def compute_synth(x, steps: int) -> np.ndarray:
+    """Artifact compute stage c_i (binary32, as the stage is defined)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib().orc_compute_synth(_p(x), x.size, int(steps), _p(y))
+    return y
+
+
+def stream_synth(x, table, R: int) -> np.ndarray:
+    """Artifact memory / host-link stage m_i / p_i over `table` (binary32)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    T = np.ascontiguousarray(table, dtype=np.float32).reshape(-1)
+    nq, W = x.shape
+    y = np.empty_like(x)
+    lib().orc_stream_synth(_p(x), nq, W, _p(T), T.size, int(R), _p(y))
+    return y
+
+
+def pipeline_artifact(x, stages, top_k: int):
+    """A chain of artifact stages, each ("c", steps) or ("m", table, R), then
+    the top-k of the last stage's rows: returns (rows, idx, val)."""
+    z = np.ascontiguousarray(x, dtype=np.float32)
+    for st in stages:
+        z = compute_synth(z, st[1]) if st[0] == "c" else stream_synth(z, st[1], st[2])
+    idx, val = topk(z.astype(np.float64), top_k)
+    return z, idx, val
 
 
 def embed_gather(tokens, E) -> np.ndarray:

@@ -11,7 +11,8 @@
 //   1. stage math of the synthetic microservices (stand-ins for the Sec. 3
 //      suite): u8 normalisation, 2x2 pooling, dense layers with ReLU / erf-GELU,
 //      argmax / top-k, the number formats the reduced-precision arms use, and
-//      the FP8 arm's per-tensor quantisation and scaled dense layers;
+//      the FP8 arm's per-tensor quantisation and scaled dense layers, and the
+//      artifact compute / memory / host-link stages (binary32 by definition);
 //   2. whole-pipeline references (the plain 2-stage and the 3-stage BF16 pipelines);
 //   3. an event-driven simulator of the wait queue, batch trigger and
 //      multi-instance stage pipeline (Sec. 5.2 steps 1-2, Sec. 4.1);
@@ -250,6 +251,41 @@ void orc_embed_gather(const int32_t* tok, int64_t n_rows, const double* E, int V
     for (int64_t r = 0; r < n_rows; ++r) {
         const int32_t t = tok[r];
         for (int d = 0; d < D; ++d) out[r * D + d] = (t >= 0 && t < V) ? E[(int64_t)t * D + d] : 0.0;
+    }
+}
+
+// Artifact compute-intensive stage (the c_i of Sec. 2.3 and Sec. 8.5, whose
+// arithmetic intensity is a parameter): every value x runs `steps` iterations
+// of y <- fma(y, 127/128, x / 128) from y = 0.  The stage is defined in
+// binary32 with one rounding per fused step, so this reference computes in
+// binary32 too (std::fma on floats rounds once); the exact real result is
+// x (1 - (127/128)^steps).
+void orc_compute_synth(const float* x, int64_t n, int steps, float* y) {
+    for (int64_t i = 0; i < n; ++i) {
+        const float b = x[i] * 0.0078125f;
+        float a = 0.0f;
+        for (int k = 0; k < steps; ++k) a = std::fma(a, 0.9921875f, b);
+        y[i] = a;
+    }
+}
+
+// Artifact memory- / host-link-intensive stage (the m_i and p_i of Sec. 8.5):
+// row q of width W gets y_j = x_j + T[b + j] + T[b + W + j] + ... (R / W table
+// windows, added left to right in binary32), b = W * (h mod (L / W - R / W + 1)),
+// h = the high 32 bits of the 64-bit product bits(x_0) * 0x9E3779B97F4A7C15.
+void orc_stream_synth(const float* x, int64_t nq, int W, const float* T, int64_t L, int R, float* y) {
+    const uint64_t starts = (uint64_t)(L / W - R / W + 1);
+    for (int64_t q = 0; q < nq; ++q) {
+        const float* xr = x + q * W;
+        uint32_t bits;
+        std::memcpy(&bits, xr, 4);
+        const uint32_t h = (uint32_t)(((uint64_t)bits * 0x9E3779B97F4A7C15ull) >> 32);
+        const int64_t b = (int64_t)(h % (uint32_t)starts) * W;
+        for (int j = 0; j < W; ++j) {
+            float a = xr[j];
+            for (int r = 0; r < R / W; ++r) a = a + T[b + (int64_t)r * W + j];
+            y[q * W + j] = a;
+        }
     }
 }
 
