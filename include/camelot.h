@@ -89,6 +89,22 @@ int camelot_version(void);
  *   EMBED_GATHER   : int32 token IDs [T] -> bf16 rows [T][D], row t = E[tok[t]] for
  *                    0 <= tok < V and zero for any other ID (padding).  dims =
  *                    {V, D, T}, D a multiple of 8; weights[0] = E, bf16 [V][D].
+ *   COMPUTE_SYNTH  : artifact compute-intensive stage (the c_i of Sec. 2.3 and
+ *                    Sec. 8.5): f32 rows of W -> f32 rows of W, y_j = the n-th
+ *                    iterate of y <- fma(y, 127/128, x_j / 128) from y = 0 (n FMA
+ *                    steps per value, each rounded once in f32; the exact value
+ *                    is x_j (1 - (127/128)^n)).  dims = {W, n}, W a multiple of 4.
+ *   STREAM_SYNTH   : artifact memory- or host-link-intensive stage (m_i, p_i):
+ *                    f32 rows of W -> f32 rows of W, y_j = x_j + T[b + j] +
+ *                    T[b + W + j] + ... (R / W terms, added left to right in f32)
+ *                    over the table T of L f32 values in weights[0]: device
+ *                    memory for m_i, pinned host memory mapped into the device
+ *                    (cudaHostAllocMapped) for p_i.  The window start b = W (h mod
+ *                    (L / W - R / W + 1)), h = the high 32 bits of the 64-bit
+ *                    product bits(x_0) * 0x9E3779B97F4A7C15.  dims = {W, R, L}, W
+ *                    a multiple of 4, R and L multiples of W, R <= L.  The table
+ *                    is NOT copied: it must stay valid while the stage exists.
+ * COMPUTE_SYNTH and STREAM_SYNTH may be final (top_k > 0: top-k of the row).
  * Token-level tensor-core stages: a GEMM_BF16 / GEMM_FP8 stage with
  * rows_per_query T > 1 treats each query as T rows (its input row is T x
  * dims[0] elements) and runs the dense chain on every row; a final such stage
@@ -102,7 +118,9 @@ typedef enum {
     CAMELOT_STAGE_GEMM_BF16 = 4,
     CAMELOT_STAGE_GEMM_FP8 = 5,
     CAMELOT_STAGE_NORMALIZE_U8_E4M3 = 6,
-    CAMELOT_STAGE_EMBED_GATHER = 7
+    CAMELOT_STAGE_EMBED_GATHER = 7,
+    CAMELOT_STAGE_COMPUTE_SYNTH = 8,
+    CAMELOT_STAGE_STREAM_SYNTH = 9
 } camelot_stage_kind;
 
 typedef enum { CAMELOT_ACT_NONE = 0, CAMELOT_ACT_RELU = 1, CAMELOT_ACT_GELU = 2 } camelot_act;

@@ -20,6 +20,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EAGAIN", "ETIMEDOUT", "ECUDA", "ESTAT
 
 STAGE_NORMALIZE_U8, STAGE_NORM_POOL2_BF16, STAGE_MLP_FP32, STAGE_GEMM_BF16 = 1, 2, 3, 4
 STAGE_GEMM_FP8, STAGE_NORMALIZE_U8_E4M3, STAGE_EMBED_GATHER = 5, 6, 7
+STAGE_COMPUTE_SYNTH, STAGE_STREAM_SYNTH = 8, 9
 ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
 HANDOFF_GLOBAL, HANDOFF_HOST_STAGED = 0, 1
 POLICY_MAX_PEAK, POLICY_MIN_SM = 0, 1

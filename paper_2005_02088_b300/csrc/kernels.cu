@@ -399,8 +399,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Host-callable launch helpers (used by the runtime in runtime.cpp).
 namespace camelot {
 
-// The instantiations: the four pipeline shapes of the workloads, every kind on
-// its own (direct launches), and all kinds together (any other pipeline).
+// The instantiations: the pipeline shapes of the workloads (the artifact
+// kinds together), every other kind on its own (direct launches), and all
+// kinds together (any other pipeline).
 constexpr uint32_t kKindSets[] = {
     kind_bit(KIND_NORMALIZE_U8), kind_bit(KIND_NORM_POOL2_BF16), kind_bit(KIND_MLP_FP32),
     kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8), kind_bit(KIND_NORMALIZE_U8_E4M3),
@@ -409,6 +410,7 @@ constexpr uint32_t kKindSets[] = {
     kind_bit(KIND_NORM_POOL2_BF16) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
     kind_bit(KIND_NORMALIZE_U8_E4M3) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
     kind_bit(KIND_EMBED_GATHER) | kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8),
+    kind_bit(KIND_COMPUTE_SYNTH) | kind_bit(KIND_STREAM_SYNTH),
     kAllKinds};
 constexpr int kNumSets = sizeof(kKindSets) / sizeof(kKindSets[0]);
 
@@ -421,8 +423,8 @@ template <int... I>
 const void* const SetTable<I...>::pipe[sizeof...(I)] = {(const void*)pipeline_kernel<kKindSets[I]>...};
 template <int... I>
 const void* const SetTable<I...>::direct[sizeof...(I)] = {(const void*)stage_direct_kernel<kKindSets[I]>...};
-using Table = SetTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10>;
-static_assert(kNumSets == 11, "instantiation table");
+using Table = SetTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11>;
+static_assert(kNumSets == 12, "instantiation table");
 
 // The first (narrowest) instantiation holding every kind in `kinds`.
 static int pick(uint32_t kinds) {

@@ -332,6 +332,48 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
             sp.scratch_bytes = layout_scratch(sp, d->max_batch);
             break;
         }
+        case CAMELOT_STAGE_COMPUTE_SYNTH:
+        case CAMELOT_STAGE_STREAM_SYNTH: {
+            const bool stream = d->kind == CAMELOT_STAGE_STREAM_SYNTH;
+            const int W = d->dims[0];
+            if (W <= 0 || W % 4) return bail(fail(CAMELOT_EINVAL, "dims[0] (row width W) must be a positive multiple of 4"));
+            if (d->top_k > W) return bail(fail(CAMELOT_EINVAL, "top_k exceeds the row width"));
+            sp.W = W;
+            sp.in_row_bytes = (size_t)W * 4;
+            sp.out_row_bytes = d->top_k ? 0 : (size_t)W * 4;
+            sp.out_width = W;
+            if (!stream) {
+                if (d->dims[1] < 0) return bail(fail(CAMELOT_EINVAL, "dims[1] (FMA steps) must be >= 0"));
+                sp.H = d->dims[1];
+            } else {
+                const int R = d->dims[1], L = d->dims[2];
+                if (R <= 0 || L <= 0 || R % W || L % W || R > L)
+                    return bail(fail(CAMELOT_EINVAL, "STREAM_SYNTH dims {W, R, L}: R, L positive multiples of W, R <= L"));
+                if (!d->weights[0] || (reinterpret_cast<uintptr_t>(d->weights[0]) & 15))
+                    return bail(fail(CAMELOT_EINVAL, "weights[0] (the table) must be a 16-byte aligned pointer"));
+                cudaPointerAttributes a{};
+                if (cudaPointerGetAttributes(&a, d->weights[0]) != cudaSuccess) {
+                    cudaGetLastError();
+                    return bail(fail(CAMELOT_EINVAL, "weights[0] is not device or mapped pinned host memory"));
+                }
+                const void* dp = nullptr;
+                if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) dp = d->weights[0];
+                else if (a.type == cudaMemoryTypeHost && a.devicePointer) dp = a.devicePointer;
+                if (!dp) return bail(fail(CAMELOT_EINVAL, "weights[0] is not device or mapped pinned host memory"));
+                sp.H = R / W;
+                sp.C = L / W - R / W + 1;
+                sp.layer[0].w = (const float*)dp;
+            }
+            // scratch: a final stage's output rows, then the result arrays
+            size_t off = 0;
+            sp.layer[0].h_off = 0;
+            if (d->top_k) off = align_up((size_t)d->max_batch * W * 4, 256);
+            sp.res_off = off;
+            off = align_up(off + (size_t)d->max_batch * kMaxTopK * 8, 256);
+            sp.tile_off = off;
+            sp.scratch_bytes = off;
+            break;
+        }
         case CAMELOT_STAGE_EMBED_GATHER: {
             const int V = d->dims[0], D = d->dims[1], T = d->dims[2];
             if (V <= 0 || D <= 0 || T <= 0 || D % 8)
@@ -374,7 +416,7 @@ static const size_t kDirectHeader = align_up(sizeof(Ctl), 256) + align_up(sizeof
 // Internal helpers shared with noalloc.cu (not part of the C ABI).
 const StageParams* camelot_internal_stage_params(const camelot_stage* st) { return &st->sp; }
 size_t camelot_internal_layout_scratch(StageParams& sp, int B) {
-    return (sp.kind == KIND_MLP_FP32 || is_tensor_kind(sp.kind)) ? layout_scratch(sp, B) : 0;
+    return (sp.kind == KIND_MLP_FP32 || is_tensor_kind(sp.kind)) ? layout_scratch(sp, B) : sp.scratch_bytes;
 }
 int camelot_internal_sm_count() { return sm_count(); }
 camelot_status camelot_internal_fail(camelot_status st, const char* msg) { return fail(st, "%s", msg); }
@@ -803,9 +845,12 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         return fail(CAMELOT_EINVAL, "allocation needs %d SMs, the device offers %d", total, sms * per_sm);
     if (is_tensor_kind(stages[0]->sp.kind) && stages[0]->sp.rows > 1)
         return fail(CAMELOT_EINVAL, "a token-level tensor-core stage cannot be the first stage");
-    if (o.logits_sink && stages[n_stages - 1]->sp.kind != KIND_MLP_FP32 &&
-        !is_tensor_kind(stages[n_stages - 1]->sp.kind))
-        return fail(CAMELOT_EINVAL, "logits_sink needs a dense final stage");
+    {
+        const int fk = stages[n_stages - 1]->sp.kind;
+        if (o.logits_sink && fk != KIND_MLP_FP32 && !is_tensor_kind(fk) && fk != KIND_COMPUTE_SYNTH &&
+            fk != KIND_STREAM_SYNTH)
+            return fail(CAMELOT_EINVAL, "logits_sink needs a dense or artifact final stage");
+    }
 
     auto* p = new camelot_pipeline();
     auto bail = [&](camelot_status s) { pipeline_free(p); return s; };
@@ -844,7 +889,7 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         hp.st[s] = stages[s]->sp;
         StageParams tmp = stages[s]->sp;
         const bool dense = tmp.kind == KIND_MLP_FP32 || is_tensor_kind(tmp.kind);
-        const size_t per = dense ? align_up(layout_scratch(tmp, B), 256) : 0;
+        const size_t per = dense ? align_up(layout_scratch(tmp, B), 256) : align_up(tmp.scratch_bytes, 256);
         hp.st[s] = tmp;   // scratch offsets laid out for batch B
         hp.inst_scratch[s] = per;
         hp.scratch_off[s] = scr;

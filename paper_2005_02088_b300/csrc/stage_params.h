@@ -20,7 +20,7 @@ constexpr size_t kSmemBytes = 216 * 1024;  // dynamic shared memory per CTA: > h
 
 enum StageKind : int32_t { KIND_NORMALIZE_U8 = 1, KIND_NORM_POOL2_BF16 = 2, KIND_MLP_FP32 = 3,
                            KIND_GEMM_BF16 = 4, KIND_GEMM_FP8 = 5, KIND_NORMALIZE_U8_E4M3 = 6,
-                           KIND_EMBED_GATHER = 7 };
+                           KIND_EMBED_GATHER = 7, KIND_COMPUTE_SYNTH = 8, KIND_STREAM_SYNTH = 9 };
 __host__ __device__ inline bool is_tensor_kind(int32_t k) { return k == KIND_GEMM_BF16 || k == KIND_GEMM_FP8; }
 enum Act : int32_t { ACT_NONE = 0, ACT_RELU = 1, ACT_GELU = 2 };
 
@@ -59,7 +59,10 @@ struct StageParams {
     int32_t n_layers;
     int32_t top_k;          // 0 = intermediate stage
     int32_t max_batch;
-    int32_t H, W, C;        // image kinds; EMBED_GATHER: H = vocabulary, W = row width D
+    int32_t H, W, C;        // image kinds; EMBED_GATHER: H = vocabulary, W = row width D;
+                            // COMPUTE_SYNTH: W = row width, H = FMA steps; STREAM_SYNTH: W = row
+                            // width, H = table windows per query (R / W), C = window starts
+                            // (L / W - R / W + 1), layer[0].w = the table
     int32_t rows;           // rows per query: tokens (EMBED_GATHER, token-level tensor-core stages), else 1
     int32_t res_k;          // results per query in the final-stage result arrays (top_k, or tags of
                             // the first tokens for a token-level stage)

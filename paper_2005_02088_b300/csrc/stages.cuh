@@ -547,6 +547,81 @@ static __device__ void token_argmax(const StageCtx& cx, RowRef z, int n, int T, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Artifact stages (the c_i, m_i and p_i of Sec. 2.3 and Sec. 8.5): tunable
+// compute, memory or host-link intensity.  An intermediate stage writes its
+// f32 rows to `out`; a final one writes them to the instance's scratch and
+// takes their top-k.
+// ---------------------------------------------------------------------------
+// COMPUTE_SYNTH: y <- fma(y, 127/128, x / 128), P.H steps from y = 0, per
+// value; every thread runs four independent chains (one float4).
+static __device__ bool compute_synth_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                                          RowRef out, const FinalOut& fo) {
+    const int W4 = P.W / 4, steps = P.H;
+    const bool fin = P.top_k > 0;
+    const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)P.W * 4} : out;
+    const int total = n * W4;
+    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
+        const int q = e / W4, c = e - q * W4;
+        const float4 x = __ldcs(reinterpret_cast<const float4*>(in.row(q)) + c);
+        const float b0 = x.x * 0.0078125f, b1 = x.y * 0.0078125f, b2 = x.z * 0.0078125f, b3 = x.w * 0.0078125f;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 8
+        for (int i = 0; i < steps; ++i) {
+            a0 = __fmaf_rn(a0, 0.9921875f, b0);
+            a1 = __fmaf_rn(a1, 0.9921875f, b1);
+            a2 = __fmaf_rn(a2, 0.9921875f, b2);
+            a3 = __fmaf_rn(a3, 0.9921875f, b3);
+        }
+        __stcg(reinterpret_cast<float4*>(y.row(q)) + c, make_float4(a0, a1, a2, a3));
+    }
+    if (!fin) return true;
+    if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+    topk_rows(cx, y, n, P.W, P.top_k, fo);
+    return true;
+}
+
+// STREAM_SYNTH: y_j = x_j + sum over the query's P.H table windows, added in
+// window order; 16 table loads in flight per thread.
+static __device__ bool stream_synth_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
+                                         RowRef out, const FinalOut& fo) {
+    const int W4 = P.W / 4, terms = P.H;
+    const uint32_t starts = (uint32_t)P.C;
+    const float4* T = reinterpret_cast<const float4*>(P.layer[0].w);
+    const bool fin = P.top_k > 0;
+    const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)P.W * 4} : out;
+    const int total = n * W4;
+    constexpr int U = 16;
+    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
+        const int q = e / W4, c = e - q * W4;
+        const float* xr = reinterpret_cast<const float*>(in.row(q));
+        const uint32_t bits = __float_as_uint(xr[0]);
+        const uint32_t h = (uint32_t)(((unsigned long long)bits * 0x9E3779B97F4A7C15ull) >> 32);
+        const float4* tw = T + (size_t)(h % starts) * W4 + c;
+        float4 acc = __ldcs(reinterpret_cast<const float4*>(xr) + c);
+        for (int r0 = 0; r0 < terms; r0 += U) {
+            float4 t[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (r0 + u < terms) t[u] = __ldcs(tw + (size_t)(r0 + u) * W4);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (r0 + u < terms) {
+                    acc.x += t[u].x;
+                    acc.y += t[u].y;
+                    acc.z += t[u].z;
+                    acc.w += t[u].w;
+                }
+            }
+        }
+        __stcg(reinterpret_cast<float4*>(y.row(q)) + c, acc);
+    }
+    if (!fin) return true;
+    if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+    topk_rows(cx, y, n, P.W, P.top_k, fo);
+    return true;
+}
+
 // The whole FP32 MLP stage.  Returns false if a group barrier failed.
 static __device__ bool mlp_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out,
                          const FinalOut& fo) {

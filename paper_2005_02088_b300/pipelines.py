@@ -21,6 +21,31 @@ def stage_normalize(H: int, W: int, Cc: int, max_batch: int) -> int:
     return cm.camelot_stage_prepare(d)
 
 
+def stage_compute_synth(W: int, steps: int, top_k: int, max_batch: int) -> int:
+    """Artifact compute-intensive stage (c_i): `steps` FMA steps per value."""
+    d = cm.StageDesc()
+    d.kind = cm.STAGE_COMPUTE_SYNTH
+    d.dims[0], d.dims[1] = W, steps
+    d.top_k = top_k
+    d.max_batch = max_batch
+    return cm.camelot_stage_prepare(d)
+
+
+def stage_stream_synth(W: int, R: int, table, top_k: int, max_batch: int) -> int:
+    """Artifact memory- or host-link-intensive stage (m_i / p_i): R table
+    floats per query from `table` (a device tensor, or pinned host memory
+    mapped into the device: pass its data pointer)."""
+    d = cm.StageDesc()
+    d.kind = cm.STAGE_STREAM_SYNTH
+    L = table.numel() if hasattr(table, "numel") else int(table[1])
+    ptr = table.data_ptr() if hasattr(table, "data_ptr") else int(table[0])
+    d.dims[0], d.dims[1], d.dims[2] = W, R, L
+    d.weights[0] = ptr
+    d.top_k = top_k
+    d.max_batch = max_batch
+    return cm.camelot_stage_prepare(d)
+
+
 def stage_norm_pool2(H: int, W: int, Cc: int, max_batch: int) -> int:
     d = cm.StageDesc()
     d.kind = cm.STAGE_NORM_POOL2_BF16
