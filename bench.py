@@ -881,8 +881,8 @@ def run_serving(args):
     stage), Eq. 1 again inside each share.  Measured: the largest total rate at
     which all four hold p99 <= QoS replaying concurrent device-resident traces
     (bisection), each pipeline's p50/p99 there, the same rate with each pipeline
-    alone, and the host-submitted mix through camelot_server (device-memory
-    admission) at a fraction of that rate."""
+    alone, and the largest host-submitted mix rate through camelot_server
+    (device-memory admission) with p99 <= QoS."""
     import torch
     import synth
     names = ["fp32-2stage", "text-2stage", "bf16-3stage", "fp8-2stage"]
@@ -972,47 +972,62 @@ def run_serving(args):
         out["mix"] = res_mix
         out["alone_at_same_rate"] = alone
 
-        # host-submitted mix through camelot_server at 30 % of that rate
-        lam_h = 0.3 * lam_best
-        pipes = [wl.pipeline(0, a[0], a[1], data_slots=1024, device_data=1) for wl, a in zip(wls, allocs)]
-        opts = cm.camelot_server_options_default()
-        opts.device_bytes_budget = 256 << 20
-        srv = cm.camelot_server_create(pipes, opts)
-        try:
-            nq = 4000
-            arr = [synth.poisson_arrivals_ns(50 + i, nq, lam_h / 4) for i in range(4)]
-            t0 = time.monotonic_ns() + 2_000_000
-            arr = [(a + t0).astype(np.int64) for a in arr]
-            sent, done, got = [0] * 4, [[] for _ in range(4)], [0] * 4
-            buf = (cm.Completion * 4096)()
-            deadline = time.time() + 120
-            while any(g < nq for g in got):
-                now = time.monotonic_ns()
+        # host-submitted mix through camelot_server: the largest total rate
+        # (geometric bisection below 30 % of the device-resident peak) at which
+        # every pipeline holds p99 <= QoS, latency from arrival to the poll
+        def host_mix(lam_h, seed):
+            pipes = [wl.pipeline(0, a[0], a[1], data_slots=1024, device_data=1) for wl, a in zip(wls, allocs)]
+            opts = cm.camelot_server_options_default()
+            opts.device_bytes_budget = 256 << 20
+            srv = cm.camelot_server_create(pipes, opts)
+            try:
+                nq = 4000
+                arr = [synth.poisson_arrivals_ns(seed + i, nq, lam_h / 4) for i in range(4)]
+                t0 = time.monotonic_ns() + 2_000_000
+                arr = [(a + t0).astype(np.int64) for a in arr]
+                sent, done, got = [0] * 4, [[] for _ in range(4)], [0] * 4
+                buf = (cm.Completion * 4096)()
+                deadline = time.time() + 120
+                while any(g < nq for g in got):
+                    now = time.monotonic_ns()
+                    for i in range(4):
+                        if sent[i] < nq and arr[i][sent[i]] <= now:
+                            m = min(int(np.searchsorted(arr[i], now, side="right")) - sent[i], 256)
+                            if cm.camelot_server_submit(srv, i, 1, wls[i].xq_host[sent[i]:sent[i] + m], m,
+                                                        arr[i][sent[i]:sent[i] + m], allow_eagain=True):
+                                sent[i] += m
+                        k = cm.camelot_server_poll(srv, i, buf, 0)
+                        if k:
+                            done[i].append(np.frombuffer(buf, dtype=COMP_DTYPE, count=k).copy())
+                            got[i] += k
+                    if time.time() > deadline:
+                        raise TimeoutError("host-submitted mix")
+                host = {}
                 for i in range(4):
-                    if sent[i] < nq and arr[i][sent[i]] <= now:
-                        m = min(int(np.searchsorted(arr[i], now, side="right")) - sent[i], 256)
-                        if cm.camelot_server_submit(srv, i, 1, wls[i].xq_host[sent[i]:sent[i] + m], m,
-                                                    arr[i][sent[i]:sent[i] + m], allow_eagain=True):
-                            sent[i] += m
-                    k = cm.camelot_server_poll(srv, i, buf, 0)
-                    if k:
-                        done[i].append(np.frombuffer(buf, dtype=COMP_DTYPE, count=k).copy())
-                        got[i] += k
-                if time.time() > deadline:
-                    raise TimeoutError("host-submitted mix")
-            host = {}
-            for i in range(4):
-                c = np.concatenate(done[i])
-                lat = (c["t_poll"] - c["t_arrival"])[500:]
-                st = cm.camelot_server_stats(srv, i)
-                host[names[i]] = {"p99_ms": float(np.percentile(lat, 99)) * 1e-6,
-                                  "p50_ms": float(np.percentile(lat, 50)) * 1e-6,
-                                  "peak_inflight_bytes": st.peak_inflight_bytes, "deferred": st.deferred}
-        finally:
-            cm.camelot_server_destroy(srv)
-            for p in pipes:
-                cm.camelot_pipeline_destroy(p)
-        out["host_submitted"] = {"total_offered_qps": lam_h, "budget_bytes": 256 << 20, "per_pipeline": host}
+                    c = np.concatenate(done[i])
+                    lat = (c["t_poll"] - c["t_arrival"])[500:]
+                    st = cm.camelot_server_stats(srv, i)
+                    host[names[i]] = {"p99_ms": float(np.percentile(lat, 99)) * 1e-6,
+                                      "p50_ms": float(np.percentile(lat, 50)) * 1e-6,
+                                      "peak_inflight_bytes": st.peak_inflight_bytes, "deferred": st.deferred}
+                return host
+            finally:
+                cm.camelot_server_destroy(srv)
+                for p in pipes:
+                    cm.camelot_pipeline_destroy(p)
+
+        hi_h, lo_h, best_h = 0.3 * lam_best, 0.02 * lam_best, None
+        for it in range(6):
+            lam = hi_h if it == 0 else (lo_h * hi_h) ** 0.5
+            r = host_mix(lam, 50 + 10 * it)
+            if all(v["p99_ms"] <= QOS_NS * 1e-6 for v in r.values()):
+                best_h, lo_h = (lam, r), lam
+                if it == 0:
+                    break
+            else:
+                hi_h = lam
+        lam_h, host = best_h if best_h else (0.0, {})
+        out["host_submitted"] = {"peak_total_qps": lam_h, "budget_bytes": 256 << 20, "per_pipeline": host}
     finally:
         for wl in wls:
             wl.close()
@@ -1025,6 +1040,219 @@ def run_serving(args):
                    "queries_per_trace_per_pipeline": q_n},
         "serving": out, "clocks": clk.summary(),
     }
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
+# Artifact stages (the c_i, m_i, p_i of Sec. 2.3 / Sec. 8.5): rows of 4096 f32,
+# batch 16.  Intensity grows with the index for all three families (the
+# reading of Sec. 8.5; Sec. 2.3 orders m the other way round).
+ART_W, ART_B = 4096, 16
+ART_STEPS = {1: 32, 2: 128, 3: 512}                 # c_i: FMA steps per value
+ART_M_R = {1: 16384, 2: 65536, 3: 262144}           # m_i: device-table floats per query (64 KB .. 1 MB)
+ART_P_R = {1: 4096, 2: 16384, 3: 65536}             # p_i: host-table floats per query (16 KB .. 256 KB)
+ART_M_L, ART_P_L = 1 << 28, 1 << 26                  # table sizes: 1 GB device, 256 MB pinned host
+
+
+def run_artifact(args):
+    """Camelot-NC ablation (Sec. 8.4) on the artifact pipelines (the 9 c_j + m_k
+    and the 27 p_i + c_j + m_k of Sec. 8.5), and the host-link contention sweep
+    (Sec. 6.1).
+
+    Every stage is profiled alone (p99 of one batch at each 8-SM quota); the
+    Eq. 1 allocation is solved with the global-memory bandwidth constraint
+    (Camelot: budget = measured HBM copy bandwidth) and without it (Camelot-NC).
+    Each distinct allocation then runs a device-resident Poisson trace of about
+    0.25 s at 90 % of the peak its solver predicts, and its p99 is compared
+    with the QoS.  The sweep copies 1 GB host -> device on k streams at once
+    (k = 1..8) and runs k instances of p_3 in one pipeline."""
+    import torch
+    import synth
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    torch.cuda.set_device(0)
+    sms = (torch.cuda.get_device_properties(0).multi_processor_count // 8) * 8
+    hbm = _peaks().get("hbm_gbs", 6400.0)
+    W, B = ART_W, ART_B
+    g = torch.Generator(device="cuda").manual_seed(0)
+    t_dev = torch.randn(ART_M_L, device="cuda", generator=g) * 1e-3
+    t_host = (torch.randn(ART_P_L, device="cuda", generator=g) * 1e-3).cpu().pin_memory()
+    base = torch.randn((8192, W), device="cuda", generator=g)
+    st = {}
+    for i in (1, 2, 3):
+        st[f"p{i}"] = pl.stage_stream_synth(W, ART_P_R[i], t_host, 0, B)
+        st[f"c{i}"] = pl.stage_compute_synth(W, ART_STEPS[i], 0, B)
+        st[f"m{i}"] = pl.stage_stream_synth(W, ART_M_R[i], t_dev, 5, B)
+    hbm_bytes = {k: B * 2 * W * 4 for k in st}          # rows in and out
+    for i in (1, 2, 3):
+        hbm_bytes[f"m{i}"] = B * (W * 4 + ART_M_R[i] * 4 + 40)
+    levels = list(range(8, sms + 1, 8))
+    out = {"stages": {k: {"desc": v} for k, v in {
+        **{f"c{i}": f"compute: {ART_STEPS[i]} FMA steps per value" for i in (1, 2, 3)},
+        **{f"m{i}": f"memory: {ART_M_R[i] * 4 // 1024} KB of a 1 GB device table per query" for i in (1, 2, 3)},
+        **{f"p{i}": f"host link: {ART_P_R[i] * 4 // 1024} KB of a 256 MB pinned host table per query"
+           for i in (1, 2, 3)}}.items()}}
+    try:
+        # ---- solo profile of every stage
+        buf_in = base[:B].contiguous()
+        buf_out = torch.empty((B, W), device="cuda")
+        idx = torch.empty((B, 5), dtype=torch.int32, device="cuda")
+        val = torch.empty((B, 5), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        dur = {}
+        for k, s_ in st.items():
+            _, _, sb = cm.camelot_stage_info(s_, B)
+            scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+            fin = k.startswith("m")
+            d = []
+            for pq in levels:
+                a = (s_, pq, buf_in, B, None if fin else buf_out, idx if fin else None, val if fin else None, None,
+                     scr, sb, stream)
+                cm.camelot_stage_time(*a, runs=2)
+                d.append(float(np.percentile(cm.camelot_stage_time(*a, runs=20), 99)) * 1e-3)
+            dur[k] = np.array(d)
+            out["stages"][k]["batch_ms_at_8_sms"] = d[0] * 1e3
+            out["stages"][k]["gbs_at_8_sms"] = hbm_bytes[k] / d[0] / 1e9
+
+        def solve(names, bw_budget):
+            n = len(names)
+            f = np.ascontiguousarray(np.stack([B / dur[k] for k in names])[None], np.float64)
+            bw = np.ascontiguousarray(np.stack([hbm_bytes[k] / dur[k] / 1e9 for k in names])[None], np.float64)
+            dd = np.ascontiguousarray(np.stack([dur[k] for k in names])[None], np.float64)
+            mem = np.ascontiguousarray(np.full((1, n), 64e6), np.float64)
+            bs = np.array([B], np.int32)
+            pr = cm.Profile(n, len(levels), 1, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, dd.ctypes.data,
+                            mem.ctypes.data)
+            cons = cm.Constraints(sms, sms // 8, bw_budget, 200e9, QOS_NS * 1e-9, 0.0, cm.SOLVER_EXHAUSTIVE, 0,
+                                  0.0, 0.0, 0)
+            a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
+            inst, quota = [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)]
+            demand = sum(inst[i] * float(bw[0, i, quota[i] // 8 - 1]) for i in range(n))
+            return inst, quota, obj, demand
+
+        buf = (cm.Completion * 8192)()
+
+        def run_trace(p, offs, data):
+            off = torch.from_numpy(offs.astype(np.int64)).cuda()
+            torch.cuda.synchronize()
+            cm.camelot_submit_trace(p, 0, data, len(offs), off)
+            parts, got, t_end = [], 0, time.time() + 120
+            while got < len(offs):
+                k = cm.camelot_poll(p, buf, timeout_us=2000)
+                if k:
+                    parts.append(np.frombuffer(buf, dtype=COMP_DTYPE, count=k).copy())
+                    got += k
+                elif time.time() > t_end:
+                    raise TimeoutError("artifact trace")
+            c = np.concatenate(parts)
+            t_end = time.time() + 10
+            while cm.camelot_pipeline_stats(p).total_launch_ms <= run_trace.last.get(p, 0.0):
+                if time.time() > t_end:
+                    break
+                time.sleep(0.0005)
+            ms = cm.camelot_pipeline_stats(p).total_launch_ms
+            dt = ms - run_trace.last.get(p, 0.0)
+            run_trace.last[p] = ms
+            return c, dt
+        run_trace.last = {}
+
+        def measure(names, inst, quota, lam):
+            stages = [st[k] for k in names]
+            o = pl.options(exit_after_trace=1, query_slots=1 << 19, idle_exit_ns=20_000_000)
+            p = cm.camelot_pipeline_create(stages, pl.alloc(inst, quota, B), 0, o)
+            run_trace.last[p] = 0.0
+            try:
+                nq = int(min(400_000, max(20_000, lam * 0.25)))
+                data = base.repeat((nq + 8191) // 8192, 1)[:nq].contiguous()
+                c, ms = run_trace(p, np.zeros(min(nq, 20_000), np.int64), data)
+                sat = min(nq, 20_000) / (ms * 1e-3)
+                c, _ = run_trace(p, synth.poisson_arrivals_ns(7, nq, lam), data)
+                lat = (c["t_done"] - c["t_arrival"])[nq // 10:]
+                span = (c["t_done"].max() - c["t_arrival"].min()) * 1e-9
+                del data
+                return {"offered_qps": lam, "saturation_qps": sat, "p99_ms": float(np.percentile(lat, 99)) * 1e-6,
+                        "achieved_qps": nq / span, "queries": nq}
+            finally:
+                cm.camelot_pipeline_destroy(p)
+
+        # ---- Camelot vs Camelot-NC on the 27 pipelines
+        cases = []
+        combos = [[f"c{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
+        combos += [[f"p{i}", f"c{j}", f"m{k}"] for i in (1, 2, 3) for j in (1, 2, 3) for k in (1, 2, 3)]
+        with ClockSampler(0) as clk:
+            for names in combos:
+                ca = solve(names, hbm)
+                nc = solve(names, 1e12)
+                row = {"pipeline": "+".join(names),
+                       "camelot": {"instances": ca[0], "sm_quota": ca[1], "predicted_peak_qps": ca[2],
+                                   "predicted_gbs": ca[3]},
+                       "nc": {"instances": nc[0], "sm_quota": nc[1], "predicted_peak_qps": nc[2],
+                              "predicted_gbs": nc[3]}}
+                row["camelot"].update(measure(names, ca[0], ca[1], 0.9 * ca[2]))
+                if (nc[0], nc[1]) == (ca[0], ca[1]):
+                    row["nc"]["same_as_camelot"] = True
+                else:
+                    row["nc"].update(measure(names, nc[0], nc[1], 0.9 * nc[2]))
+                cases.append(row)
+            # ---- host-link contention: k concurrent 1 GB host -> device copies
+            src = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+            dsts = [torch.empty(1 << 30, dtype=torch.uint8, device="cuda") for _ in range(8)]
+            streams = [torch.cuda.Stream() for _ in range(8)]
+            copies = []
+            for kk in (1, 2, 3, 4, 6, 8):
+                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(kk)]
+                torch.cuda.synchronize()
+                for c_ in range(kk):
+                    with torch.cuda.stream(streams[c_]):
+                        evs[c_][0].record()
+                        dsts[c_].copy_(src, non_blocking=True)
+                        evs[c_][1].record()
+                torch.cuda.synchronize()
+                t = [a.elapsed_time(b_) * 1e-3 for a, b_ in evs]
+                copies.append({"copies": kk, "seconds_per_copy": float(np.mean(t)),
+                               "aggregate_gbs": kk * (1 << 30) / max(t) / 1e9})
+            del dsts, src
+            # ---- k instances of p3 in one pipeline (p3 -> c1 final)
+            pst = []
+            fin = pl.stage_compute_synth(W, ART_STEPS[1], 1, B)
+            try:
+                for kk in (1, 2, 3, 4, 6, 8):
+                    o = pl.options(exit_after_trace=1, query_slots=1 << 16, idle_exit_ns=20_000_000)
+                    p = cm.camelot_pipeline_create([st["p3"], fin], pl.alloc([kk, 2], [8, 8], B), 0, o)
+                    run_trace.last[p] = 0.0
+                    try:
+                        nq = 8000
+                        data = base[:nq].contiguous()
+                        run_trace(p, np.zeros(nq, np.int64), data)
+                        c, ms = run_trace(p, np.zeros(nq, np.int64), data)
+                        thr = nq / (ms * 1e-3)
+                        pst.append({"instances": kk, "queries_per_s": thr,
+                                    "host_link_gbs": thr * ART_P_R[3] * 4 / 1e9,
+                                    "per_instance_gbs": thr * ART_P_R[3] * 4 / 1e9 / kk})
+                    finally:
+                        cm.camelot_pipeline_destroy(p)
+            finally:
+                cm.camelot_stage_release(fin)
+        out["cases"] = cases
+        out["host_link"] = {"concurrent_copies": copies, "p3_instances": pst}
+        viol = lambda r: r.get("p99_ms", 0.0) > QOS_NS * 1e-6
+        diff = [c for c in cases if not c["nc"].get("same_as_camelot")]
+        out["summary"] = {
+            "pipelines": len(cases), "nc_allocation_differs": len(diff),
+            "nc_qos_violations": sum(viol(c["nc"]) for c in diff),
+            "camelot_qos_violations": sum(viol(c["camelot"]) for c in cases),
+            "nc_worst_p99_over_qos": max([c["nc"]["p99_ms"] / (QOS_NS * 1e-6) for c in diff] or [0.0]),
+            "camelot_worst_p99_over_qos": max(c["camelot"]["p99_ms"] / (QOS_NS * 1e-6) for c in cases)}
+    finally:
+        for s_ in st.values():
+            cm.camelot_stage_release(s_)
+    line = {"metric": "Camelot-NC ablation: QoS violations of the Eq. 1 allocation without the global-memory "
+                      "bandwidth constraint, 36 artifact pipelines, at 90 % of each solver's predicted peak",
+            "value": out["summary"]["nc_qos_violations"], "unit": "pipelines violating p99 <= QoS",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "artifact pipelines c_j + m_k and p_i + c_j + m_k, rows of 4096 f32, batch 16",
+                       "qos_p99_ms": QOS_NS / 1e6, "hbm_budget_gbs": hbm},
+            "artifact": out, "clocks": clk.summary()}
     print(json.dumps(line, default=float), flush=True)
     return 0
 
@@ -1056,6 +1284,8 @@ def main():
     ap.add_argument("--pred-samples", type=int, default=20000)
     ap.add_argument("--pred-runs", type=int, default=100)
     ap.add_argument("--serving", action="store_true", help="run the four-pipeline serving study instead")
+    ap.add_argument("--artifact", action="store_true",
+                    help="run the Camelot-NC ablation on the artifact pipelines and the host-link sweep instead")
     ap.add_argument("--diurnal", type=float, default=0.0,
                     help="run the diurnal low-load study over this many seconds (60 = the compressed day)")
     args = ap.parse_args()
@@ -1071,6 +1301,8 @@ def main():
         return run_diurnal(args)
     if args.serving:
         return run_serving(args)
+    if args.artifact:
+        return run_artifact(args)
     dist = None
     if world > 1:
         import torch

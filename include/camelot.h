@@ -477,6 +477,56 @@ camelot_status camelot_server_stats(camelot_server* s, int pipeline, camelot_lan
  * dropped; admitted ones stay in their pipelines). */
 camelot_status camelot_server_destroy(camelot_server* s);
 
+/* ------------------------------------------------------- cross-process ring */
+/* Handoff between stages that run in different processes (the paper's
+ * deployment, Sec. 6.2: each microservice is a process and the next stage maps
+ * the previous one's global-memory output through a CUDA IPC handle).  A ring
+ * of `slots` device buffers of `slot_bytes` each, created by the producer
+ * process, mapped by the consumer process through cudaIpcOpenMemHandle, and
+ * two inter-process CUDA events per slot: ready[k] (the producer's writes to
+ * slot k are done) and free[k] (the consumer's reads of slot k are done).
+ * Ordering on the GPU is by stream waits on those events; no kernel ever waits
+ * for another process.  The host side of each process tells the other which
+ * slot it has recorded (over any host channel, e.g. a pipe): a begin call may
+ * only be made after the matching end call of the other side has returned,
+ * because a stream wait sees an event's most recent record.
+ *   producer: produce_begin(k) -> write slot k on the stream -> produce_end(k)
+ *   consumer: consume_begin(k) -> read slot k on the stream  -> consume_end(k)
+ * Both sides must use the same device. */
+typedef struct camelot_xring camelot_xring;
+#define CAMELOT_XRING_MAX_SLOTS 64
+typedef struct {
+    uint64_t slot_bytes;
+    uint32_t slots;
+    int32_t device;
+    unsigned char mem[64];                                /* cudaIpcMemHandle_t      */
+    unsigned char ready[CAMELOT_XRING_MAX_SLOTS][64];     /* cudaIpcEventHandle_t    */
+    unsigned char free_[CAMELOT_XRING_MAX_SLOTS][64];
+} camelot_xring_handle;
+
+/* Producer side: allocate the slots (one device allocation, 256-byte aligned
+ * slots) and the events, and fill the handle to send to the consumer.  Errors:
+ * EINVAL (slots outside 1..64, slot_bytes 0), ENOMEM, ECUDA. */
+camelot_status camelot_xring_create(uint64_t slot_bytes, uint32_t slots, camelot_xring** out,
+                                    camelot_xring_handle* handle);
+/* Consumer side (another process): map the slots and open the events.
+ * Errors: EINVAL (malformed handle, other device), ECUDA (the handle does not
+ * open in this process, e.g. the creating process itself). */
+camelot_status camelot_xring_open(const camelot_xring_handle* handle, camelot_xring** out);
+/* Device address of slot k (NULL for k out of range). */
+void* camelot_xring_slot(const camelot_xring* x, uint32_t k);
+/* Stream-ordered begin / end of one side's use of slot k (`stream` is a
+ * cudaStream_t; NULL = legacy default stream).  produce_begin waits for
+ * free[k], produce_end records ready[k]; consume_begin waits for ready[k],
+ * consume_end records free[k].  Errors: EINVAL (k, wrong side), ECUDA. */
+camelot_status camelot_xring_produce_begin(camelot_xring* x, uint32_t k, void* stream);
+camelot_status camelot_xring_produce_end(camelot_xring* x, uint32_t k, void* stream);
+camelot_status camelot_xring_consume_begin(camelot_xring* x, uint32_t k, void* stream);
+camelot_status camelot_xring_consume_end(camelot_xring* x, uint32_t k, void* stream);
+/* Unmap (consumer) or free (producer, after the consumer has closed) the ring
+ * and its events. */
+camelot_status camelot_xring_destroy(camelot_xring* x);
+
 /* ------------------------------------------------------------ allocator */
 typedef enum {
     CAMELOT_POLICY_MAX_PEAK = 0,  /* Eq. 1: maximise min_i N_i f_i(p_i)                   */

@@ -80,6 +80,16 @@ class ServerStats(C.Structure):
                 ("status", C.c_int32), ("pad_", C.c_int32)]
 
 
+XRING_MAX_SLOTS = 64
+
+
+class XringHandle(C.Structure):
+    """camelot_xring_handle: plain bytes, safe to send to another process."""
+    _fields_ = [("slot_bytes", C.c_uint64), ("slots", C.c_uint32), ("device", C.c_int32),
+                ("mem", C.c_ubyte * 64), ("ready", (C.c_ubyte * 64) * XRING_MAX_SLOTS),
+                ("free_", (C.c_ubyte * 64) * XRING_MAX_SLOTS)]
+
+
 class Profile(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("n_levels", C.c_int32), ("n_batches", C.c_int32),
                 ("unit", C.c_int32), ("batch_sizes", C.c_void_p), ("thr_qps", C.c_void_p),
@@ -130,6 +140,14 @@ _SIGS = {
     "camelot_server_poll": (C.c_int, [P, C.c_int, P, C.c_uint32, P, C.c_int64]),
     "camelot_server_stats": (C.c_int, [P, C.c_int, P]),
     "camelot_server_destroy": (C.c_int, [P]),
+    "camelot_xring_create": (C.c_int, [C.c_uint64, C.c_uint32, P, P]),
+    "camelot_xring_open": (C.c_int, [P, P]),
+    "camelot_xring_slot": (P, [P, C.c_uint32]),
+    "camelot_xring_produce_begin": (C.c_int, [P, C.c_uint32, P]),
+    "camelot_xring_produce_end": (C.c_int, [P, C.c_uint32, P]),
+    "camelot_xring_consume_begin": (C.c_int, [P, C.c_uint32, P]),
+    "camelot_xring_consume_end": (C.c_int, [P, C.c_uint32, P]),
+    "camelot_xring_destroy": (C.c_int, [P]),
 }
 
 _lib = None
@@ -390,3 +408,41 @@ def camelot_server_stats(s: int, pipeline: int) -> ServerStats:
 
 def camelot_server_destroy(s: int) -> None:
     _check(load().camelot_server_destroy(s))
+
+
+def camelot_xring_create(slot_bytes: int, slots: int):
+    """Producer side: returns (ring, handle bytes for the consumer process)."""
+    x, h = C.c_void_p(), XringHandle()
+    _check(load().camelot_xring_create(slot_bytes, slots, C.byref(x), C.byref(h)))
+    return x.value, bytes(h)
+
+
+def camelot_xring_open(handle: bytes) -> int:
+    h = XringHandle.from_buffer_copy(handle)
+    x = C.c_void_p()
+    _check(load().camelot_xring_open(C.byref(h), C.byref(x)))
+    return x.value
+
+
+def camelot_xring_slot(x: int, k: int) -> int:
+    return load().camelot_xring_slot(x, k) or 0
+
+
+def camelot_xring_produce_begin(x: int, k: int, stream=None) -> None:
+    _check(load().camelot_xring_produce_begin(x, k, _ptr(stream)))
+
+
+def camelot_xring_produce_end(x: int, k: int, stream=None) -> None:
+    _check(load().camelot_xring_produce_end(x, k, _ptr(stream)))
+
+
+def camelot_xring_consume_begin(x: int, k: int, stream=None) -> None:
+    _check(load().camelot_xring_consume_begin(x, k, _ptr(stream)))
+
+
+def camelot_xring_consume_end(x: int, k: int, stream=None) -> None:
+    _check(load().camelot_xring_consume_end(x, k, _ptr(stream)))
+
+
+def camelot_xring_destroy(x: int) -> None:
+    _check(load().camelot_xring_destroy(x))

@@ -582,7 +582,9 @@ static __device__ bool compute_synth_body(const StageCtx& cx, const StageParams&
 }
 
 // STREAM_SYNTH: y_j = x_j + sum over the query's P.H table windows, added in
-// window order; 16 table loads in flight per thread.
+// window order.  Each CTA first works out the window start of every query of
+// the batch (shared memory), so the table loads depend on nothing in flight;
+// 32 table loads of 16 bytes are in flight per thread.
 static __device__ bool stream_synth_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                          RowRef out, const FinalOut& fo) {
     const int W4 = P.W / 4, terms = P.H;
@@ -590,15 +592,19 @@ static __device__ bool stream_synth_body(const StageCtx& cx, const StageParams& 
     const float4* T = reinterpret_cast<const float4*>(P.layer[0].w);
     const bool fin = P.top_k > 0;
     const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)P.W * 4} : out;
+    uint32_t* wstart = reinterpret_cast<uint32_t*>(cx.smem);     // [n] window index per query
+    for (int q = threadIdx.x; q < n; q += kThreads) {
+        const uint32_t bits = __float_as_uint(*reinterpret_cast<const float*>(in.row(q)));
+        const uint32_t h = (uint32_t)(((unsigned long long)bits * 0x9E3779B97F4A7C15ull) >> 32);
+        wstart[q] = h % starts;
+    }
+    __syncthreads();
     const int total = n * W4;
-    constexpr int U = 16;
+    constexpr int U = 32;
     for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
         const int q = e / W4, c = e - q * W4;
-        const float* xr = reinterpret_cast<const float*>(in.row(q));
-        const uint32_t bits = __float_as_uint(xr[0]);
-        const uint32_t h = (uint32_t)(((unsigned long long)bits * 0x9E3779B97F4A7C15ull) >> 32);
-        const float4* tw = T + (size_t)(h % starts) * W4 + c;
-        float4 acc = __ldcs(reinterpret_cast<const float4*>(xr) + c);
+        const float4* tw = T + (size_t)wstart[q] * W4 + c;
+        float4 acc = __ldcs(reinterpret_cast<const float4*>(in.row(q)) + c);
         for (int r0 = 0; r0 < terms; r0 += U) {
             float4 t[U];
 #pragma unroll
