@@ -363,6 +363,7 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                 sp.H = R / W;
                 sp.C = L / W - R / W + 1;
                 sp.layer[0].w = (const float*)dp;
+                sp.layer[0].act = a.type == cudaMemoryTypeHost ? 1 : 0;   // table in pinned host memory
             }
             // scratch: a final stage's output rows, then the result arrays
             size_t off = 0;

@@ -3,6 +3,7 @@
 // instantiation holding just its own kinds, so the compiler lays out and
 // allocates registers for those bodies only.
 #pragma once
+#include "artifact.cuh"
 #include "gemm_bf16.cuh"
 #include "stages.cuh"
 

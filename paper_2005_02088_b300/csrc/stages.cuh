@@ -486,19 +486,28 @@ static __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int
 #pragma unroll
         for (int r = 0; r < kMaxTopK; ++r) { bv[r] = -INFINITY; bi[r] = 0x7fffffff; }
         const float* zr = reinterpret_cast<const float*>(z.row(q));
-        for (int j = lane; j < N; j += 32) {
-            const float v = __ldcg(zr + j);
-            if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
-            // insert (v, j): j grows along the scan, so ties keep the earlier index first
-            if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
-                float cv = v;
-                int ci = j;
+        // 8 loads in flight per lane, then the insertions in index order
+        for (int j0 = lane; j0 < N; j0 += 32 * 8) {
+            float vv[8];
 #pragma unroll
-                for (int r = 0; r < kMaxTopK; ++r) {
-                    if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
-                        const float tv = bv[r];
-                        const int ti = bi[r];
-                        bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+            for (int u = 0; u < 8; ++u) vv[u] = j0 + 32 * u < N ? __ldcg(zr + j0 + 32 * u) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u;
+                if (j >= N) break;
+                const float v = vv[u];
+                if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
+                // insert (v, j): j grows along the lane's scan, so ties keep the earlier index first
+                if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
+                    float cv = v;
+                    int ci = j;
+#pragma unroll
+                    for (int r = 0; r < kMaxTopK; ++r) {
+                        if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
+                            const float tv = bv[r];
+                            const int ti = bi[r];
+                            bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+                        }
                     }
                 }
             }
@@ -545,87 +554,6 @@ static __device__ void token_argmax(const StageCtx& cx, RowRef z, int n, int T, 
             if (fo.logits.base != nullptr) reinterpret_cast<int32_t*>(fo.logits.row(q))[t] = bi;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Artifact stages (the c_i, m_i and p_i of Sec. 2.3 and Sec. 8.5): tunable
-// compute, memory or host-link intensity.  An intermediate stage writes its
-// f32 rows to `out`; a final one writes them to the instance's scratch and
-// takes their top-k.
-// ---------------------------------------------------------------------------
-// COMPUTE_SYNTH: y <- fma(y, 127/128, x / 128), P.H steps from y = 0, per
-// value; every thread runs four independent chains (one float4).
-static __device__ bool compute_synth_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
-                                          RowRef out, const FinalOut& fo) {
-    const int W4 = P.W / 4, steps = P.H;
-    const bool fin = P.top_k > 0;
-    const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)P.W * 4} : out;
-    const int total = n * W4;
-    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
-        const int q = e / W4, c = e - q * W4;
-        const float4 x = __ldcs(reinterpret_cast<const float4*>(in.row(q)) + c);
-        const float b0 = x.x * 0.0078125f, b1 = x.y * 0.0078125f, b2 = x.z * 0.0078125f, b3 = x.w * 0.0078125f;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 8
-        for (int i = 0; i < steps; ++i) {
-            a0 = __fmaf_rn(a0, 0.9921875f, b0);
-            a1 = __fmaf_rn(a1, 0.9921875f, b1);
-            a2 = __fmaf_rn(a2, 0.9921875f, b2);
-            a3 = __fmaf_rn(a3, 0.9921875f, b3);
-        }
-        __stcg(reinterpret_cast<float4*>(y.row(q)) + c, make_float4(a0, a1, a2, a3));
-    }
-    if (!fin) return true;
-    if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
-    topk_rows(cx, y, n, P.W, P.top_k, fo);
-    return true;
-}
-
-// STREAM_SYNTH: y_j = x_j + sum over the query's P.H table windows, added in
-// window order.  Each CTA first works out the window start of every query of
-// the batch (shared memory), so the table loads depend on nothing in flight;
-// 32 table loads of 16 bytes are in flight per thread.
-static __device__ bool stream_synth_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
-                                         RowRef out, const FinalOut& fo) {
-    const int W4 = P.W / 4, terms = P.H;
-    const uint32_t starts = (uint32_t)P.C;
-    const float4* T = reinterpret_cast<const float4*>(P.layer[0].w);
-    const bool fin = P.top_k > 0;
-    const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)P.W * 4} : out;
-    uint32_t* wstart = reinterpret_cast<uint32_t*>(cx.smem);     // [n] window index per query
-    for (int q = threadIdx.x; q < n; q += kThreads) {
-        const uint32_t bits = __float_as_uint(*reinterpret_cast<const float*>(in.row(q)));
-        const uint32_t h = (uint32_t)(((unsigned long long)bits * 0x9E3779B97F4A7C15ull) >> 32);
-        wstart[q] = h % starts;
-    }
-    __syncthreads();
-    const int total = n * W4;
-    constexpr int U = 32;
-    for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
-        const int q = e / W4, c = e - q * W4;
-        const float4* tw = T + (size_t)wstart[q] * W4 + c;
-        float4 acc = __ldcs(reinterpret_cast<const float4*>(in.row(q)) + c);
-        for (int r0 = 0; r0 < terms; r0 += U) {
-            float4 t[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (r0 + u < terms) t[u] = __ldcs(tw + (size_t)(r0 + u) * W4);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (r0 + u < terms) {
-                    acc.x += t[u].x;
-                    acc.y += t[u].y;
-                    acc.z += t[u].z;
-                    acc.w += t[u].w;
-                }
-            }
-        }
-        __stcg(reinterpret_cast<float4*>(y.row(q)) + c, acc);
-    }
-    if (!fin) return true;
-    if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
-    topk_rows(cx, y, n, P.W, P.top_k, fo);
-    return true;
 }
 
 // The whole FP32 MLP stage.  Returns false if a group barrier failed.
