@@ -61,7 +61,7 @@ WORKLOADS = {
               "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
               "arrivals; p99 QoS 20 ms"),
         batch=32, row=224 * 224 * 3, even=([1, 1, 1], [48, 48, 48]),
-        profile_alloc=([5, 10, 3], [8, 8, 8]),
+        profile_alloc=([3, 11, 4], [8, 8, 8]),
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
@@ -1055,9 +1055,9 @@ ART_M_L, ART_P_L = 1 << 28, 1 << 26                  # table sizes: 1 GB device,
 
 
 def run_artifact(args):
-    """Camelot-NC ablation (Sec. 8.4) on the artifact pipelines (the 9 c_j + m_k
-    and the 27 p_i + c_j + m_k of Sec. 8.5), and the host-link contention sweep
-    (Sec. 6.1).
+    """Camelot-NC ablation (Sec. 8.4) on the artifact pipelines (the 9 c_j + m_k,
+    9 memory-only m_j + m_k and the 27 p_i + c_j + m_k of Sec. 8.5), and the
+    host-link contention sweep (Sec. 6.1).
 
     Every stage is profiled alone (p99 of one batch at each 8-SM quota); the
     Eq. 1 allocation is solved with the global-memory bandwidth constraint
@@ -1082,13 +1082,17 @@ def run_artifact(args):
         st[f"p{i}"] = pl.stage_stream_synth(W, ART_P_R[i], t_host, 0, B)
         st[f"c{i}"] = pl.stage_compute_synth(W, ART_STEPS[i], 0, B)
         st[f"m{i}"] = pl.stage_stream_synth(W, ART_M_R[i], t_dev, 5, B)
+        st[f"n{i}"] = pl.stage_stream_synth(W, ART_M_R[i], t_dev, 0, B)   # m_i as an intermediate stage
     hbm_bytes = {k: B * 2 * W * 4 for k in st}          # rows in and out
     for i in (1, 2, 3):
         hbm_bytes[f"m{i}"] = B * (W * 4 + ART_M_R[i] * 4 + 40)
+        hbm_bytes[f"n{i}"] = B * (2 * W * 4 + ART_M_R[i] * 4)
     levels = list(range(8, sms + 1, 8))
     out = {"stages": {k: {"desc": v} for k, v in {
         **{f"c{i}": f"compute: {ART_STEPS[i]} FMA steps per value" for i in (1, 2, 3)},
         **{f"m{i}": f"memory: {ART_M_R[i] * 4 // 1024} KB of a 1 GB device table per query" for i in (1, 2, 3)},
+        **{f"n{i}": f"memory (intermediate stage): {ART_M_R[i] * 4 // 1024} KB of the device table per query"
+           for i in (1, 2, 3)},
         **{f"p{i}": f"host link: {ART_P_R[i] * 4 // 1024} KB of a 256 MB pinned host table per query"
            for i in (1, 2, 3)}}.items()}}
     try:
@@ -1177,6 +1181,7 @@ def run_artifact(args):
         # ---- Camelot vs Camelot-NC on the 27 pipelines
         cases = []
         combos = [[f"c{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
+        combos += [[f"n{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
         combos += [[f"p{i}", f"c{j}", f"m{k}"] for i in (1, 2, 3) for j in (1, 2, 3) for k in (1, 2, 3)]
         with ClockSampler(0) as clk:
             for names in combos:
@@ -1247,12 +1252,83 @@ def run_artifact(args):
         for s_ in st.values():
             cm.camelot_stage_release(s_)
     line = {"metric": "Camelot-NC ablation: QoS violations of the Eq. 1 allocation without the global-memory "
-                      "bandwidth constraint, 36 artifact pipelines, at 90 % of each solver's predicted peak",
+                      "bandwidth constraint, 45 artifact pipelines, at 90 % of each solver's predicted peak",
             "value": out["summary"]["nc_qos_violations"], "unit": "pipelines violating p99 <= QoS",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "artifact pipelines c_j + m_k and p_i + c_j + m_k, rows of 4096 f32, batch 16",
+            "config": {"workload": "artifact pipelines c_j + m_k, m_j + m_k and p_i + c_j + m_k, rows of 4096 f32, batch 16",
                        "qos_p99_ms": QOS_NS / 1e6, "hbm_budget_gbs": hbm},
             "artifact": out, "clocks": clk.summary()}
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
+def run_ipc(args):
+    """Cross-process handoff (Sec. 6.2, setup cost Sec. 8.7): the plain FP32
+    2-stage pipeline with its stages in two processes, batches handed over in
+    place through the CUDA IPC ring, against the same two stages launched by
+    one process on one stream.  Reports the ring setup times (create + export
+    in the producer, open in the consumer), throughput with the ring's 8 slots
+    in flight, and the per-batch latency with one batch in flight."""
+    import torch
+    import synth
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl, xproc
+    torch.cuda.set_device(0)
+    B, n = 16, 4096
+    x, ws = synth.cfg1_inputs(0, n_queries=1024)
+    xr = np.ascontiguousarray(x.reshape(1024, -1)[np.arange(n) % 1024])
+    prod = {"kind": "normalize", "dims": (64, 64, 3)}
+    cons = {"kind": "mlp_fp32", "weights": ws, "acts": [1, 1, 0], "top_k": 1}
+    ctas = (16, 64)
+    # one process, one stream, the same direct launches
+    s0 = pl.stage_normalize(64, 64, 3, B)
+    wd = [torch.from_numpy(w).cuda() for w in ws]
+    s1 = pl.stage_dense(cm.STAGE_MLP_FP32, wd, [1, 1, 0], 1, B)
+    try:
+        q = torch.from_numpy(xr).cuda()
+        mid = torch.empty((B, 12288), dtype=torch.float32, device="cuda")
+        idx = torch.empty((B, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty((B, 1), dtype=torch.float32, device="cuda")
+        _, _, sb0 = cm.camelot_stage_info(s0, B)
+        _, _, sb1 = cm.camelot_stage_info(s1, B)
+        scr0 = torch.empty(sb0 + 256, dtype=torch.uint8, device="cuda")
+        scr1 = torch.empty(sb1 + 256, dtype=torch.uint8, device="cuda")
+
+        def one(b):
+            cm.camelot_stage_launch(s0, ctas[0], q[b:b + B], B, mid, None, None, None, scr0, sb0, None)
+            cm.camelot_stage_launch(s1, ctas[1], mid, B, None, idx, val, None, scr1, sb1, None)
+        for b in range(0, 256, B):
+            one(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(0, n, B):
+            one(b)
+        torch.cuda.synchronize()
+        local_qps = n / (time.perf_counter() - t0)
+        lat = []
+        for b in range(0, 64 * B, B):
+            t = time.perf_counter_ns()
+            one(b)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter_ns() - t) * 1e-9)
+        local_lat = float(np.median(lat))
+    finally:
+        cm.camelot_stage_release(s0)
+        cm.camelot_stage_release(s1)
+    with ClockSampler(0) as clk:
+        r = xproc.run_split(prod, cons, xr, batch=B, top_k=1, slots=8, ctas=ctas, paced=False, timeout_s=300)
+        rp = xproc.run_split(prod, cons, xr[:64 * B], batch=B, top_k=1, slots=8, ctas=ctas, paced=True,
+                             timeout_s=300)
+    line = {"metric": "cross-process handoff: queries/s and per-batch latency of the plain 2-stage pipeline with "
+                      "its stages in two processes (CUDA IPC ring) vs one process",
+            "value": n / r["consumer_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["fp32-2stage"]["desc"], "batch": B, "queries": n, "ring_slots": 8,
+                       "ctas": list(ctas), "mps": "not used (the two processes time-share the GPU)"},
+            "ipc": {"ring_create_ms": r["ring_create_s"] * 1e3, "ring_open_ms": r["ring_open_s"] * 1e3,
+                    "two_process_qps": n / r["consumer_s"],
+                    "two_process_batch_latency_ms": float(np.median(rp["latency_s"])) * 1e3,
+                    "one_process_qps": local_qps, "one_process_batch_latency_ms": local_lat * 1e3},
+            "clocks": clk.summary()}
     print(json.dumps(line, default=float), flush=True)
     return 0
 
@@ -1284,6 +1360,7 @@ def main():
     ap.add_argument("--pred-samples", type=int, default=20000)
     ap.add_argument("--pred-runs", type=int, default=100)
     ap.add_argument("--serving", action="store_true", help="run the four-pipeline serving study instead")
+    ap.add_argument("--ipc", action="store_true", help="run the cross-process handoff study instead")
     ap.add_argument("--artifact", action="store_true",
                     help="run the Camelot-NC ablation on the artifact pipelines and the host-link sweep instead")
     ap.add_argument("--diurnal", type=float, default=0.0,
@@ -1303,6 +1380,8 @@ def main():
         return run_serving(args)
     if args.artifact:
         return run_artifact(args)
+    if args.ipc:
+        return run_ipc(args)
     dist = None
     if world > 1:
         import torch

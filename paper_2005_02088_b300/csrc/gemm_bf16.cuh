@@ -56,7 +56,7 @@ struct GemmSmem {
     uint64_t* tfull;       // [2 * kIssuers] accumulator complete
     uint64_t* tfree;       // [2 * kIssuers] accumulator read out (4 arrivals: epilogue warps)
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
-    uint32_t* ring_it;     // stages filled so far (all launches of this CTA)
+    uint32_t* fills;       // [kMaxGemmStages] times each ring slot has been filled (all calls of this CTA)
     uint32_t* acc_it;      // [kIssuers] units finished so far by each issuer
     char* stage_out;       // [4 epilogue warps][kEpiStageBytes] staging of tiled output blocks
 };
@@ -73,8 +73,8 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     g.tfull = g.empty + kMaxGemmStages;
     g.tfree = g.tfull + 2 * kIssuers;
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
-    g.ring_it = g.tmem_slot + 1;
-    g.acc_it = g.ring_it + 1;
+    g.fills = g.tmem_slot + 1;
+    g.acc_it = g.fills + kMaxGemmStages;
     g.stage_out = base + kRingBytes + 1024;
     return g;
 }
@@ -91,7 +91,7 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
             mbar_init(&g.tfull[b], 1);
             mbar_init(&g.tfree[b], 4);
         }
-        *g.ring_it = 0;
+        for (int s = 0; s < kMaxGemmStages; ++s) g.fills[s] = 0;
         for (int w = 0; w < kIssuers; ++w) g.acc_it[w] = 0;
         mbar_fence_init();
     }
@@ -286,7 +286,11 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     const int U = CM * ((rows + kGemmN - 1) / kGemmN);
     const int u0 = (int)((long long)cx.rank * U / cx.nctas);
     const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
-    const uint32_t ring0 = *g.ring_it;
+    // ring positions count from 0 in every call: position gi uses slot gi mod
+    // (stages of this geometry), the fills[slot] + gi / stages -th fill of that
+    // slot, so the barrier phases stay right whatever the tile height (and so
+    // the stage size) of the calls before
+    const uint32_t ring0 = 0;
     uint32_t accb[kIssuers];
 #pragma unroll
     for (int w = 0; w < kIssuers; ++w) accb[w] = g.acc_it[w];
@@ -326,8 +330,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
-                if (gi >= (uint32_t)kGemmStages &&
-                    !mbar_wait_bounded(&g.empty[s], ((gi / kGemmStages) - 1) & 1, cx, 1))
+                const uint32_t use = g.fills[s] + gi / kGemmStages;
+                if (use >= 1 && !mbar_wait_bounded(&g.empty[s], (use - 1) & 1, cx, 1))
                     return false;
                 const size_t kbg = ui.c * (kc_bytes / 128) + kb;   // first k-block of the stage
                 mbar_arrive_expect_tx(&g.full[s], nk * (kATileBytes + kBTileBytes));
@@ -351,7 +355,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
-                if (!mbar_wait_bounded(&g.full[s], (gi / kGemmStages) & 1, cx, 5)) return false;
+                if (!mbar_wait_bounded(&g.full[s], (g.fills[s] + gi / kGemmStages) & 1, cx, 5)) return false;
                 tc_fence_after();
                 // descriptors of the stage's first A and B slices; a slice 32
                 // bytes further along is the start field + 2 (the field is
@@ -431,7 +435,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     if (threadIdx.x == 0 && u0 < u1) {
         uint32_t stages = 0;
         for (int u = u0; u < u1; ++u) stages += info(u).ns;
-        *g.ring_it = ring0 + stages;
+        for (int sl = 0; sl < kGemmStages; ++sl)
+            g.fills[sl] += (stages + (uint32_t)(kGemmStages - 1 - sl)) / (uint32_t)kGemmStages;
         const uint32_t cnt = (uint32_t)(u1 - u0);
         g.acc_it[0] = accb[0] + (cnt + 1) / 2;
         g.acc_it[1] = accb[1] + cnt / 2;
