@@ -1204,18 +1204,29 @@ def run_artifact(args):
             streams = [torch.cuda.Stream() for _ in range(8)]
             copies = []
             for kk in (1, 2, 3, 4, 6, 8):
+                # every copy starts after one start event and the span ends when
+                # the last one finishes (per-stream events alone would miss the
+                # copies' start offsets)
                 evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                        for _ in range(kk)]
+                t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
+                main = torch.cuda.current_stream()
+                t_start.record(main)
                 for c_ in range(kk):
+                    streams[c_].wait_event(t_start)
                     with torch.cuda.stream(streams[c_]):
                         evs[c_][0].record()
                         dsts[c_].copy_(src, non_blocking=True)
                         evs[c_][1].record()
+                for c_ in range(kk):
+                    main.wait_event(evs[c_][1])
+                t_end.record(main)
                 torch.cuda.synchronize()
                 t = [a.elapsed_time(b_) * 1e-3 for a, b_ in evs]
-                copies.append({"copies": kk, "seconds_per_copy": float(np.mean(t)),
-                               "aggregate_gbs": kk * (1 << 30) / max(t) / 1e9})
+                span = t_start.elapsed_time(t_end) * 1e-3
+                copies.append({"copies": kk, "seconds_per_copy": float(np.mean(t)), "span_s": span,
+                               "aggregate_gbs": kk * (1 << 30) / span / 1e9})
             del dsts, src
             # ---- k instances of p3 in one pipeline (p3 -> c1 final)
             pst = []
