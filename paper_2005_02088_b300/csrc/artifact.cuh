@@ -44,7 +44,7 @@ static __device__ bool compute_synth_body(const StageCtx& cx, const StageParams&
 // STREAM_SYNTH over a table in pinned host memory (the p_i): y_j = x_j + sum
 // over the query's P.H table windows, added in window order.  Each CTA first
 // works out the window start of every query of the batch (shared memory), so
-// the table loads depend on nothing in flight; 32 loads of 16 bytes are in
+// the table loads depend on nothing in flight; 16 loads of 16 bytes are in
 // flight per thread.
 static __device__ bool stream_synth_loads(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                          RowRef out, const FinalOut& fo) {
@@ -61,7 +61,7 @@ static __device__ bool stream_synth_loads(const StageCtx& cx, const StageParams&
     }
     __syncthreads();
     const int total = n * W4;
-    constexpr int U = 32;
+    constexpr int U = 16;
     for (int e = cx.rank * kThreads + threadIdx.x; e < total; e += cx.nctas * kThreads) {
         const int q = e / W4, c = e - q * W4;
         const float4* tw = T + (size_t)wstart[q] * W4 + c;

@@ -99,8 +99,8 @@ static __device__ void normalize_body(const StageCtx& cx, const StageParams& P, 
 // Embedding gather of the text-tagging microservice: out row t of query q =
 // E[tok] (bf16, D columns) for 0 <= tok < V, zero otherwise.  One warp takes
 // 8 consecutive token rows at a time: lanes 0-7 read the 8 token IDs, then
-// every lane loads its 16-byte pieces of all 8 table rows (up to 32 loads in
-// flight) before storing them.
+// every lane loads its 16-byte pieces of all 8 table rows (up to 16 loads in
+// flight, 64 pieces of each row per round) before storing them.
 static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowRef in, int n, RowRef out) {
     const int V = P.H, D = P.W, T = P.rows;
     const uint4* E = reinterpret_cast<const uint4*>(P.layer[0].w);
@@ -117,13 +117,13 @@ static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowR
             t = r0 + lane - q * T;
             tk = reinterpret_cast<const int32_t*>(in.row(q))[t];
         }
-        for (int pb = 0; pb < pieces; pb += 128) {
-            uint4 v[8][4];
+        for (int pb = 0; pb < pieces; pb += 64) {
+            uint4 v[8][2];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int tok = __shfl_sync(0xffffffffu, tk, k);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 2; ++i) {
                     const int p = pb + 32 * i + lane;
                     v[k][i] = make_uint4(0u, 0u, 0u, 0u);
                     if (p < pieces && tok >= 0 && tok < V) v[k][i] = __ldg(E + (size_t)tok * pieces + p);
@@ -135,7 +135,7 @@ static __device__ void embed_body(const StageCtx& cx, const StageParams& P, RowR
                 const int qk = __shfl_sync(0xffffffffu, q, k), tt = __shfl_sync(0xffffffffu, t, k);
                 if (r >= rows) break;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 2; ++i) {
                     const int p = pb + 32 * i + lane;
                     if (p < pieces) {
                         char* dst = P.out_tiled ? out.base + tiled_offset(r, (size_t)p * 16, rowb, P.out_tile_h)
