@@ -100,6 +100,27 @@ static __device__ bool stream_synth_loads(const StageCtx& cx, const StageParams&
 constexpr int kStreamStages = 4;
 constexpr uint32_t kStreamChunk = 32 * 1024;
 
+// The ring's mbarriers and their completed fill counts (after the ring),
+// initialised once per kernel launch by stream_setup; calls continue the
+// counts, so the barriers are never re-initialised in use.
+__device__ __forceinline__ char* stream_base(float* smem) {
+    return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem) + 1023) & ~static_cast<uintptr_t>(1023));
+}
+__device__ __forceinline__ uint64_t* stream_bars(float* smem) {
+    return reinterpret_cast<uint64_t*>(stream_base(smem) + kStreamStages * kStreamChunk);
+}
+__device__ __forceinline__ uint32_t* stream_fills(float* smem) {
+    return reinterpret_cast<uint32_t*>(stream_bars(smem) + kStreamStages);
+}
+__device__ __forceinline__ void stream_setup(float* smem) {
+    if (threadIdx.x < kStreamStages) {
+        mbar_init(&stream_bars(smem)[threadIdx.x], 1);
+        stream_fills(smem)[threadIdx.x] = 0u;
+    }
+    if (threadIdx.x == 0) mbar_fence_init();
+    __syncthreads();
+}
+
 static __device__ bool stream_synth_bulk(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                          RowRef out, const FinalOut& fo) {
     const int W = P.W, W4 = W / 4, terms = P.H;
@@ -109,16 +130,13 @@ static __device__ bool stream_synth_bulk(const StageCtx& cx, const StageParams& 
     const RowRef y = fin ? RowRef{cx.scratch + P.layer[0].h_off, 0, ~0ull, (size_t)W * 4} : out;
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(cx.smem) + 1023) & ~static_cast<uintptr_t>(1023));
     float* ring = reinterpret_cast<float*>(base);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + kStreamStages * kStreamChunk);
-    uint32_t* wstart = reinterpret_cast<uint32_t*>(full + kStreamStages);
+    uint64_t* full = stream_bars(cx.smem);
+    uint32_t* sfill = stream_fills(cx.smem);
+    uint32_t* wstart = sfill + kStreamStages;
     const int crows = max(1, (int)(kStreamChunk / ((uint32_t)W * 4)));   // table rows per chunk
     const int nch = (terms + crows - 1) / crows;                        // chunks per query
     const int myq = cx.rank < n ? (n - cx.rank + cx.nctas - 1) / cx.nctas : 0;
     const int total = myq * nch;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStreamStages; ++s) mbar_init(&full[s], 1);
-        mbar_fence_init();
-    }
     for (int i = threadIdx.x; i < myq; i += kThreads) {
         const uint32_t bits = __float_as_uint(*reinterpret_cast<const float*>(in.row(cx.rank + i * cx.nctas)));
         const uint32_t h = (uint32_t)(((unsigned long long)bits * 0x9E3779B97F4A7C15ull) >> 32);
@@ -148,7 +166,7 @@ static __device__ bool stream_synth_bulk(const StageCtx& cx, const StageParams& 
         }
         for (int c = 0; c < nch; ++c) {
             const int g = i * nch + c, s = g % kStreamStages;
-            if (!mbar_wait_bounded(&full[s], (uint32_t)(g / kStreamStages) & 1u, cx, 7)) return false;
+            if (!mbar_wait_bounded(&full[s], (sfill[s] + (uint32_t)(g / kStreamStages)) & 1u, cx, 7)) return false;
             const float4* rows = reinterpret_cast<const float4*>(ring + (size_t)s * (kStreamChunk / 4));
             const int nr = min(crows, terms - c * crows);
             for (int r = 0; r < nr; ++r) {
@@ -174,6 +192,11 @@ static __device__ bool stream_synth_bulk(const StageCtx& cx, const StageParams& 
             if (c4 < W4) __stcg(yr + c4, acc[k]);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int sl = 0; sl < kStreamStages; ++sl)
+            sfill[sl] += (uint32_t)(total + kStreamStages - 1 - sl) / kStreamStages;
+    __syncthreads();
     if (!fin) return true;
     if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
     topk_rows(cx, y, n, W, P.top_k, fo);

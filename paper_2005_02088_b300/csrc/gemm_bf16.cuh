@@ -112,26 +112,6 @@ __device__ __forceinline__ void gemm_teardown(float* smem) {
     if (threadIdx.x < 32) tmem_dealloc(*g.tmem_slot, kTmemCols);
 }
 
-// Bounded wait on an mbarrier phase; records an error and returns false.
-// These waits hand work between the warps of one CTA every few hundred
-// nanoseconds, so they spin on try_wait (which parks the thread in hardware
-// until the phase flips or a short time passes) with no sleep; the deadline,
-// the iteration cap and the pipeline's error word are checked every 256
-// attempts.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, const StageCtx& cx,
-                                                  uint32_t where) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t deadline = gtime() + cx.limit_ns;
-    const uint64_t cap = cx.limit_ns / 16 + 4000000ull;
-    for (uint64_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 0 && (it > cap || gtime() > deadline || has_error(cx.ctl))) {
-            record_error(cx.ctl, DEV_ERR_GROUP_BARRIER, 400 + 10 * cx.where + where);
-            return false;
-        }
-    }
-}
-
 // Output of one layer: bf16 rows, f32 rows (logits) or e4m3 rows.
 enum OutFmt : int { OUT_BF16 = 0, OUT_F32 = 1, OUT_E4M3 = 2 };
 struct LayerOut {

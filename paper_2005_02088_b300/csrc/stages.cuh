@@ -13,6 +13,7 @@
 
 #include "device_sync.cuh"
 #include "stage_params.h"
+#include "tc_ptx.cuh"
 
 namespace camelot {
 
@@ -32,6 +33,27 @@ struct FinalOut {
     float* val;        // [n][top_k]
     RowRef logits;     // final layer output rows (base == nullptr: not wanted)
 };
+
+// Bounded wait on an mbarrier phase; records an error and returns false.
+// These waits hand work between the warps of one CTA every few hundred
+// nanoseconds, so they spin on try_wait (which parks the thread in hardware
+// until the phase flips or a short time passes) with no sleep; the deadline,
+// the iteration cap and the pipeline's error word are checked every 256
+// attempts.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, const StageCtx& cx,
+                                                  uint32_t where) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t deadline = gtime() + cx.limit_ns;
+    const uint64_t cap = cx.limit_ns / 16 + 4000000ull;
+    for (uint64_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && (it > cap || gtime() > deadline || has_error(cx.ctl))) {
+            record_error(cx.ctl, DEV_ERR_GROUP_BARRIER, 400 + 10 * cx.where + where);
+            return false;
+        }
+    }
+}
+
 
 // 16-byte global -> shared copy that bypasses L1 and completes asynchronously;
 // one commit group per weight quad, waited for per lane.
@@ -201,13 +223,33 @@ static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams
 // result is the round-to-nearest-even of the exact value.
 // Work is cut into groups of G consecutive output rows of one query (2G input
 // rows, contiguous in the image).  Each warp streams its groups into two
-// shared-memory buffers with cp.async, the next group's copy in flight while
-// the current one is computed, and each lane produces four consecutive
+// shared-memory buffers with one bulk copy per group (the copy engine moves
+// far more per SM than 16-byte loads do), the next group's copy in flight
+// while the current one is computed, and each lane produces four consecutive
 // outputs (8 bytes) at a time.  Output value m of an output row reads input
 // bytes i0 = 2 m - (m mod C) and i0 + C of the row pair (pixels 2w and 2w + 1,
 // channel c, with m = w C + c).
 // ---------------------------------------------------------------------------
 constexpr int kPoolBufBytes = 12 * 1024;   // per warp and buffer: 2 x 8 warps x 12 KB = 192 KB
+
+// The pool stage's 16 mbarriers (one per warp and buffer) and their completed
+// fill counts, after the buffers.  Initialised once per kernel launch by
+// pool_setup; every later call continues the counts, so the wait parities
+// stay right across batches (mbarriers are never re-initialised in use).
+__device__ __forceinline__ uint64_t* pool_bars(float* smem) {
+    return reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(smem) + kWarps * 2 * kPoolBufBytes);
+}
+__device__ __forceinline__ uint32_t* pool_fills(float* smem) {
+    return reinterpret_cast<uint32_t*>(pool_bars(smem) + 2 * kWarps);
+}
+__device__ __forceinline__ void pool_setup(float* smem) {
+    if (threadIdx.x < 2 * kWarps) {
+        mbar_init(&pool_bars(smem)[threadIdx.x], 1);
+        pool_fills(smem)[threadIdx.x] = 0u;
+    }
+    if (threadIdx.x == 0) mbar_fence_init();
+    __syncthreads();
+}
 
 static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                      RowRef out) {
@@ -221,23 +263,44 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
     const int groups = n * gpq;
     const int d128 = 128 % C;                      // channel step between a lane's items (32 x 4 values)
     uint8_t* buf = reinterpret_cast<uint8_t*>(cx.smem) + warp * 2 * kPoolBufBytes;
-    auto issue = [&](int g, uint8_t* dst) {
+    // device-resident contiguous rows (traces, direct launches): one bulk copy
+    // per group (its 2G input rows are contiguous) into the warp's buffer,
+    // completion on that buffer's mbarrier; rows of the query ring, which may
+    // live in pinned host memory: cp.async
+    const bool bulk = in.mask == ~0ull;
+    uint64_t* bar = pool_bars(cx.smem) + warp * 2;
+    uint32_t* fills = pool_fills(cx.smem) + warp * 2;
+    const uint64_t pol = l2_policy_evict_first();          // each image is read once
+    auto issue = [&](int g, int b) {
         const int q = g / gpq, ho0 = (g - q * gpq) * G;
-        const int nv = min(G, Ho - ho0) * pair_bytes / 16;
-        const uint4* src = reinterpret_cast<const uint4*>(in.row(q) + (size_t)ho0 * pair_bytes);
-        for (int i = lane; i < nv; i += 32) cp_async16(dst + 16 * i, src + i);
-        cp_async_commit();
+        const uint32_t bytes = (uint32_t)(min(G, Ho - ho0) * pair_bytes);
+        const char* src = in.row(q) + (size_t)ho0 * pair_bytes;
+        if (bulk) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bar[b], bytes);
+                bulk_load_hint(buf + b * kPoolBufBytes, src, bytes, &bar[b], pol);
+            }
+        } else {
+            for (int i = lane; i < (int)(bytes / 16); i += 32)
+                cp_async16(buf + b * kPoolBufBytes + 16 * i, reinterpret_cast<const uint4*>(src) + i);
+            cp_async_commit();
+        }
     };
     const int gstride = cx.nctas * kWarps;
     int cur = 0;
+    uint32_t uses[2] = {fills[0], fills[1]};                // completed fills of each buffer (all calls)
     int g = cx.rank * kWarps + warp;
-    if (g < groups) issue(g, buf);
+    if (g < groups) issue(g, 0);
     for (; g < groups; g += gstride, cur ^= 1) {
         if (g + gstride < groups) {
-            issue(g + gstride, buf + (cur ^ 1) * kPoolBufBytes);
-            cp_async_wait<1>();
-        } else {
+            issue(g + gstride, cur ^ 1);
+            if (!bulk) cp_async_wait<1>();
+        } else if (!bulk) {
             cp_async_wait<0>();
+        }
+        if (bulk) {
+            if (!mbar_wait_bounded(&bar[cur], uses[cur] & 1u, cx, 8)) return;
+            ++uses[cur];
         }
         __syncwarp();
         const uint8_t* sm = buf + cur * kPoolBufBytes;
@@ -274,6 +337,10 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
             if (c >= C) c -= C;
         }
         __syncwarp();
+    }
+    if (bulk && lane == 0) {
+        fills[0] = uses[0];
+        fills[1] = uses[1];
     }
 }
 
