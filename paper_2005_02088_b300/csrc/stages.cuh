@@ -226,7 +226,9 @@ static __device__ void normalize_e4m3_body(const StageCtx& cx, const StageParams
 // shared-memory buffers with one bulk copy per group (the copy engine moves
 // far more per SM than 16-byte loads do), the next group's copy in flight
 // while the current one is computed, and each lane produces four consecutive
-// outputs (8 bytes) at a time.  Output value m of an output row reads input
+// outputs (8 bytes) at a time (3-channel images: 12 outputs from three 8-byte
+// loads per input row, so the byte-wise shared-memory reads do not bound it).
+// Output value m of an output row reads input
 // bytes i0 = 2 m - (m mod C) and i0 + C of the row pair (pixels 2w and 2w + 1,
 // channel c, with m = w C + c).
 // ---------------------------------------------------------------------------
@@ -262,6 +264,7 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
     const int gpq = (Ho + G - 1) / G;              // groups per query
     const int groups = n * gpq;
     const int d128 = 128 % C;                      // channel step between a lane's items (32 x 4 values)
+    const bool rgb4 = C == 3 && (P.W / 2) % 4 == 0;    // the 3-channel path below
     uint8_t* buf = reinterpret_cast<uint8_t*>(cx.smem) + warp * 2 * kPoolBufBytes;
     // device-resident contiguous rows (traces, direct launches): one bulk copy
     // per group (its 2G input rows are contiguous) into the warp's buffer,
@@ -305,6 +308,50 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
         __syncwarp();
         const uint8_t* sm = buf + cur * kPoolBufBytes;
         const int q = g / gpq, ho0 = (g - q * gpq) * G;
+        if (rgb4) {
+            // 3 channels, output width a multiple of 4: a lane takes 4 output
+            // pixels (12 values), reading their 24 input bytes of each row with
+            // three 8-byte loads and storing three 8-byte runs
+            const int k4 = (P.W / 2) / 4;                       // items per output row
+            const int items = min(G, Ho - ho0) * k4;
+            for (int it = lane; it < items; it += 32) {
+                const int r = it / k4, k = it - r * k4;
+                const uint2* a0 = reinterpret_cast<const uint2*>(sm + r * pair_bytes + 24 * k);
+                const uint2* a1 = reinterpret_cast<const uint2*>(sm + r * pair_bytes + WC + 24 * k);
+                uint32_t w0[6], w1[6];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const uint2 u0 = a0[t], u1 = a1[t];
+                    w0[2 * t] = u0.x; w0[2 * t + 1] = u0.y;
+                    w1[2 * t] = u1.x; w1[2 * t + 1] = u1.y;
+                }
+                auto byte = [](const uint32_t (&w)[6], int o) { return (w[o >> 2] >> (8 * (o & 3))) & 0xffu; };
+                uint32_t packed[6];
+#pragma unroll
+                for (int v = 0; v < 12; v += 2) {
+                    float y2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = (v + h) / 3, cch = (v + h) % 3;   // output pixel, channel
+                        const int o = 6 * j + cch;                      // pixel 2j, then 2j + 1 at + 3
+                        const uint32_t sum = byte(w0, o) + byte(w0, o + 3) + byte(w1, o) + byte(w1, o + 3);
+                        y2[h] = (static_cast<float>(sum) * 0.25f - 127.5f) * 0.015625f;
+                    }
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(y2[0], y2[1]);
+                    packed[v / 2] = *reinterpret_cast<const uint32_t*>(&pr);
+                }
+                const size_t b0 = ((size_t)(ho0 + r) * out_vals + 12 * k) * 2;   // byte in the output row
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const size_t bt = b0 + 8 * t;
+                    char* dst = P.out_tiled ? out.base + tiled_offset(q, bt, P.out_row_bytes, P.out_tile_h)
+                                            : out.row(q) + bt;
+                    __stcg(reinterpret_cast<uint2*>(dst), make_uint2(packed[2 * t], packed[2 * t + 1]));
+                }
+            }
+            __syncwarp();
+            continue;
+        }
         const int items = min(G, Ho - ho0) * P4;
         int r = lane / P4, i = lane - r * P4;      // output row in the group, item in the row
         int c = (4 * i) % C;                       // channel of the item's first value
