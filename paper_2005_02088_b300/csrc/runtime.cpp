@@ -101,9 +101,11 @@ static void stage_free(camelot_stage* st) {
     delete st;
 }
 
-// K-chunk of a tensor-core layer: 1024 columns for long K, else 256 (whole
-// 128-byte k-blocks for bf16 and e4m3 alike).
-static int choose_kc_gemm(int K) { return std::min(K, K >= 8192 ? 1024 : 256); }
+// K-chunk of a tensor-core layer: the whole K up to 1024 columns (one chunk:
+// no partial sums and no reduce pass; a batch layer of 1024 inputs is a few
+// ring stages per unit), 1024 columns for long K (whole 128-byte k-blocks
+// for bf16 and e4m3 alike).
+static int choose_kc_gemm(int K) { return K <= 1024 ? K : 1024; }
 
 // K-chunk of a task layer: about 128 chunks over K, a multiple of 4 in [32, kMaxKC].
 static int choose_kc(int K) {
