@@ -590,77 +590,88 @@ static __device__ void dense_head(const StageCtx& cx, const LayerParams& L, RowR
 }
 
 // Top-k of each row (value descending, index ascending on ties).  A CTA takes
-// whole rows; its 8 warps scan one segment of the row each (8 loads in flight
-// per lane, insertion into the lane's sorted top-k), reduce their lanes to the
-// segment's top-k, and warp 0 merges the 8 segment lists.  The result does not
-// depend on the split (the order is total).  The logits row is copied on the
-// way when wanted.
+// several rows at once, each with wpr warps (all 8 warps on one row when the
+// CTA has only one row to do, one warp per row when it has 8 or more): every
+// warp scans a segment of its row (8 loads in flight per lane, insertion into
+// the lane's sorted top-k) and reduces its lanes to the segment's top-k, and
+// the row's first warp merges the segment lists.  The result does not depend
+// on the split (the order is total).  The logits row is copied on the way
+// when wanted.
 static __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int k, const FinalOut& fo) {
     __shared__ float s_v[kWarps][kMaxTopK];
     __shared__ int s_i[kWarps][kMaxTopK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int seg = (N + kWarps - 1) / kWarps;
-    for (int q = cx.rank; q < n; q += cx.nctas) {
-        float bv[kMaxTopK];
-        int bi[kMaxTopK];
+    const int rpc = (n + cx.nctas - 1) / cx.nctas;            // rows per CTA
+    int wpr = kWarps;                                          // warps per row
+    while (wpr > 1 && wpr * rpc > kWarps) wpr >>= 1;
+    const int at_once = kWarps / wpr;
+    const int slot = warp / wpr, sw = warp - slot * wpr;       // row slot, warp within the row
+    const int seg = (N + wpr - 1) / wpr;
+    for (int q0 = cx.rank * at_once; q0 < n; q0 += cx.nctas * at_once) {
+        const int q = q0 + slot;
+        if (q < n) {
+            float bv[kMaxTopK];
+            int bi[kMaxTopK];
 #pragma unroll
-        for (int r = 0; r < kMaxTopK; ++r) { bv[r] = -INFINITY; bi[r] = 0x7fffffff; }
-        const float* zr = reinterpret_cast<const float*>(z.row(q));
-        const int jb = warp * seg, je = min(N, jb + seg);
-        for (int j0 = jb + lane; j0 < je; j0 += 32 * 8) {
-            float vv[8];
+            for (int r = 0; r < kMaxTopK; ++r) { bv[r] = -INFINITY; bi[r] = 0x7fffffff; }
+            const float* zr = reinterpret_cast<const float*>(z.row(q));
+            const int jb = sw * seg, je = min(N, jb + seg);
+            for (int j0 = jb + lane; j0 < je; j0 += 32 * 8) {
+                float vv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) vv[u] = j0 + 32 * u < je ? __ldcg(zr + j0 + 32 * u) : 0.f;
+                for (int u = 0; u < 8; ++u) vv[u] = j0 + 32 * u < je ? __ldcg(zr + j0 + 32 * u) : 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + 32 * u;
-                if (j >= je) break;
-                const float v = vv[u];
-                if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
-                // insert (v, j): j grows along the lane's scan, so ties keep the earlier index first
-                if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
-                    float cv = v;
-                    int ci = j;
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + 32 * u;
+                    if (j >= je) break;
+                    const float v = vv[u];
+                    if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
+                    // insert (v, j): j grows along the lane's scan, so ties keep the earlier index first
+                    if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
+                        float cv = v;
+                        int ci = j;
 #pragma unroll
-                    for (int r = 0; r < kMaxTopK; ++r) {
-                        if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
-                            const float tv = bv[r];
-                            const int ti = bi[r];
-                            bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+                        for (int r = 0; r < kMaxTopK; ++r) {
+                            if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
+                                const float tv = bv[r];
+                                const int ti = bi[r];
+                                bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+                            }
                         }
                     }
                 }
             }
-        }
-        // the segment's top-k: k rounds of warp-wide best, the winning lane pops its head
-        for (int r = 0; r < k; ++r) {
-            float v = bv[0];
-            int i = bi[0];
-            warp_best(v, i);
-            if (lane == 0) {
-                s_v[warp][r] = v;
-                s_i[warp][r] = i;
-            }
-            if (bi[0] == i) {
+            // the segment's top-k: k rounds of warp-wide best, the winning lane pops its head
+            for (int r = 0; r < k; ++r) {
+                float v = bv[0];
+                int i = bi[0];
+                warp_best(v, i);
+                if (lane == 0) {
+                    s_v[warp][r] = v;
+                    s_i[warp][r] = i;
+                }
+                if (bi[0] == i) {
 #pragma unroll
-                for (int t = 0; t + 1 < kMaxTopK; ++t) { bv[t] = bv[t + 1]; bi[t] = bi[t + 1]; }
-                bv[kMaxTopK - 1] = -INFINITY;
-                bi[kMaxTopK - 1] = 0x7fffffff;
+                    for (int t = 0; t + 1 < kMaxTopK; ++t) { bv[t] = bv[t + 1]; bi[t] = bi[t + 1]; }
+                    bv[kMaxTopK - 1] = -INFINITY;
+                    bi[kMaxTopK - 1] = 0x7fffffff;
+                }
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            // the 8 k candidates (segment c / k, rank c % k), c = lane and
-            // lane + 32: each lane keeps its two in order, the better first;
-            // empty entries carry index 0x7fffffff and lose every comparison
+        if (q < n && sw == 0) {
+            // the row's wpr k candidates (warp slot * wpr + c / k, rank c % k),
+            // c = lane and lane + 32: each lane keeps its two in order, the
+            // better first; empty entries carry index 0x7fffffff and lose
+            // every comparison
             float cv[2] = {-INFINITY, -INFINITY};
             int ci[2] = {0x7fffffff, 0x7fffffff};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c = lane + 32 * h;
-                if (c < kWarps * k && s_i[c / k][c % k] != 0x7fffffff) {
-                    cv[h] = s_v[c / k][c % k];
-                    ci[h] = s_i[c / k][c % k];
+                if (c < wpr * k && s_i[warp + c / k][c % k] != 0x7fffffff) {
+                    cv[h] = s_v[warp + c / k][c % k];
+                    ci[h] = s_i[warp + c / k][c % k];
                 }
             }
             if (cv[1] > cv[0] || (cv[1] == cv[0] && ci[1] < ci[0])) {
