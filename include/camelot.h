@@ -367,7 +367,8 @@ camelot_status camelot_pipeline_create(camelot_stage* const* stages, int n_stage
  * arrival_ns (host, nullable) gives each query's arrival stamp on the host
  * CLOCK_MONOTONIC scale; NULL stamps them with the time of the call.  All or
  * nothing: EAGAIN if fewer than n slots are free (poll to free them), ESTATE
- * if the pipeline is in the error state or a trace is running. */
+ * if the pipeline is in the error state or a trace is running.  n = 0 queues
+ * nothing, returns OK and stores the next query ID (queries may be NULL). */
 camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id, const void* queries,
                               uint32_t n, const int64_t* arrival_ns, uint64_t* first_query_id);
 
@@ -378,7 +379,8 @@ camelot_status camelot_submit(camelot_pipeline* p, uint32_t stream_id, const voi
  * host is out of the loop.  Requires no outstanding queries and n <=
  * query_slots.  Completion stamps of trace queries are on the device clock.
  * The device buffers must stay valid until the trace's completions are polled.
- * Errors: EINVAL, ESTATE (outstanding queries / error state). */
+ * Errors: EINVAL (null buffer, n = 0, n > query_slots), ESTATE (outstanding
+ * queries / error state). */
 camelot_status camelot_submit_trace(camelot_pipeline* p, uint32_t stream_id, const void* queries,
                                     uint32_t n, const int64_t* arrival_off_ns,
                                     uint64_t* first_query_id);

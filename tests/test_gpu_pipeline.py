@@ -151,6 +151,60 @@ def test_backpressure_eagain_then_drain(stages):
         cm.camelot_pipeline_destroy(p)
 
 
+def test_empty_inputs(stages):
+    """n = 0: a submit queues nothing, launches nothing and returns the next ID;
+    an empty or over-long trace is EINVAL; a poll with nothing outstanding times
+    out empty.  The pipeline then runs normally."""
+    x, _ = cfg1_data(N_Q)
+    p = cm.camelot_pipeline_create(list(stages), pl.alloc([1, 1], [8, 8], 16), 0,
+                                   pl.options(query_slots=64))
+    try:
+        assert cm.camelot_submit(p, 0, None, 0) == 0
+        buf = (cm.Completion * 8)()
+        assert cm.camelot_poll(p, buf, timeout_us=2000) == 0
+        st = cm.camelot_pipeline_stats(p)
+        assert st.submitted == 0 and st.completed == 0 and st.kernel_launches == 0
+        xd = torch.from_numpy(x[:1]).cuda()
+        off = torch.zeros(65, dtype=torch.int64, device="cuda")
+        for n in (0, 65):                     # empty; longer than query_slots
+            with pytest.raises(cm.CamelotError) as e:
+                cm.camelot_submit_trace(p, 0, xd, n, off)
+            assert e.value.status == cm.EINVAL
+        assert cm.camelot_submit(p, 0, x[:3], 3) == 0
+        comps, t_end = [], time.time() + 20
+        while len(comps) < 3 and time.time() < t_end:
+            k = cm.camelot_poll(p, buf, timeout_us=1000)
+            comps += [pl._copy(buf[i]) for i in range(k)]
+        assert [c.query_id for c in comps] == [0, 1, 2] and all(c.status == 0 for c in comps)
+        assert cm.camelot_submit(p, 0, None, 0) == 3
+    finally:
+        cm.camelot_pipeline_destroy(p)
+
+
+def test_trace_fills_every_query_slot(stages):
+    """The longest trace allowed (n = query_slots): every slot of the completion
+    ring in use at once; results equal the host-submitted run."""
+    _, ref, _ = _run(stages, 0)
+    x, _ = cfg1_data(N_Q)
+    xd = torch.from_numpy(x).cuda()
+    off = torch.zeros(N_Q, dtype=torch.int64, device="cuda")
+    sink = torch.zeros((65536, 10), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    p = cm.camelot_pipeline_create(list(stages), pl.alloc([1, 2], [8, 16], 16), 0,
+                                   pl.options(query_slots=N_Q, logits_sink=sink.data_ptr()))
+    try:
+        assert cm.camelot_submit_trace(p, 7, xd, N_Q, off) == 0
+        buf = (cm.Completion * N_Q)()
+        comps, t_end = [], time.time() + 30
+        while len(comps) < N_Q and time.time() < t_end:
+            k = cm.camelot_poll(p, buf, timeout_us=1000)
+            comps += [pl._copy(buf[i]) for i in range(k)]
+    finally:
+        cm.camelot_pipeline_destroy(p)
+    assert [c.query_id for c in comps] == list(range(N_Q))
+    assert np.array_equal(sink[:N_Q].cpu().numpy(), ref)
+
+
 def test_small_data_ring_wraps(stages):
     # 64 pinned query rows behind 256 descriptors: submissions wait for stage 0
     # to free data rows, results are unchanged

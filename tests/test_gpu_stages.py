@@ -166,6 +166,9 @@ def test_launch_rejects_bad_arguments():
             cm.camelot_stage_launch(st, 1, buf, 5, buf, None, None, None, buf, 1 << 20, None)
         assert e.value.status == cm.EINVAL        # n > max_batch
         with pytest.raises(cm.CamelotError) as e:
+            cm.camelot_stage_launch(st, 1, buf, 0, buf, None, None, None, buf, 1 << 20, None)
+        assert e.value.status == cm.EINVAL        # empty batch
+        with pytest.raises(cm.CamelotError) as e:
             cm.camelot_stage_launch(st, 10000, buf, 1, buf, None, None, None, buf, 1 << 20, None)
         assert e.value.status == cm.EINVAL        # more CTAs than SMs
     finally:
