@@ -51,16 +51,22 @@ __device__ __forceinline__ int issuer_of_warp(int warp) { return warp == 1 ? 0 :
 
 struct GemmSmem {
     char* ring;            // stages of 2 weight tiles then 2 query tiles (RingGeom)
-    uint64_t* full;        // [stages] both operands landed (1 arrival + tx bytes)
+    uint64_t* full;        // [stages][kIssuers] both operands landed (1 arrival + tx bytes), one
+                           // barrier per slot and issuer: see gemm_layer_tasks
     uint64_t* empty;       // [stages] MMAs reading the stage are done
     uint64_t* tfull;       // [2 * kIssuers] accumulator complete
     uint64_t* tfree;       // [2 * kIssuers] accumulator read out (4 arrivals: epilogue warps)
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
     uint32_t* fills;       // [kMaxGemmStages] times each ring slot has been filled (all calls of this CTA)
     uint32_t* acc_it;      // [kIssuers] units finished so far by each issuer
+    uint32_t* ifills;      // [kMaxGemmStages][kIssuers] fills of each slot for each issuer (all calls)
     char* stage_out;       // [4 epilogue warps][kEpiStageBytes] staging of tiled output blocks
 };
 constexpr uint32_t kEpiStageBytes = 32 * 32 * 2;   // one 32-row x 32-column block of bf16
+// the barriers and counters of GemmSmem fit the 1024 bytes between the ring and stage_out
+static_assert(8 * (kMaxGemmStages * kIssuers + kMaxGemmStages + 4 * kIssuers) +
+                  4 * (1 + kMaxGemmStages + kIssuers + kMaxGemmStages * kIssuers) <= 1024,
+              "GEMM barrier block");
 
 __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     char* base = reinterpret_cast<char*>(
@@ -69,12 +75,13 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     g.ring = base;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + kRingBytes);
     g.full = bars;
-    g.empty = g.full + kMaxGemmStages;
+    g.empty = g.full + kMaxGemmStages * kIssuers;
     g.tfull = g.empty + kMaxGemmStages;
     g.tfree = g.tfull + 2 * kIssuers;
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
     g.fills = g.tmem_slot + 1;
     g.acc_it = g.fills + kMaxGemmStages;
+    g.ifills = g.acc_it + kIssuers;
     g.stage_out = base + kRingBytes + 1024;
     return g;
 }
@@ -84,7 +91,7 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
     GemmSmem g = gemm_smem(smem);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kMaxGemmStages; ++s) {
-            mbar_init(&g.full[s], 1);
+            for (int w = 0; w < kIssuers; ++w) mbar_init(&g.full[s * kIssuers + w], 1);
             mbar_init(&g.empty[s], 1);
         }
         for (int b = 0; b < 2 * kIssuers; ++b) {
@@ -93,6 +100,7 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
         }
         for (int s = 0; s < kMaxGemmStages; ++s) g.fills[s] = 0;
         for (int w = 0; w < kIssuers; ++w) g.acc_it[w] = 0;
+        for (int i = 0; i < kMaxGemmStages * kIssuers; ++i) g.ifills[i] = 0;
         mbar_fence_init();
     }
     if (threadIdx.x < 32) {
@@ -306,7 +314,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             const uint64_t pol = l2_policy_evict_last();
             const char* wt = reinterpret_cast<const char*>(L.w);
             const int KB = K * esz / 128;                // weight tiles per 128-row block
-            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int, int j, uint32_t gi) {
+            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) {
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
@@ -314,19 +322,31 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 if (use >= 1 && !mbar_wait_bounded(&g.empty[s], (use - 1) & 1, cx, 1))
                     return false;
                 const size_t kbg = ui.c * (kc_bytes / 128) + kb;   // first k-block of the stage
-                mbar_arrive_expect_tx(&g.full[s], nk * (kATileBytes + kBTileBytes));
+                uint64_t* fb = &g.full[s * kIssuers + (r & 1)];      // the issuer that reads it
+                mbar_arrive_expect_tx(fb, nk * (kATileBytes + kBTileBytes));
                 bulk_load_hint(g.ring + s * kStageBytes, wt + ((size_t)ui.mt * KB + kbg) * kATileBytes,
-                               nk * kATileBytes, &g.full[s], pol);
+                               nk * kATileBytes, fb, pol);
                 bulk_load_hint(g.ring + s * kStageBytes + kKbPerStage * kATileBytes,
                                xt + ((size_t)(ui.row0 / kGemmN) * KB + kbg) * kBTileBytes, nk * kBTileBytes,
-                               &g.full[s], pol);
+                               fb, pol);
                 return true;
             });
         } else if (iw >= 0 && lane == 0) {
             constexpr bool f8 = ESZ == 1;
             constexpr uint32_t idesc = f8 ? idesc_e4m3_f32(128, NT) : idesc_bf16_f32(128, NT);
             uint32_t k = accb[iw];
-            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) mutable {
+            // This issuer's fills of each slot so far.  A slot's successive
+            // fills can go to different issuers (the stages of a unit pair
+            // alternate), and the fill before this one may still be landing
+            // when this issuer arrives: on a barrier shared by both issuers
+            // the parity wait would then pass one phase early.  Each (slot,
+            // issuer) barrier is waited on by one thread only, in fill order,
+            // so its phase is never more than one behind the wait.
+            uint32_t uf[kMaxGemmStages];
+#pragma unroll
+            for (int s = 0; s < kMaxGemmStages; ++s) uf[s] = g.ifills[s * kIssuers + iw];
+            const bool done = for_each_stage(u0, u1, ring0, info, [=, &uf](UnitInfo ui, int r, int j,
+                                                                          uint32_t gi) mutable {
                 if ((r & 1) != iw) return true;
                 const int acc = acc_of(iw, k);
                 const int ns = ui.ns;
@@ -335,7 +355,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
                 const int s = gi % kGemmStages;
-                if (!mbar_wait_bounded(&g.full[s], (g.fills[s] + gi / kGemmStages) & 1, cx, 5)) return false;
+                if (!mbar_wait_bounded(&g.full[s * kIssuers + iw], uf[s] & 1u, cx, 5)) return false;
+                ++uf[s];
                 tc_fence_after();
                 // descriptors of the stage's first A and B slices; a slice 32
                 // bytes further along is the start field + 2 (the field is
@@ -369,6 +390,10 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 }
                 return true;
             });
+            if (done) {
+#pragma unroll
+                for (int s = 0; s < kMaxGemmStages; ++s) g.ifills[s * kIssuers + iw] = uf[s];
+            }
         } else if (warp >= kWarpEpi0) {
             // accumulator rows 32 (warp % 4) .. +31, the NT query columns 32 at
             // a time; units in order, each from its issuer's accumulator
