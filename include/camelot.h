@@ -148,6 +148,11 @@ typedef struct {
                                            scales, calibrated by the caller) */
     int32_t rows_per_query;             /* tensor-core kinds: rows per query (0 or 1 = one;
                                            T > 1 = token-level, see above); else 0 */
+    int32_t ring_slots;                 /* tensor-core kinds: slots of the bulk-copy ring that
+                                           streams weight and operand tiles (0 = as many as
+                                           fit in shared memory, at most 5; 2..5 = at most
+                                           that many).  Results do not depend on it.  Other
+                                           kinds: 0.  EINVAL outside these values. */
 } camelot_stage_desc;
 
 /* A prepared stage: validated descriptor plus the library's own copy of its

@@ -37,7 +37,7 @@ class StageDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
                 ("act", C.c_int32 * MAX_LAYERS), ("top_k", C.c_int32), ("max_batch", C.c_int32),
                 ("weights", C.c_void_p * MAX_LAYERS), ("scales", C.c_float * (MAX_LAYERS + 1)),
-                ("rows_per_query", C.c_int32)]
+                ("rows_per_query", C.c_int32), ("ring_slots", C.c_int32)]
 
 
 class Alloc(C.Structure):

@@ -27,7 +27,7 @@ namespace camelot {
 constexpr int kKbPerStage = 2;                   // k-blocks per stage: one 32 KB weight copy
 constexpr uint32_t kATileBytes = 128 * 128;      // one weight tile: 128 rows x 128 bytes
 constexpr uint32_t kRingBytes = 200 * 1024;      // shared memory of the stage ring
-constexpr int kMaxGemmStages = 5;
+constexpr int kMaxGemmStages = kMaxRingSlots;
 constexpr int kIssuers = 2;                      // MMA-issuing warps
 constexpr uint32_t kTmemCols = 512;              // two accumulators per issuer, up to 128 columns each
 
@@ -59,13 +59,13 @@ struct GemmSmem {
     uint32_t* tmem_slot;   // TMEM base address written by tcgen05.alloc
     uint32_t* fills;       // [kMaxGemmStages] times each ring slot has been filled (all calls of this CTA)
     uint32_t* acc_it;      // [kIssuers] units finished so far by each issuer
-    uint32_t* ifills;      // [kMaxGemmStages][kIssuers] fills of each slot for each issuer (all calls)
+    uint32_t* ipar;        // [kIssuers] bit s: phase parity of the issuer's next wait on slot s (all calls)
     char* stage_out;       // [4 epilogue warps][kEpiStageBytes] staging of tiled output blocks
 };
 constexpr uint32_t kEpiStageBytes = 32 * 32 * 2;   // one 32-row x 32-column block of bf16
 // the barriers and counters of GemmSmem fit the 1024 bytes between the ring and stage_out
 static_assert(8 * (kMaxGemmStages * kIssuers + kMaxGemmStages + 4 * kIssuers) +
-                  4 * (1 + kMaxGemmStages + kIssuers + kMaxGemmStages * kIssuers) <= 1024,
+                  4 * (1 + kMaxGemmStages + 2 * kIssuers) <= 1024,
               "GEMM barrier block");
 
 __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
@@ -81,7 +81,7 @@ __device__ __forceinline__ GemmSmem gemm_smem(float* smem) {
     g.tmem_slot = reinterpret_cast<uint32_t*>(g.tfree + 2 * kIssuers);
     g.fills = g.tmem_slot + 1;
     g.acc_it = g.fills + kMaxGemmStages;
-    g.ifills = g.acc_it + kIssuers;
+    g.ipar = g.acc_it + kIssuers;
     g.stage_out = base + kRingBytes + 1024;
     return g;
 }
@@ -100,7 +100,7 @@ __device__ __forceinline__ void gemm_setup(float* smem) {
         }
         for (int s = 0; s < kMaxGemmStages; ++s) g.fills[s] = 0;
         for (int w = 0; w < kIssuers; ++w) g.acc_it[w] = 0;
-        for (int i = 0; i < kMaxGemmStages * kIssuers; ++i) g.ifills[i] = 0;
+        for (int w = 0; w < kIssuers; ++w) g.ipar[w] = 0;
         mbar_fence_init();
     }
     if (threadIdx.x < 32) {
@@ -263,7 +263,12 @@ template <int ESZ, int NT>
 static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L, const char* xt, int rows,
                                         float* Pbuf, const LayerOut& direct) {
     using G = RingGeom<NT>;
-    constexpr int kGemmStages = G::kStages;
+    // ring slots of this layer: all that fit (G::kStages), or fewer when the stage asks for fewer;
+    // the full ring (the usual case) keeps a constant divisor
+    const uint32_t nslot = (L.ring > 0 && L.ring < G::kStages) ? (uint32_t)L.ring : (uint32_t)G::kStages;
+    const bool full_ring = nslot == (uint32_t)G::kStages;
+    auto slot_of = [=](uint32_t gi) { return (int)(full_ring ? gi % (uint32_t)G::kStages : gi % nslot); };
+    auto round_of = [=](uint32_t gi) { return full_ring ? gi / (uint32_t)G::kStages : gi / nslot; };
     constexpr uint32_t kBTileBytes = G::kBTile;
     constexpr uint32_t kStageBytes = G::kStage;
     constexpr int kGemmN = NT;
@@ -275,9 +280,9 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     const int u0 = (int)((long long)cx.rank * U / cx.nctas);
     const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
     // ring positions count from 0 in every call: position gi uses slot gi mod
-    // (stages of this geometry), the fills[slot] + gi / stages -th fill of that
-    // slot, so the barrier phases stay right whatever the tile height (and so
-    // the stage size) of the calls before
+    // nslot, the fills[slot] + gi / nslot -th fill of that slot, so the barrier
+    // phases stay right whatever the tile height (and so the stage size) or the
+    // slot count of the calls before
     const uint32_t ring0 = 0;
     uint32_t accb[kIssuers];
 #pragma unroll
@@ -317,8 +322,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) {
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
-                const int s = gi % kGemmStages;
-                const uint32_t use = g.fills[s] + gi / kGemmStages;
+                const int s = slot_of(gi);
+                const uint32_t use = g.fills[s] + round_of(gi);
                 if (use >= 1 && !mbar_wait_bounded(&g.empty[s], (use - 1) & 1, cx, 1))
                     return false;
                 const size_t kbg = ui.c * (kc_bytes / 128) + kb;   // first k-block of the stage
@@ -335,18 +340,17 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             constexpr bool f8 = ESZ == 1;
             constexpr uint32_t idesc = f8 ? idesc_e4m3_f32(128, NT) : idesc_bf16_f32(128, NT);
             uint32_t k = accb[iw];
-            // This issuer's fills of each slot so far.  A slot's successive
-            // fills can go to different issuers (the stages of a unit pair
-            // alternate), and the fill before this one may still be landing
-            // when this issuer arrives: on a barrier shared by both issuers
-            // the parity wait would then pass one phase early.  Each (slot,
-            // issuer) barrier is waited on by one thread only, in fill order,
-            // so its phase is never more than one behind the wait.
-            uint32_t uf[kMaxGemmStages];
-#pragma unroll
-            for (int s = 0; s < kMaxGemmStages; ++s) uf[s] = g.ifills[s * kIssuers + iw];
-            const bool done = for_each_stage(u0, u1, ring0, info, [=, &uf](UnitInfo ui, int r, int j,
-                                                                          uint32_t gi) mutable {
+            // A slot's successive fills can go to different issuers (the
+            // stages of a unit pair alternate), and the fill before this one
+            // may still be landing when this issuer arrives: on a barrier
+            // shared by both issuers the parity wait would then pass one
+            // phase early.  Each (slot, issuer) barrier is waited on by one
+            // thread only, in fill order, so its phase is never more than one
+            // behind the wait, and the wait needs only its parity: bit s of
+            // par, flipped at every wait on slot s and kept in shared memory
+            // for the next call (a register here, no per-slot array).
+            uint32_t par = g.ipar[iw];
+            for_each_stage(u0, u1, ring0, info, [=](UnitInfo ui, int r, int j, uint32_t gi) mutable {
                 if ((r & 1) != iw) return true;
                 const int acc = acc_of(iw, k);
                 const int ns = ui.ns;
@@ -354,9 +358,10 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                     return false;
                 const int kb = j * kKbPerStage;
                 const int nk = min(kKbPerStage, ui.nkb - kb);
-                const int s = gi % kGemmStages;
-                if (!mbar_wait_bounded(&g.full[s * kIssuers + iw], uf[s] & 1u, cx, 5)) return false;
-                ++uf[s];
+                const int s = slot_of(gi);
+                if (!mbar_wait_bounded(&g.full[s * kIssuers + iw], (par >> s) & 1u, cx, 5)) return false;
+                par ^= 1u << s;
+                g.ipar[iw] = par;
                 tc_fence_after();
                 // descriptors of the stage's first A and B slices; a slice 32
                 // bytes further along is the start field + 2 (the field is
@@ -390,10 +395,6 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
                 }
                 return true;
             });
-            if (done) {
-#pragma unroll
-                for (int s = 0; s < kMaxGemmStages; ++s) g.ifills[s * kIssuers + iw] = uf[s];
-            }
         } else if (warp >= kWarpEpi0) {
             // accumulator rows 32 (warp % 4) .. +31, the NT query columns 32 at
             // a time; units in order, each from its issuer's accumulator
@@ -440,8 +441,8 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     if (threadIdx.x == 0 && u0 < u1) {
         uint32_t stages = 0;
         for (int u = u0; u < u1; ++u) stages += info(u).ns;
-        for (int sl = 0; sl < kGemmStages; ++sl)
-            g.fills[sl] += (stages + (uint32_t)(kGemmStages - 1 - sl)) / (uint32_t)kGemmStages;
+        for (uint32_t sl = 0; sl < nslot; ++sl)
+            g.fills[sl] += (stages + (nslot - 1 - sl)) / nslot;
         const uint32_t cnt = (uint32_t)(u1 - u0);
         g.acc_it[0] = accb[0] + (cnt + 1) / 2;
         g.acc_it[1] = accb[1] + cnt / 2;

@@ -158,6 +158,10 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
         return fail(CAMELOT_EINVAL, "max_batch %d outside 1..256", d->max_batch);
     if (d->top_k < 0 || d->top_k > kMaxTopK)
         return fail(CAMELOT_EINVAL, "top_k %d outside 0..%d", d->top_k, kMaxTopK);
+    const bool tc_kind = d->kind == CAMELOT_STAGE_GEMM_BF16 || d->kind == CAMELOT_STAGE_GEMM_FP8;
+    if (d->ring_slots != 0 && (!tc_kind || d->ring_slots < 2 || d->ring_slots > kMaxRingSlots))
+        return fail(CAMELOT_EINVAL, "ring_slots %d: 0, or 2..%d for tensor-core kinds", d->ring_slots,
+                    kMaxRingSlots);
     camelot_status cs = ensure_configured();
     if (cs != CAMELOT_OK) return cs;
     StageParams sp{};
@@ -289,6 +293,7 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                 Lp.KC = T > 1 ? K : choose_kc_gemm(K);
                 Lp.C = (K + Lp.KC - 1) / Lp.KC;
                 Lp.esz = esz;
+                Lp.ring = d->ring_slots;
                 Lp.vscale = 1.f;
                 Lp.qscale = 0.f;
                 if (f8) {

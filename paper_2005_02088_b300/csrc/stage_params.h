@@ -15,6 +15,7 @@ constexpr int kQGroup = 16;            // queries per register tile of the FP32 
 constexpr int kNBlock = 128;           // neurons per warp task (4 per lane)
 constexpr int kMaxKC = 128;            // largest K-chunk of a warp task
 constexpr int kWRing = 8;              // weight quads in flight per warp (cp.async ring)
+constexpr int kMaxRingSlots = 5;       // tensor-core layers: most bulk-copy ring slots
 constexpr size_t kSmemBytes = 216 * 1024;  // dynamic shared memory per CTA: > half an SM,
                                            // so exactly one CTA fits on an SM
 
@@ -49,7 +50,7 @@ struct LayerParams {
     int32_t esz;        // tensor-core layers: bytes per element (2 bf16, 1 e4m3)
     float vscale;       // tensor-core layers: accumulator scale (1 for bf16)
     float qscale;       // FP8 layers: scale of the output codes (0 = f32 / bf16 output)
-    int32_t pad_;
+    int32_t ring;       // tensor-core layers: ring slots to use (0 = all that fit)
     size_t p_off;       // scratch offset of this layer's partial sums (task layers)
     size_t h_off;       // scratch offset of its output rows (hidden layers / logits)
 };

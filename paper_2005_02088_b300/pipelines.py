@@ -54,11 +54,13 @@ def stage_norm_pool2(H: int, W: int, Cc: int, max_batch: int) -> int:
     return cm.camelot_stage_prepare(d)
 
 
-def stage_dense(kind: int, weights, acts, top_k: int, max_batch: int) -> int:
+def stage_dense(kind: int, weights, acts, top_k: int, max_batch: int, ring_slots: int = 0) -> int:
     """Dense chain stage from device tensors ``weights[l]`` of shape [out, in]
-    (float32 for MLP_FP32, bfloat16 for GEMM_BF16)."""
+    (float32 for MLP_FP32, bfloat16 for GEMM_BF16); ``ring_slots`` caps the
+    bulk-copy ring of a tensor-core stage (0 = all that fit)."""
     d = cm.StageDesc()
     d.kind = kind
+    d.ring_slots = ring_slots
     d.n_layers = len(weights)
     d.dims[0] = weights[0].shape[1]
     for i, w in enumerate(weights):

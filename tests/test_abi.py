@@ -159,3 +159,17 @@ def test_allocate_rejects_bad_input():
     with pytest.raises(cm.CamelotError) as e:
         cm.camelot_allocate(pr, 0, _cons(prob))
     assert e.value.status == cm.EINVAL
+
+
+def test_stage_prepare_rejects_bad_ring_slots():
+    """ring_slots is checked before any device work: 1, 6 and any value on a
+    kind without a bulk-copy ring are EINVAL (no GPU needed)."""
+    import ctypes
+    for kind, slots in ((cm.STAGE_GEMM_BF16, 1), (cm.STAGE_GEMM_BF16, 6), (cm.STAGE_GEMM_FP8, -1),
+                        (cm.STAGE_MLP_FP32, 3), (cm.STAGE_NORMALIZE_U8, 2)):
+        d = cm.StageDesc()
+        d.kind, d.max_batch, d.ring_slots = kind, 16, slots
+        st = ctypes.c_void_p()
+        assert cm.load().camelot_stage_prepare(ctypes.byref(d), ctypes.byref(st)) == cm.EINVAL
+        assert b"ring_slots" in cm.load().camelot_last_error()
+        assert st.value is None

@@ -7,6 +7,8 @@ Tolerance: the accumulation is FP32 in an order the tensor core fixes, so a
 pre-activation may differ from the exact sum by up to 4 K 2^-24 sum|w x|; the
 GELU passes at most 1.13 times that on, and rounding to bf16 adds one bf16
 unit (2^-8 relative) where the two sides round on different sides of a tie."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -136,3 +138,45 @@ def test_three_stage_pipeline_bf16(orc):
     finally:
         for s in (s0, s1, s2):
             cm.camelot_stage_release(s)
+
+
+@pytest.mark.parametrize("slots", [2, 3, 4])
+def test_ring_slots_do_not_change_results(slots):
+    """The 3-stage pipeline with the GEMM stages' bulk-copy rings capped at 2, 3
+    or 4 slots gives bit-identical results to the full ring, over a saturated
+    trace long enough for many ring wraps per CTA.  With an odd slot count a
+    slot's successive fills alternate between the two MMA issuers: the case in
+    which a parity wait on a barrier shared by both issuers can pass a phase
+    early and stall the ring."""
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    n = 2048
+    x, ws32 = synth.cfg2_inputs(0, n_queries=64)
+    xd = torch.from_numpy(np.ascontiguousarray(x.reshape(64, -1))).cuda()[torch.arange(n).cuda() % 64]
+    wd = [_bf(w).cuda() for w in ws32]
+    off = torch.zeros(n, dtype=torch.int64, device="cuda")
+    res = {}
+    for r in (0, slots):
+        st = [pl.stage_norm_pool2(224, 224, 3, max_batch=32),
+              pl.stage_dense(cm.STAGE_GEMM_BF16, [wd[0], wd[1]], [2, 2], top_k=0, max_batch=32, ring_slots=r),
+              pl.stage_dense(cm.STAGE_GEMM_BF16, [wd[2]], [0], top_k=5, max_batch=32, ring_slots=r)]
+        try:
+            torch.cuda.synchronize()
+            p = cm.camelot_pipeline_create(st, pl.alloc([2, 6, 2], [8, 8, 8], 32),
+                                           0, pl.options(exit_after_trace=1))
+            try:
+                assert cm.camelot_submit_trace(p, 0, xd, n, off) == 0
+                buf = (cm.Completion * 4096)()
+                comps, t_end = [], time.time() + 60
+                while len(comps) < n and time.time() < t_end:
+                    k = cm.camelot_poll(p, buf, timeout_us=2000)
+                    comps += [pl._copy(buf[i]) for i in range(k)]
+                assert cm.camelot_pipeline_stats(p).device_status == 0
+            finally:
+                cm.camelot_pipeline_destroy(p)
+        finally:
+            for s in st:
+                cm.camelot_stage_release(s)
+        assert [c.query_id for c in comps] == list(range(n)) and all(c.status == 0 for c in comps)
+        res[r] = (np.array([list(c.idx) for c in comps]), np.array([list(c.val) for c in comps], np.float32))
+    assert np.array_equal(res[0][0], res[slots][0])
+    assert np.array_equal(res[0][1].view(np.uint32), res[slots][1].view(np.uint32))
