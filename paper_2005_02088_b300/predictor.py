@@ -320,7 +320,7 @@ def study(runners: dict, costs: dict, *, n_samples: int = 20000, runs: int = 100
           total_sms: int = 148, unit: int = 8, batches=tuple(range(1, 65)), alloc_batches=(8, 16, 32, 64),
           epochs: int = 600, lr: float = 3e-3, lr_final: float = 3e-4, co_bytes: int = 1 << 30,
           bw_gbs: float = 6500.0, qos_s: float = 20e-3, train_frac: float = 0.7, log=None) -> dict:
-    """Profile, train and judge the predictor end to end.
+    """Profile, train and evaluate the predictor end to end.
 
     1. ``n_samples`` random (stage, batch, SM quota, co-runner quota)
        configurations, each labelled with the p99 of ``runs`` launches.

@@ -229,7 +229,7 @@ def test_stage_time_and_corunner(orc):
 
 def test_predictor_study_small():
     """Profile the cfg1 stages under random quotas, batches and co-runners,
-    train on the GPU, and judge: held-out MAPE, the gain over the
+    train on the GPU, and evaluate: held-out MAPE, the gain over the
     contention-unaware solo-profile table, and Eq. 1 allocation from the
     predicted table within 5% of brute force over the measured table."""
     from paper_2005_02088_b300 import camelot as cm, predictor as pr
