@@ -495,30 +495,45 @@ class Workload:
         one saturated trace; returns the fastest and the table.  The solo profile
         behind Eq. 1 does not see the per-batch hand-over cost inside the
         pipeline nor the co-location of the stages, so neighbours of its choice
-        can run faster."""
+        can run faster.  When the choice has instances wider than 8 SMs, the
+        same SMs split into 8-SM instances, and that split's neighbours, are
+        measured too (the solo profile can favour a wide instance whose extra
+        SMs the pipeline does not use)."""
         n = len(inst)
-        cands = [list(inst)]
-        for i in range(n):
-            for j in range(n):
-                if i != j and inst[i] > 1:
-                    c = list(inst)
-                    c[i] -= 1
-                    c[j] += 1
-                    cands.append(c)
-            c = list(inst)
-            c[i] += 1
-            cands.append(c)
-        cands = [c for c in cands if sum(a * b for a, b in zip(c, quota)) <= (self.sms // 8) * 8]
+
+        def neighbours(base, q):
+            out = [(list(base), list(q))]
+            for i in range(n):
+                for j in range(n):
+                    if i != j and base[i] > 1:
+                        c = list(base)
+                        c[i] -= 1
+                        c[j] += 1
+                        out.append((c, list(q)))
+                c = list(base)
+                c[i] += 1
+                out.append((c, list(q)))
+            return out
+
+        cands = neighbours(inst, quota)
+        if any(q != 8 for q in quota):
+            cands += neighbours([a * q // 8 for a, q in zip(inst, quota)], [8] * n)
+        seen, uniq = set(), []
+        for c, q in cands:
+            key = (tuple(c), tuple(q))
+            if key not in seen and sum(a * b for a, b in zip(c, q)) <= (self.sms // 8) * 8:
+                seen.add(key)
+                uniq.append((c, q))
         table = []
-        for c in cands:
-            p = self.pipeline(0, c, quota)
+        for c, q in uniq:
+            p = self.pipeline(0, c, q)
             try:
                 _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
-                table.append({"instances": c, "sm_quota": list(quota), "saturation_qps": Q_STEP / (ms * 1e-3)})
+                table.append({"instances": c, "sm_quota": q, "saturation_qps": Q_STEP / (ms * 1e-3)})
             finally:
                 self.cm.camelot_pipeline_destroy(p)
         best = max(table, key=lambda r: r["saturation_qps"])
-        return best["instances"], list(quota), table
+        return best["instances"], best["sm_quota"], table
 
     def allocate(self, levels, dur, qos_s=QOS_NS * 1e-9):
         cm = self.cm
@@ -679,7 +694,8 @@ def run_gpu(args, rank: int, world: int, dist):
         "config": {"workload": w["desc"], "queries_per_step": Q_STEP, "batch": w["batch"],
                    "alloc": {"instances": inst, "sm_quota": quota,
                              "chosen_by": "camelot_allocate (Eq. 1 on the solo profile), then the fastest by measured "
-                                          "saturation of that allocation and its one-instance neighbours"},
+                                          "saturation of that allocation and its one-instance neighbours (and of the same SMs "
+                                          "split into 8-SM instances)"},
                    "handoff": "global", "qos_p99_ms": QOS_NS / 1e6, "peak_rate_qps": lam,
                    "l2": "inputs larger than L2 (22,000 query rows, 3.3 GB per step)",
                    "parallelism": "replicas" if world > 1 else "single"},
