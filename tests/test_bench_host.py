@@ -1,0 +1,61 @@
+"""Host logic of the benchmark's allocation refinement (no GPU): which
+allocations it measures and which it keeps."""
+import os
+import sys
+import types
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+
+
+class _FakeWorkload:
+    """Stands in for bench.Workload: records the allocations created and
+    returns a saturated-trace duration from a given rate table."""
+
+    def __init__(self, rate, sms=148):
+        self.sms = sms
+        self.rate = rate
+        self.made = []
+        self.cm = types.SimpleNamespace(camelot_pipeline_destroy=lambda p: None)
+
+    def pipeline(self, mode, inst, quota):
+        assert mode == 0
+        self.made.append((tuple(inst), tuple(quota)))
+        return len(self.made) - 1
+
+    def trace(self, p, offsets):
+        inst, quota = self.made[p]
+        return None, len(offsets) / self.rate(inst, quota) * 1e3
+
+
+def _total(inst, quota):
+    return sum(a * q for a, q in zip(inst, quota))
+
+
+def test_refine_neighbours_within_sm_budget():
+    wl = _FakeWorkload(lambda i, q: 1.0 + i[1])
+    inst, quota, table = bench.Workload.refine(wl, [3, 12, 3], [8, 8, 8])
+    allocs = {(tuple(r["instances"]), tuple(r["sm_quota"])) for r in table}
+    assert len(allocs) == len(table)                     # each measured once
+    assert ((3, 12, 3), (8, 8, 8)) in allocs             # the allocator's own choice
+    assert all(_total(a, q) <= 144 for a, q in allocs)   # 18 units of 8 SMs on 148 SMs
+    # moves of one instance between stages (the +1 moves exceed the budget)
+    assert allocs == {((3, 12, 3), (8, 8, 8)), ((2, 13, 3), (8, 8, 8)), ((2, 12, 4), (8, 8, 8)),
+                      ((4, 11, 3), (8, 8, 8)), ((3, 11, 4), (8, 8, 8)), ((4, 12, 2), (8, 8, 8)),
+                      ((3, 13, 2), (8, 8, 8))}
+    assert (inst, quota) == ([2, 13, 3], [8, 8, 8])       # the fastest under the fake rates
+
+
+def test_refine_tries_the_8_sm_split_of_wide_instances():
+    # a pipeline in which two 8-SM instances beat one 16-SM instance
+    wl = _FakeWorkload(lambda i, q: 1.0 + sum(a for a, w in zip(i, q) if w == 8))
+    inst, quota, table = bench.Workload.refine(wl, [1, 16], [16, 8])
+    allocs = {(tuple(r["instances"]), tuple(r["sm_quota"])) for r in table}
+    assert ((1, 16), (16, 8)) in allocs and ((2, 16), (8, 8)) in allocs
+    assert all(_total(a, q) <= 144 for a, q in allocs)
+    assert quota == [8, 8] and _total(inst, quota) <= 144
+    # nothing to split: only the one-instance neighbours
+    wl2 = _FakeWorkload(lambda i, q: 1.0)
+    _, _, t2 = bench.Workload.refine(wl2, [2, 16], [8, 8])
+    assert all(r["sm_quota"] == [8, 8] for r in t2)
