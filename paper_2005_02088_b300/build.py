@@ -32,6 +32,27 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def _deps(dfile: str):
+    """Prerequisites listed in an nvcc -MD dependency file (None if absent)."""
+    try:
+        text = open(dfile).read()
+    except OSError:
+        return None
+    text = text.replace("\\\n", " ")
+    _, _, rhs = text.partition(":")
+    return [p for p in rhs.split() if p]
+
+
+def _obj_stale(src: str, obj: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    deps = _deps(obj + ".d")
+    if deps is None:
+        return True
+    t = os.path.getmtime(obj)
+    return any(not os.path.exists(p) or os.path.getmtime(p) > t for p in deps + [src, os.path.abspath(__file__)])
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
@@ -39,8 +60,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(objdir, exist_ok=True)
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        if not force and not _obj_stale(src, obj):
+            return obj
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
-               "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+               "-I", os.path.join(ROOT, "include"), "-MD", "-MF", obj + ".d", "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "cu"] if "runtime" in os.path.basename(src) else []
         if verbose:

@@ -3,10 +3,13 @@ stream, TMEM accumulator) against the FP64 oracle on bf16-rounded operands,
 and of the whole 3-stage pipeline (2x2 pool + normalise to bf16 -> 37632 ->
 1024 -> 1024 GELU -> 1024 -> 1000 logits + top-5).
 
-Tolerance: the accumulation is FP32 in an order the tensor core fixes, so a
-pre-activation may differ from the exact sum by up to 4 K 2^-24 sum|w x|; the
-GELU passes at most 1.13 times that on, and rounding to bf16 adds one bf16
-unit (2^-8 relative) where the two sides round on different sides of a tie."""
+Tolerance: the accumulation is FP32 in an order the tensor core fixes.  A
+pre-activation may differ from the exact sum by at most the instruction-model
+bound of tests/tc_bound.py (per MMA instruction, (t + 2) 2^-23 times the
+accumulator plus the instruction's |products|, summed over the chunk, then
+the chunk-order f32 sum); the GELU passes at most 1.13 times that on, and the
+bf16 output must lie between the roundings of the interval's ends.  The
+serial-sum worst case 4 K 2^-24 sum|w x| is checked as well."""
 import time
 
 import numpy as np
@@ -14,6 +17,8 @@ import pytest
 import torch
 
 import synth
+import tc_bound
+from gpu_common import bf16_chain_check
 
 pytestmark = pytest.mark.gpu
 
@@ -55,11 +60,15 @@ def test_gemm_layer_matches_oracle(orc, K, N, n, act, ctas):
         cm.camelot_stage_launch(st, ctas, xd, n, out, None, None, None, scr, sb, None)
         torch.cuda.synchronize()
         got = _f64(out)
-        ref, bound = _layer_bound(orc, _f64(x), _f64(w), act)
-        err = np.abs(got - ref)
-        lim = bound + 2.0 ** -8 * np.abs(ref) + 1e-30
         assert np.all(np.isfinite(got))
-        assert np.all(err <= lim), float((err / lim).max())
+        # inside the bf16 bracket of the accumulation bound (instruction model)
+        ref, lo, hi = tc_bound.bf16_layer_bracket(orc, _f64(x), _f64(w), act)
+        assert np.all((got >= lo) & (got <= hi))
+        # and inside the serial-sum worst case (4 K u sum|w x|) plus one bf16 unit
+        _, bound = _layer_bound(orc, _f64(x), _f64(w), act)
+        assert np.all(np.abs(got - ref) <= bound + 2.0 ** -8 * np.abs(ref) + 1e-30)
+        # the typical error is far below the bound: nearly every value is the oracle's own rounding
+        assert np.mean(got == orc.round_bf16(ref)) > 0.97, np.mean(got == orc.round_bf16(ref))
     finally:
         cm.camelot_stage_release(st)
 
@@ -128,13 +137,15 @@ def test_three_stage_pipeline_bf16(orc):
         idx = np.array([[c.idx[r] for r in range(5)] for c in comps])
         ref_idx, _ = orc.topk(lg.astype(np.float64), 5)
         assert np.array_equal(idx, ref_idx)                        # exact on its own logits
-        z_emul, idx_emul = orc.pipeline_gemm3(x, [_f64(w) for w in wb], top_k=5, emulate_bf16=True)
-        rel = np.abs(lg - z_emul).max() / np.abs(z_emul).max()
-        assert rel < 2e-2, rel
-        agree = np.mean([set(a) == set(b) for a, b in zip(idx, idx_emul)])
-        assert agree >= 0.8, agree
-        top1 = np.mean(idx[:, 0] == idx_emul[:, 0])
-        assert top1 >= 0.9, top1
+        # element-wise, link by link, against the oracle; top-5 exact where fixed
+        res = bf16_chain_check(orc, x, wb, lg, idx)
+        assert res["top5_fixed_on_gpu_input"] >= 0.9 * n, res
+        # accuracy of the bf16 arm against the unquantised FP64 pipeline (reported)
+        z64, i64 = orc.pipeline_gemm3(x, [np.asarray(w, np.float64) for w in ws32], top_k=5)
+        res["top1_agree_fp64"] = float(np.mean(idx[:, 0] == i64[:, 0]))
+        res["top5_set_agree_fp64"] = float(np.mean([set(a) == set(b) for a, b in zip(idx, i64)]))
+        res["max_abs_err_fp64"] = float(np.abs(lg - z64).max())
+        print("bf16 3-stage parity:", res)
     finally:
         for s in (s0, s1, s2):
             cm.camelot_stage_release(s)
