@@ -74,6 +74,8 @@ def _declare(L):
         "orc_pipeline_gemm3": (None, [P, I64, C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_int,
                                       P, P, C.c_int]),
         "orc_simulate": (I64, [P, I64, C.c_int, C.c_double, C.c_int, P, P, P, P, I64, P, P]),
+        "orc_simulate_qos": (I64, [P, I64, C.c_int, C.c_double, C.c_double, P, C.c_int, P, P, P, P, I64,
+                                   P, P, P]),
         "orc_allocate_exhaustive": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
                                     + [C.c_int] + [P] * 5),
         "orc_allocate_anneal": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
@@ -349,6 +351,25 @@ def simulate(arrivals_s, B: int, t_wait: float, instances, tau, caps=None, mult=
                             _p(caps), _p(mult) if mult is not None else None, mlen, _p(done),
                             _p(bs))
     return done, bs[:nb]
+
+
+def simulate_qos(arrivals_s, B: int, t_wait: float, qos_budget: float, lat, instances, tau, caps=None):
+    """simulate() with the QoS form of the batch trigger (Sec. 5.2 step 2): a
+    partial batch of k queries also leaves once its oldest query has waited
+    qos_budget - lat[k - 1] (lat[k - 1] = predicted latency of a k-query batch,
+    qos_budget = QoS less its margin).  Returns (done, batch sizes, issue times)."""
+    arr = _f64(arrivals_s)
+    ns = len(instances)
+    inst = np.ascontiguousarray(instances, dtype=np.int32)
+    tau = _f64(tau).reshape(ns, B)
+    lat = _f64(lat).reshape(B)
+    caps = np.ascontiguousarray(caps if caps is not None else [1 << 30] * ns, dtype=np.int32)
+    done = np.empty(arr.size, np.float64)
+    bs = np.empty(arr.size, np.int32)
+    iss = np.empty(arr.size, np.float64)
+    nb = lib().orc_simulate_qos(_p(arr), arr.size, int(B), float(t_wait), float(qos_budget), _p(lat), ns,
+                                _p(inst), _p(tau), _p(caps), None, 0, _p(done), _p(bs), _p(iss))
+    return done, bs[:nb], iss[:nb]
 
 
 # ---------------------------------------------------------------------------

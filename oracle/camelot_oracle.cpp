@@ -372,9 +372,19 @@ void orc_pipeline_gemm3(const uint8_t* x, int64_t nq, int H, int W, const int* d
 // time of every query (`done`, seconds) and the size of every issued batch in
 // order (`batch_sizes`, may be null; capacity nq).  Returns the number of
 // batches issued.
-int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_stages,
-                     const int* inst, const double* tau, const int* cap, const double* mult,
-                     int64_t mult_len, double* done, int32_t* batch_sizes) {
+//
+// QoS form of the trigger (Sec. 5.2 step 2, "the first query tends to suffer
+// from QoS violation"): with `lat` non-null, a batch of k = min(waiting, B)
+// queries also leaves once the oldest has waited qos_budget - lat[k - 1], where
+// lat[k - 1] is the predicted latency of a k-query batch and qos_budget the QoS
+// bound less its margin: waiting longer would make the oldest query's wait plus
+// its batch's latency exceed the budget.  The wait bound is the smaller of that
+// and t_wait (at once when it is <= 0).  `issue` (nullable, capacity nq)
+// receives the time each batch was issued.
+int64_t orc_simulate_qos(const double* arr, int64_t nq, int B, double t_wait, double qos_budget,
+                         const double* lat, int n_stages, const int* inst, const double* tau,
+                         const int* cap, const double* mult, int64_t mult_len, double* done,
+                         int32_t* batch_sizes, double* issue) {
     struct Batch { int64_t first; int n; };
     struct Ev {
         double t; int stage; int64_t seq; int64_t batch;
@@ -402,6 +412,12 @@ int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_
         return v;
     };
     auto out_slot_free = [&](int s) { return s == n_stages - 1 || slots_used[s] < cap[s]; };
+    // how long the oldest of `waiting` queries may wait before its batch leaves
+    auto wait_bound = [&](int64_t waiting) {
+        if (!lat) return t_wait;
+        const int k = (int)std::min<int64_t>(waiting, B);
+        return std::min(t_wait, std::max(0.0, qos_budget - lat[k - 1]));
+    };
 
     while (completed < nq) {
         // Dispatch everything that can start at time t, later stages first.
@@ -422,11 +438,12 @@ int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_
             while (idle[0] > 0 && out_slot_free(0) && next_issue < next_arr) {
                 int64_t waiting = next_arr - next_issue;
                 bool full = waiting >= B;
-                bool late = t >= arr[next_issue] + t_wait;  // same sum as the event time
+                bool late = t >= arr[next_issue] + wait_bound(waiting);  // same sum as the event time
                 if (!full && !late) break;
                 int b = (int)std::min<int64_t>(waiting, B);
                 batches.push_back({next_issue, b});
                 if (batch_sizes) batch_sizes[batches.size() - 1] = b;
+                if (issue) issue[batches.size() - 1] = t;
                 next_issue += b;
                 idle[0]--;
                 if (n_stages > 1) slots_used[0]++;
@@ -439,7 +456,7 @@ int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_
         if (!evq.empty()) t_next = evq.top().t;
         if (next_arr < nq) t_next = std::min(t_next, arr[next_arr]);
         if (next_issue < next_arr && idle[0] > 0 && out_slot_free(0))
-            t_next = std::min(t_next, arr[next_issue] + t_wait);
+            t_next = std::min(t_next, arr[next_issue] + wait_bound(next_arr - next_issue));
         if (!(t_next < INFINITY)) break;  // nothing can happen: stuck (should not occur)
         t = std::max(t, t_next);
         while (next_arr < nq && arr[next_arr] <= t) next_arr++;
@@ -459,6 +476,13 @@ int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_
         }
     }
     return (int64_t)batches.size();
+}
+
+int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_stages,
+                     const int* inst, const double* tau, const int* cap, const double* mult,
+                     int64_t mult_len, double* done, int32_t* batch_sizes) {
+    return orc_simulate_qos(arr, nq, B, t_wait, 0.0, nullptr, n_stages, inst, tau, cap, mult, mult_len, done,
+                            batch_sizes, nullptr);
 }
 
 // ---------------------------------------------------------------------------

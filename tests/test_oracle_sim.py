@@ -100,3 +100,44 @@ def test_exactly_once_in_order_single_instance(orc):
     assert bs.sum() == arr.size
     assert np.all(np.isfinite(done)) and np.all(done >= arr)
     assert np.all(np.diff(done) >= 0)
+
+
+ARR_QOS = np.array([0.0, 0.75, 1.25, 100.0, 100.125, 100.25, 100.375, 200.0, 300.0, 302.25])
+LAT = [0.5, 1.0, 1.5, 2.0]          # predicted latency of a batch of 1..4
+
+
+def test_qos_trigger_timeline(orc):
+    # Sec. 5.2 step 2 with a latency prediction: budget 3 (QoS less margin), so
+    # k waiting queries may wait 3 - LAT[k-1] = 2.5, 2.0, 1.5, 1.0.  Queries at
+    # 0, 0.75, 1.25: three wait at 1.25 and their bound 1.5 is not yet reached,
+    # so they leave at 1.5.  Four at 100..100.375 fill the batch.  A lone query
+    # at 200 leaves at 202.5.  At 302.25 a second query joins one that has
+    # waited 2.25 > 2.0: the pair leaves at once.
+    done, bs, iss = orc.simulate_qos(ARR_QOS, 4, 10.0, 3.0, LAT, [1], [[0.0625] * 4])
+    assert bs.tolist() == [3, 4, 1, 2]
+    assert iss.tolist() == [1.5, 100.375, 202.5, 302.25]
+    assert done.tolist() == [1.5625] * 3 + [100.4375] * 4 + [202.5625] + [302.3125] * 2
+
+
+def test_qos_trigger_capped_by_wait_bound(orc):
+    # the same arrivals with a fixed wait bound of 1.125 below every QoS bound but
+    # the last: the pair at 0 / 0.75 leaves at 1.125, the query at 1.25 at 2.375
+    done, bs, iss = orc.simulate_qos(ARR_QOS, 4, 1.125, 3.0, LAT, [1], [[0.0625] * 4])
+    assert bs.tolist() == [2, 1, 4, 1, 1, 1]
+    assert iss.tolist() == [1.125, 2.375, 100.375, 201.125, 301.125, 303.375]
+
+
+def test_qos_trigger_budget_spent_issues_on_arrival(orc):
+    # predicted latency above the budget: no query may wait, each leaves on arrival
+    arr = np.array([0.0, 0.5, 0.75])
+    done, bs, iss = orc.simulate_qos(arr, 4, 10.0, 1.0, [2.0, 2.0, 2.0, 2.0], [1], [[0.125] * 4])
+    assert bs.tolist() == [1, 1, 1]
+    assert iss.tolist() == [0.0, 0.5, 0.75]
+
+
+def test_qos_trigger_reduces_to_plain_rule(orc):
+    # zero predicted latency and a budget above the wait bound: the plain trigger
+    arr = np.sort(np.random.default_rng(9).uniform(0, 20, 300))
+    d1, b1 = orc.simulate(arr, 8, 0.3, [1, 2], [[0.05] * 8, [0.2] * 8], caps=[4, 1])
+    d2, b2, _ = orc.simulate_qos(arr, 8, 0.3, 5.0, [0.0] * 8, [1, 2], [[0.05] * 8, [0.2] * 8], caps=[4, 1])
+    assert np.array_equal(b1, b2) and np.array_equal(d1, d2)
