@@ -15,7 +15,8 @@
  *     comparison arm copies every handoff device -> pinned host -> device (the
  *     default main-memory mechanism of Sec. 4.2 and Sec. 6.1).
  *   - Queries wait in a queue and are batched when B of them wait or when the
- *     oldest has waited a bound (Sec. 5.2 steps 1-2).
+ *     oldest would otherwise pass the QoS bound, given the predicted latency
+ *     of the batch, or has waited a fixed bound (Sec. 5.2 steps 1-2).
  *   - camelot_allocate solves the peak-load policy (Eq. 1) and the low-load
  *     resource policy (Eq. 3) over instance counts and SM quotas.
  *
@@ -207,20 +208,29 @@ camelot_status camelot_stage_launch(const camelot_stage* st, int n_ctas, const v
  * whole device pool, a serving loop that cannot afford the latency or the
  * device-wide synchronisation of cudaMalloc/cudaFree mid-request, or a
  * plug-in that is only handed its input and output buffers).  Same arguments
- * and results as camelot_stage_launch, minus the scratch: the stage's scratch
- * lives in a static 16 MiB device array that every GPU loading the library
- * holds until the process exits.  Nothing is allocated by this call.
+ * and results as camelot_stage_launch, minus the scratch, for every stage kind
+ * except the tensor-core ones (GEMM_BF16, GEMM_FP8: refused with EINVAL; use
+ * camelot_stage_launch).  The stage's scratch lives in a static 16 MiB device
+ * array that every GPU loading the library holds until the process exits.
+ * Nothing is allocated by this call.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address and sets the kernel's shared-memory limit; make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The address is kept for the
+ *     life of the process: do not use this call after a cudaDeviceReset.
  *   - Every call on a device shares the one array and leaves its contents
  *     behind; the call clears the part that must start at zero.  Calls whose
  *     kernels overlap on the GPU (other streams, other host threads) race on
  *     the array and give wrong results: order them on one stream.
+ *   - If a wait inside the kernel gives up (2 s), the call's outputs are
+ *     overwritten with a failure pattern once every CTA is done: final
+ *     stages get -1 in every out_idx entry and NaN in out_val and out_logits;
+ *     intermediate stages get 0xFF in every output byte (NaN in f32, bf16 and
+ *     e4m3).  After synchronising the stream, a negative index or a NaN says
+ *     the call failed.
  *   - Errors: EINVAL when the batch needs more than the 16 MiB (the FP32 stage
  *     of the plain 2-stage pipeline needs about 37 KB per query and fits at
- *     every batch it accepts; very wide layers may not), plus those of
- *     camelot_stage_launch. */
+ *     every batch it accepts; very wide layers may not) or the stage is a
+ *     tensor-core stage, plus those of camelot_stage_launch. */
 camelot_status camelot_stage_launch_noalloc(const camelot_stage* st, int n_ctas, const void* in,
                                             uint32_t n, void* out, int32_t* out_idx,
                                             float* out_val, float* out_logits, void* stream);
@@ -345,9 +355,22 @@ typedef struct {
                                reads over the host link; 1: it is device memory which
                                camelot_submit fills with DMA copies (cudaMemcpyAsync,
                                at most two per call) and waits for before publishing   */
+    /* QoS-aware batch trigger (Sec. 5.2 step 2: a partial batch leaves once its
+     * first query "tends to suffer" a QoS violation).  With qos_ns > 0, a batch of
+     * b < B ready queries leaves once its oldest query has waited
+     *     min(max_wait_ns, qos_ns - qos_margin_ns - batch_latency_ns[b - 1])
+     * (at once if that is <= 0): its wait plus the predicted latency of a b-query
+     * batch through all stages would otherwise pass QoS - margin.  qos_ns = 0
+     * keeps the plain max_wait_ns rule.  batch_latency_ns[b - 1] is the predicted
+     * end-to-end service latency of a batch of b (b = 1..32), e.g. filled by
+     * camelot_trigger_latency from the allocation's profile. */
+    int64_t qos_ns;
+    int64_t qos_margin_ns;
+    int64_t batch_latency_ns[32];
 } camelot_options;
 
-/* Fill `o` with the defaults above. */
+/* Fill `o` with the defaults above (qos_ns = qos_margin_ns = 0 and a zero
+ * latency table: the plain max_wait_ns trigger). */
 void camelot_options_default(camelot_options* o);
 
 typedef struct camelot_pipeline camelot_pipeline;
@@ -425,6 +448,15 @@ typedef struct {
 } camelot_stats;
 
 camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);
+
+/* Fault injection on the host, for tests of the device-side timeouts: while
+ * `stall` is non-zero the relay thread of a host-staged pipeline copies no
+ * batch, as if the host link had stopped.  Producers then find no free slot
+ * downstream; their bounded waits give up after wait_limit_ns and the
+ * pipeline enters the error state (later calls return ESTATE; destroy stays
+ * clean).  Nothing is faulted on the GPU.  Errors: EINVAL (null pipeline, not
+ * host-staged). */
+camelot_status camelot_pipeline_stall_relay(camelot_pipeline* p, int stall);
 
 /* Stop the persistent kernel (it exits at its next check), wait for it and
  * free every resource.  Completions not yet polled are dropped. */
@@ -582,6 +614,17 @@ typedef struct {
 camelot_status camelot_allocate(const camelot_profile* prof, camelot_policy policy,
                                 const camelot_constraints* c, camelot_alloc* out,
                                 double* objective);
+
+/* Predicted end-to-end service latency of a batch of b queries (b = 1..32)
+ * through the stages of `alloc` at their allocated quotas, for the QoS-aware
+ * batch trigger (Sec. 5.2 step 2 uses the predicted latency to decide when the
+ * first query is at risk): out_ns[b - 1] = sum_i dur_i(b, level_i) with level_i
+ * = sm_quota[i] / unit - 1 (quotas must be multiples of the profile's unit
+ * within its levels).  dur is interpolated linearly between the profile's batch
+ * sizes; below the smallest one it is the smallest one's duration, above the
+ * largest it grows in proportion to b.  Host-only.  Errors: EINVAL. */
+camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelot_alloc* alloc,
+                                       int64_t* out_ns);
 
 #ifdef __cplusplus
 }

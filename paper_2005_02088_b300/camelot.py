@@ -49,7 +49,8 @@ class Options(C.Structure):
     _fields_ = [("query_slots", C.c_uint32), ("batch_slots", C.c_uint32), ("max_wait_ns", C.c_int64),
                 ("idle_exit_ns", C.c_int64), ("wait_limit_ns", C.c_int64),
                 ("logits_sink", C.c_void_p), ("exit_after_trace", C.c_int32),
-                ("data_slots", C.c_uint32), ("device_data", C.c_int32)]
+                ("data_slots", C.c_uint32), ("device_data", C.c_int32), ("qos_ns", C.c_int64),
+                ("qos_margin_ns", C.c_int64), ("batch_latency_ns", C.c_int64 * 32)]
 
 
 class Completion(C.Structure):
@@ -133,7 +134,9 @@ _SIGS = {
     "camelot_poll": (C.c_int, [P, P, C.c_uint32, P, C.c_int64]),
     "camelot_pipeline_stats": (C.c_int, [P, P]),
     "camelot_pipeline_destroy": (C.c_int, [P]),
+    "camelot_pipeline_stall_relay": (C.c_int, [P, C.c_int]),
     "camelot_allocate": (C.c_int, [P, C.c_int, P, P, P]),
+    "camelot_trigger_latency": (C.c_int, [P, P, P]),
     "camelot_server_options_default": (None, [P]),
     "camelot_server_create": (C.c_int, [P, C.c_int, P, P]),
     "camelot_server_submit": (C.c_int, [P, C.c_int, C.c_uint32, P, C.c_uint32, P]),
@@ -365,11 +368,22 @@ def camelot_pipeline_destroy(p: int) -> None:
     _check(load().camelot_pipeline_destroy(p))
 
 
+def camelot_pipeline_stall_relay(p: int, stall: bool) -> None:
+    _check(load().camelot_pipeline_stall_relay(p, 1 if stall else 0))
+
+
 def camelot_allocate(prof: Profile, policy: int, cons: Constraints):
     a = Alloc()
     obj = C.c_double()
     _check(load().camelot_allocate(C.byref(prof), policy, C.byref(cons), C.byref(a), C.byref(obj)))
     return a, obj.value
+
+
+def camelot_trigger_latency(prof: Profile, alloc: Alloc):
+    """Predicted batch latency in ns for b = 1..32 (a list of 32 ints)."""
+    out = (C.c_int64 * 32)()
+    _check(load().camelot_trigger_latency(C.byref(prof), C.byref(alloc), out))
+    return list(out)
 
 
 def camelot_server_options_default() -> ServerOptions:

@@ -229,3 +229,44 @@ extern "C" camelot_status camelot_allocate(const camelot_profile* prof, camelot_
     if (objective) *objective = policy == CAMELOT_POLICY_MAX_PEAK ? best.thr : (double)best.sms;
     return CAMELOT_OK;
 }
+
+extern "C" camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelot_alloc* alloc,
+                                                  int64_t* out_ns) {
+    if (!prof || !alloc || !out_ns || !prof->batch_sizes || !prof->dur_s)
+        return set_err(CAMELOT_EINVAL, "null argument");
+    const int n = prof->n_stages, L = prof->n_levels, nb = prof->n_batches, unit = prof->unit;
+    if (n < 1 || n > CAMELOT_MAX_STAGES || L < 1 || nb < 1 || unit < 1 || alloc->n_stages != n)
+        return set_err(CAMELOT_EINVAL, "profile and allocation shapes disagree");
+    for (int j = 0; j < nb; ++j)
+        if (prof->batch_sizes[j] < 1 || (j > 0 && prof->batch_sizes[j] <= prof->batch_sizes[j - 1]))
+            return set_err(CAMELOT_EINVAL, "batch_sizes must be positive and increasing");
+    int level[CAMELOT_MAX_STAGES];
+    for (int i = 0; i < n; ++i) {
+        const int q = alloc->sm_quota[i];
+        if (q < unit || q % unit != 0 || q / unit > L)
+            return set_err(CAMELOT_EINVAL, "an SM quota is not a level of the profile");
+        level[i] = q / unit - 1;
+    }
+    auto dur = [&](int j, int i) { return prof->dur_s[((size_t)j * n + i) * L + level[i]]; };
+    for (int b = 1; b <= 32; ++b) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int* bs = prof->batch_sizes;
+            double d;
+            if (b <= bs[0]) {
+                d = dur(0, i);
+            } else if (b >= bs[nb - 1]) {
+                d = dur(nb - 1, i) * (double)b / (double)bs[nb - 1];
+            } else {
+                int j = 0;
+                while (bs[j + 1] < b) ++j;
+                const double f = (double)(b - bs[j]) / (double)(bs[j + 1] - bs[j]);
+                d = dur(j, i) + f * (dur(j + 1, i) - dur(j, i));
+            }
+            if (!(d >= 0.0)) return set_err(CAMELOT_EINVAL, "negative or NaN duration in the profile");
+            t += d;
+        }
+        out_ns[b - 1] = (int64_t)std::llround(t * 1e9);
+    }
+    return CAMELOT_OK;
+}

@@ -48,7 +48,9 @@ __device__ bool reserve_out(const PipeParams& P, const RingDev& r, uint32_t wher
 
 // Stage 0: the wait queue and batch trigger (Sec. 5.2 steps 1-2).  A batch of
 // the oldest waiting tickets leaves when B of them are ready, or when the
-// oldest has waited max_wait_ns.  Executed by warp 0 of the leader CTA; lane 0
+// oldest has waited trig_wait_ns[k - 1] with k ready: max_wait_ns, or less when
+// the QoS rule says that the wait plus the predicted latency of a k-query batch
+// would pass QoS - margin.  Executed by warp 0 of the leader CTA; lane 0
 // returns the command.  Records the arrival time and stream of the claimed
 // tickets for the final stage.
 __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
@@ -111,7 +113,7 @@ __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
         }
         if (!trace && ls.seen_h != h) { ls.seen_h = h; ls.seen_t = now; }
         const uint64_t waited = trace ? (now - (uint64_t)oldest) : (now - ls.seen_t);
-        if (kk < P.B && waited < (uint64_t)P.max_wait_ns) { __nanosleep(200); continue; }
+        if (kk < P.B && waited < (uint64_t)P.trig_wait_ns[kk - 1]) { __nanosleep(200); continue; }
         unsigned long long got = 0;
         if (lane == 0) got = atomicCAS(&P.ctl->in_head.v, h, h + kk);
         got = __shfl_sync(0xffffffffu, got, 0);

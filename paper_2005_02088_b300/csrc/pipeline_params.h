@@ -117,6 +117,9 @@ struct PipeParams {
     TraceDev* trace;
     long long max_wait_ns, idle_ns, limit_ns;
     int exit_after_trace;
+    // batch trigger: a batch of b < B ready queries leaves once its oldest has
+    // waited trig_wait_ns[b - 1] (max_wait_ns, or less under the QoS rule)
+    long long trig_wait_ns[32];
 };
 
 }  // namespace camelot

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -515,6 +516,9 @@ extern "C" void camelot_options_default(camelot_options* o) {
     o->exit_after_trace = 0;
     o->data_slots = 0;
     o->device_data = 0;
+    o->qos_ns = 0;
+    o->qos_margin_ns = 0;
+    for (int b = 0; b < 32; ++b) o->batch_latency_ns[b] = 0;
 }
 
 struct HostRing {   // one batch ring's allocations
@@ -572,6 +576,7 @@ struct camelot_pipeline {
     // relay (host-staged)
     std::thread relay;
     std::atomic<bool> relay_stop{false};
+    std::atomic<bool> relay_hold{false};   // fault injection: the relay moves nothing
     std::atomic<uint64_t> relayed_bytes{0};
     cudaStream_t r_d2h[kMaxStages] = {}, r_h2d[kMaxStages] = {};
     std::vector<cudaEvent_t> r_ev[kMaxStages];
@@ -763,6 +768,10 @@ static void relay_main(camelot_pipeline* p) {
     std::vector<uint64_t> cur(p->n_stages, 0);
     int idle = 0;
     while (!p->relay_stop.load(std::memory_order_relaxed)) {
+        if (p->relay_hold.load(std::memory_order_relaxed)) {
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            continue;
+        }
         bool progress = false;
         for (int s = 0; s + 1 < p->n_stages; ++s) {
             HostRing& A = p->out_rings[s];
@@ -827,6 +836,9 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
         return fail(CAMELOT_EINVAL, "data_slots must be a power of two in 64..query_slots");
     if (o.max_wait_ns < 0 || o.idle_exit_ns < 1000000 || o.wait_limit_ns < 1000000)
         return fail(CAMELOT_EINVAL, "max_wait_ns >= 0, idle_exit_ns and wait_limit_ns >= 1 ms required");
+    if (o.qos_ns < 0 || o.qos_margin_ns < 0) return fail(CAMELOT_EINVAL, "qos_ns and qos_margin_ns must be >= 0");
+    for (int b = 0; b < 32; ++b)
+        if (o.batch_latency_ns[b] < 0) return fail(CAMELOT_EINVAL, "batch_latency_ns[%d] < 0", b);
     const int B = alloc->batch;
     if (B < 1 || B > 32) return fail(CAMELOT_EINVAL, "batch %d outside 1..32", B);
     int total = 0;
@@ -998,6 +1010,11 @@ extern "C" camelot_status camelot_pipeline_create(camelot_stage* const* stages, 
     P_TRY(cudaMemset(p->trace, 0, sizeof(TraceDev)));
     hp.trace = p->trace;
     hp.max_wait_ns = o.max_wait_ns;
+    for (int b = 0; b < 32; ++b) {
+        long long w = o.max_wait_ns;
+        if (o.qos_ns > 0) w = std::min(w, std::max(0ll, (long long)(o.qos_ns - o.qos_margin_ns - o.batch_latency_ns[b])));
+        hp.trig_wait_ns[b] = w;
+    }
     hp.idle_ns = o.idle_exit_ns;
     hp.limit_ns = o.wait_limit_ns;
     hp.exit_after_trace = o.exit_after_trace ? 1 : 0;
@@ -1170,6 +1187,13 @@ extern "C" camelot_status camelot_poll(camelot_pipeline* p, camelot_completion* 
         if (++spins < 4000) _mm_pause();
         else std::this_thread::yield();
     }
+}
+
+extern "C" camelot_status camelot_pipeline_stall_relay(camelot_pipeline* p, int stall) {
+    if (!p) return fail(CAMELOT_EINVAL, "null pipeline");
+    if (p->mode != CAMELOT_HANDOFF_HOST_STAGED) return fail(CAMELOT_EINVAL, "not a host-staged pipeline");
+    p->relay_hold.store(stall != 0);
+    return CAMELOT_OK;
 }
 
 extern "C" camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out) {
