@@ -42,6 +42,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (sp.kind == KIND_NORM_POOL2_BF16) pool_setup(reinterpret_cast<float*>(smem4));
     else if (sp.kind == KIND_STREAM_SYNTH) stream_setup(reinterpret_cast<float*>(smem4));
     stage_body<kAllKinds & ~(kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8))>(cx, sp, in, n, out, fo);
+
+    // The caller holds no handle on the error word in the static array, so a
+    // failed call marks its outputs instead: the last CTA to finish (the
+    // others have fenced their writes before counting themselves out) looks
+    // at the error word and, if a wait gave up, overwrites every output with
+    // the failure pattern (indices -1; every other output byte 0xFF, which is
+    // NaN in f32, bf16 and e4m3).
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl->exited[0].v, 1ull) == (unsigned long long)(gridDim.x - 1);
+        __threadfence();
+    }
+    __syncthreads();
+    if (!s_last || !has_error(ctl)) return;
+    if (sp.top_k > 0) {
+        const size_t k = (size_t)n * (size_t)sp.res_k;
+        for (size_t i = threadIdx.x; i < k; i += blockDim.x) {
+            idx[i] = -1;
+            val[i] = __int_as_float(-1);
+        }
+        if (logits.base != nullptr)
+            for (size_t i = threadIdx.x; i < (size_t)n * logits.stride; i += blockDim.x) logits.base[i] = (char)0xFF;
+    } else {
+        for (size_t i = threadIdx.x; i < (size_t)n * out.stride; i += blockDim.x) out.base[i] = (char)0xFF;
+    }
 }
 
 }  // namespace camelot
