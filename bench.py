@@ -55,7 +55,12 @@ WORKLOADS = {
         batch=16, row=12288, even=([1, 1], [72, 72]), profile_alloc=([1, 16], [16, 8]),
         flop=2 * (12288 * 512 + 512 * 256 + 256 * 10),
         # algorithmic HBM bytes per query: u8 in, f32 handoff written + read
-        bytes=12288 + 2 * 12288 * 4, weight_bytes=4 * (12288 * 512 + 512 * 256 + 256 * 10)),
+        bytes=12288 + 2 * 12288 * 4, weight_bytes=4 * (12288 * 512 + 512 * 256 + 256 * 10),
+        stage_costs=[dict(name="normalize u8 -> f32", weight_bytes=0, io_bytes=12288 + 12288 * 4, flop=0,
+                          bound="hbm"),
+                     dict(name="MLP 12288-512-256-10 fp32 + argmax",
+                          weight_bytes=4 * (12288 * 512 + 512 * 256 + 256 * 10), io_bytes=12288 * 4 + 8,
+                          flop=2 * (12288 * 512 + 512 * 256 + 256 * 10), bound="ffma")]),
     "bf16-3stage": dict(
         desc=("3-stage pipeline: 224x224x3 u8 images -> 2x2 pool + normalize (bf16) -> GEMM "
               "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
@@ -64,7 +69,13 @@ WORKLOADS = {
         profile_alloc=([3, 11, 4], [8, 8, 8]),
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
-        weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024)),
+        weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024),
+        stage_costs=[dict(name="2x2 pool + normalize -> bf16", weight_bytes=0, io_bytes=150528 + 37632 * 2, flop=0,
+                          bound="hbm"),
+                     dict(name="GEMM 37632-1024-1024 GELU (tcgen05 bf16)", weight_bytes=2 * (37632 * 1024 + 1024 * 1024),
+                          io_bytes=37632 * 2 + 1024 * 2, flop=2 * (37632 * 1024 + 1024 * 1024), bound="hbm"),
+                     dict(name="GEMM 1024-1000 + top-5 (tcgen05 bf16)", weight_bytes=2 * 1024 * 1000,
+                          io_bytes=1024 * 2 + 40, flop=2 * 1024 * 1000, bound="hbm")]),
     "text-2stage": dict(
         desc=("text tagging: int32 token queries (Zipf s=1.1 over 32000, length 16..128, padded to 128) -> "
               "embedding gather 32000x512 bf16 -> token-level GEMMs 512-2048 GELU-512-64 (bf16, tcgen05) -> "
@@ -107,6 +118,42 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def stage_roofline(name, levels, dur, inst, quota, sm_count, sm_mhz):
+    """Each stage's achieved fraction of its roofline at the allocated quota,
+    from the solo profile (one batch of B on p SMs, CUDA events): algorithmic
+    bytes (weights once per batch + input and output rows per query) per
+    second against the measured HBM copy bandwidth, both of the whole GPU and
+    of the stage's share of the SMs (p / SM count); FLOPs per second against
+    the bf16 tensor peak (tensor stages) or the FP32 FFMA peak p x 128 x 2 x
+    clock (FP32 stages)."""
+    w = WORKLOADS[name]
+    B = w["batch"]
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    out = []
+    for si, c in enumerate(w.get("stage_costs", [])):
+        p = quota[si]
+        d = float(dur[si][levels.index(p)])
+        byts = c["weight_bytes"] + B * c["io_bytes"]
+        gbs = byts / d / 1e9
+        r = {"stage": c["name"], "sm_quota": p, "instances": inst[si], "batch": B, "batch_ms": d * 1e3,
+             "algorithmic_bytes_per_batch": byts, "achieved_gbs": gbs, "hbm_frac": gbs / hbm,
+             "hbm_frac_of_sm_share": gbs / (hbm * p / sm_count), "bound": c["bound"]}
+        if c["flop"]:
+            tf = B * c["flop"] / d / 1e12
+            r["achieved_tflops"] = tf
+            if c["bound"] == "ffma":
+                pk = p * 128 * 2 * sm_mhz * 1e6 / 1e12
+                r["ffma_peak_tflops"] = pk
+                r["ffma_frac"] = tf / pk
+            else:
+                pk = peaks.get("bf16_tflops", 1800.0) * p / sm_count
+                r["tensor_peak_tflops_sm_share"] = pk
+                r["tensor_frac_of_sm_share"] = tf / pk
+        out.append(r)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -644,16 +691,58 @@ def measure_workload(name, args, local, headline: bool):
                                     "peak_rate": lam, "saturation_qps": sat["qps"],
                                     "value": (t or {}).get("qps", 0.0), "p99_ms": (t or {}).get("p99_ms")}
         out["main_alloc"] = {"instances": main_alloc[0], "sm_quota": main_alloc[1]}
+        sm_mhz = _peaks().get("sm_max_mhz", 2032.0)
+        out["stage_roofline"] = {
+            tag: stage_roofline(name, levels, dur, a[0], a[1], wl.sms, sm_mhz)
+            for tag, a in (("main_alloc", main_alloc), ("other_alloc", other_alloc))
+            if all(q in levels for q in a[1])}
         out["global"] = res[("main", 0)]
         out["host_staged"] = res[("main", 1)]
         out["other_alloc_global"] = res[("other", 0)]
         out["other_alloc_host_staged"] = res[("other", 1)]
         g, h = out["global"]["value"], out["host_staged"]["value"]
         out["global_over_host_staged"] = g / h if h else None
+        if headline:
+            out["load_curve"], out["batch_sweep"] = load_and_batch_sweep(wl, main_alloc, res)
     except Exception:
         wl.close()
         raise
     return out, timed, wl
+
+
+def load_and_batch_sweep(wl, alloc, res, fracs=(0.1, 0.25, 0.5, 0.75, 1.0), batches=(1, 2, 4, 8, 16, 32)):
+    """Latency against load and batch size on the allocated split, both
+    handoffs (Sec. 8.1-8.3 load levels): p50 / p99 of one Poisson trace at
+    each fraction of that handoff's measured peak; and, per batch size, the
+    saturated rate and the p50 / p99 at half of it."""
+    import synth
+    inst, quota = alloc
+    curve, sweep = [], []
+    for mode in (0, 1):
+        lam_pk = res[("main", mode)]["peak_rate"]
+        if not lam_pk:
+            continue
+        p = wl.pipeline(mode, inst, quota)
+        try:
+            for i, f in enumerate(fracs):
+                comps, ms = wl.trace(p, synth.poisson_arrivals_ns(700 + i, Q_STEP, f * lam_pk))
+                p99, p50 = wl.p99(comps)
+                curve.append({"handoff": ("global", "host_staged")[mode], "load_frac": f, "offered_qps": f * lam_pk,
+                              "p50_ms": p50 * 1e-6, "p99_ms": p99 * 1e-6})
+        finally:
+            wl.cm.camelot_pipeline_destroy(p)
+        for b in batches:
+            p = wl.pipeline(mode, inst, quota, batch=b)
+            try:
+                _, ms = wl.trace(p, np.zeros(Q_STEP, np.int64))
+                sat = Q_STEP / (ms * 1e-3)
+                comps, _ = wl.trace(p, synth.poisson_arrivals_ns(800 + b, Q_STEP, 0.5 * sat))
+                p99, p50 = wl.p99(comps)
+                sweep.append({"handoff": ("global", "host_staged")[mode], "batch": b, "saturation_qps": sat,
+                              "half_load_p50_ms": p50 * 1e-6, "half_load_p99_ms": p99 * 1e-6})
+            finally:
+                wl.cm.camelot_pipeline_destroy(p)
+    return curve, sweep
 
 
 def run_gpu(args, rank: int, world: int, dist):
@@ -688,9 +777,10 @@ def run_gpu(args, rank: int, world: int, dist):
     w = WORKLOADS[HEADLINE]
     sat_qps = Q_STEP / (sat_ms * 1e-3)
     # dominant kernel: the persistent pipeline kernel; per query it moves the
-    # image, the bf16 handoffs and 1/B of the weights (read once per batch)
+    # image, the bf16 handoffs and 1/B of the weights (read once per batch);
+    # achieved over the timed region (launch durations at the headline's rate)
     bytes_q = w["bytes"] + w["weight_bytes"] / w["batch"]
-    achieved = bytes_q * sat_qps / 1e9
+    achieved = bytes_q * (Q_STEP / (t["ms_per_step"] * 1e-3)) / 1e9
     hbm = peaks.get("hbm_gbs", 6400.0)
     value = world * Q_STEP / (ms_step * 1e-3)
     tpq = _measured_traffic_per_query()
@@ -714,9 +804,11 @@ def run_gpu(args, rank: int, world: int, dist):
                      "frac": achieved / hbm, "traffic": tpq * Q_STEP if tpq else None,
                      "kernel": "pipeline_kernel",
                      "basis": (f"{bytes_q:.0f} algorithmic bytes/query (image, bf16 handoffs, "
-                               f"weights/{w['batch']}) x saturated {sat_qps:.0f} queries/s; peak = "
+                               f"weights/{w['batch']}) x the queries of one timed launch / its CUDA-event "
+                               f"duration (saturated launch: {sat_qps:.0f} queries/s); peak = "
                                "measured HBM copy bandwidth; traffic = ncu DRAM bytes per query of a "
-                               "2,000-query capture x the queries of one launch")},
+                               "2,000-query capture x the queries of one launch"),
+                     "stages": head.get("stage_roofline", {}).get("main_alloc", [])},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": e2e["qps"], "unit": UNIT, "p99_ms": e2e["p99_ms"],
@@ -787,10 +879,11 @@ def run_predictor(args):
             cm.camelot_stage_release(s)
     pred = r.pop("_predictor")
     data, solo = r.pop("_data"), r.pop("_solo")
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    pred.save(os.path.join(ROOT, "gpurun_out", "predictor_cfg1.npz"))
-    np.savez(os.path.join(ROOT, "gpurun_out", "predictor_samples.npz"), solo_p99_us=solo,
-             **{k: np.asarray(v) for k, v in data.items()})
+    if args.out:
+        os.makedirs(args.out, exist_ok=True)
+        pred.save(os.path.join(args.out, "predictor_cfg1.npz"))
+        np.savez(os.path.join(args.out, "predictor_samples.npz"), solo_p99_us=solo,
+                 **{k: np.asarray(v) for k, v in data.items()})
     pred.close()
     X = prm.feature_rows(costs, data["stage"], data["batch"], data["sms"], data["corunner_sms"],
                          data["corunner_gbs"]).astype(np.float64)
@@ -1417,6 +1510,35 @@ def run_profile_case(args):
     return 0
 
 
+def run_stage_case(args):
+    """Small self-contained case for ncu: one stage of a workload run alone by
+    direct launches (camelot_stage_launch) on --ctas SMs over one batch of
+    --batch queries (default: the workload's batch), three times."""
+    wl = Workload(args.workload, 0, n_rows=256)
+    torch, cm = wl.torch, wl.cm
+    si = args.stage
+    B = args.batch or wl.B
+    st = wl.stages[si]
+    ins = [wl.xq] + [torch.zeros(B * nb, dtype=torch.uint8, device="cuda") for (nb, _) in wl.io[1:]]
+    last = si == len(wl.stages) - 1
+    out = None if last else torch.zeros(B * wl.io[si + 1][0], dtype=torch.uint8, device="cuda")
+    idx = torch.empty((B, 5), dtype=torch.int32, device="cuda")
+    val = torch.empty((B, 5), dtype=torch.float32, device="cuda")
+    _, _, sb = cm.camelot_stage_info(st, B)
+    scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for i in range(3):
+        ev[i].record()
+        cm.camelot_stage_launch(st, args.ctas, ins[si], B, out, idx if last else None, val if last else None,
+                                None, scr, sb, None)
+    ev[3].record()
+    torch.cuda.synchronize()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(3)]
+    wl.close()
+    print(json.dumps({"stage_case": args.workload, "stage": si, "ctas": args.ctas, "batch": B, "launch_ms": ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1425,10 +1547,17 @@ def main():
     ap.add_argument("--impl", default="camelot", choices=["camelot", "reference"])
     ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--stage-case", action="store_true",
+                    help="ncu case: direct launches of one stage (--stage, --ctas, --batch) of --workload")
+    ap.add_argument("--stage", type=int, default=1)
+    ap.add_argument("--ctas", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--predictor", action="store_true",
                     help="run the latency-predictor study (profiling, GPU training, allocation) instead")
     ap.add_argument("--pred-samples", type=int, default=20000)
     ap.add_argument("--pred-runs", type=int, default=100)
+    ap.add_argument("--out", default="",
+                    help="--predictor: folder for the trained parameters and the profiling samples (none if empty)")
     ap.add_argument("--serving", action="store_true", help="run the four-pipeline serving study instead")
     ap.add_argument("--ipc", action="store_true", help="run the cross-process handoff study instead")
     ap.add_argument("--artifact", action="store_true",
@@ -1442,6 +1571,8 @@ def main():
         return run_reference(args, rank)
     if args.profile_case:
         return run_profile_case(args)
+    if args.stage_case:
+        return run_stage_case(args)
     if args.predictor:
         return run_predictor(args)
     if args.diurnal > 0:

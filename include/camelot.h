@@ -30,7 +30,9 @@
  *   - A pipeline is driven by one submitting thread and one polling thread at
  *     most (they may be the same thread).
  *   - The library prints nothing; it allocates device memory only inside
- *     camelot_stage_prepare and camelot_pipeline_create.
+ *     camelot_stage_prepare, camelot_pipeline_create, camelot_predictor_create,
+ *     camelot_corunner_start, camelot_xring_create / open, camelot_server_create
+ *     and camelot_fp8_scale (a 4-byte result word).
  */
 #ifndef CAMELOT_H_
 #define CAMELOT_H_
@@ -175,6 +177,14 @@ camelot_status camelot_stage_release(camelot_stage* st);
 camelot_status camelot_stage_export_weights(const camelot_stage* st, int layer, void* out, size_t bytes,
                                             float* weight_scale);
 
+/* Static activation scale of an FP8 layer input (the calibration of the FP8
+ * arm): *scale = f32(max |x| / 448) over the n f32 values at x (device),
+ * computed by a reduction kernel on `stream` (NULL = legacy default stream);
+ * the call waits for it.  448 is the largest finite E4M3 magnitude, so the
+ * calibration values map onto the code range.  Errors: EINVAL (null pointer,
+ * n = 0, a maximum that is zero or infinite), ENOMEM, ECUDA. */
+camelot_status camelot_fp8_scale(const float* x, size_t n, void* stream, float* scale);
+
 /* Row sizes in bytes of one query's input and output for the stage (output
  * bytes are 0 for a final stage), and the device scratch bytes a direct launch
  * of `n` rows needs. */
@@ -317,6 +327,58 @@ camelot_status camelot_predictor_train_step(camelot_predictor* p, const float* X
                                             const uint32_t* idx, uint32_t n, float lr, float* loss,
                                             void* stream);
 camelot_status camelot_predictor_destroy(camelot_predictor* p);
+
+/* Algorithmic work of one stage, the inputs of the predictor's features and
+ * of the allocator's bandwidth and memory terms (Table 2: C(i,s) FLOPs, M the
+ * memory footprint). */
+typedef struct {
+    int32_t stage_id;        /* the stage's identity as the predictor's first feature */
+    int32_t pad_;
+    double flop_per_query;   /* FLOPs of one query                                   */
+    double bytes_per_batch;  /* bytes read once per batch (the weights)              */
+    double bytes_per_query;  /* bytes read and written per query (input + output row) */
+    double mem_bytes;        /* device memory of one instance (Constraint-4's M)      */
+} camelot_stage_cost;
+
+/* Raw predictor features of n configurations (host, float [n][12], the order
+ * the predictor is trained on): for stage costs[s], s = stage[r] (an index
+ * into costs), batch b = batch[r], quota p = sms[r] SMs, a co-runner on c =
+ * co_sms[r] SMs (0 = none) streaming g = co_gbs[r] GB/s when alone:
+ *   [id, b, p, F, Y, F / Y, c, c > 0 ? g : 0, c > 0, p + c, log2 b, 1 / p]
+ * with id = costs[s].stage_id,
+ * F = b flop_per_query and Y = bytes_per_batch + b bytes_per_query.  The
+ * paper's features are the batch size and the SM share from solo runs (Sec.
+ * 7.1); the work and co-runner terms let the model see contention (Sec. 4.2).
+ * Host-only.  Errors: EINVAL (null pointer, stage index, b < 1, p < 1). */
+camelot_status camelot_predictor_features(const camelot_stage_cost* costs, int n_stages, uint32_t n,
+                                          const int32_t* stage, const int32_t* batch, const int32_t* sms,
+                                          const int32_t* co_sms, const double* co_gbs, float* X);
+
+/* The allocator's table (Table 2 quantities) from batch latencies: for
+ * lat_s[b][i][l] (host, [n_batches][n_stages][n_levels], seconds, > 0) the
+ * duration d = lat_s, the throughput of one instance f = B_b / d, its
+ * bandwidth demand (bytes_per_batch + B_b bytes_per_query) / d / 1e9 GB/s, and
+ * mem[b][i] = costs[i].mem_bytes; outputs are host arrays of the same shapes,
+ * laid out as camelot_profile expects.  Host-only.  Errors: EINVAL. */
+camelot_status camelot_profile_from_latency(const camelot_stage_cost* costs, int n_stages,
+                                            const int32_t* batch_sizes, int n_batches, int n_levels,
+                                            const double* lat_s, double* thr, double* bw, double* dur,
+                                            double* mem);
+
+/* The performance model inside the allocator (Sec. 7.1-7.2): fills the
+ * camelot_profile arrays thr, bw, dur ([n_batches][n_stages][n_levels]) and
+ * mem ([n_batches][n_stages]) from the predictor's latency estimate for every
+ * batch size, stage and quota level (level l = (l + 1) unit SMs), beside a
+ * co-runner on co_sms SMs streaming co_gbs GB/s alone (0 = none).  The network
+ * predicts log of the latency in microseconds.  Builds the features as
+ * camelot_predictor_features does, runs the forward kernel on the rows in one
+ * launch (in the predictor's own scratch, at most 65536 rows) and converts as
+ * camelot_profile_from_latency does.  Synchronous (legacy default stream);
+ * must not overlap other calls on the same predictor.  Errors: EINVAL, ECUDA. */
+camelot_status camelot_profile_predict(camelot_predictor* p, const camelot_stage_cost* costs, int n_stages,
+                                       const int32_t* batch_sizes, int n_batches, int unit, int n_levels,
+                                       int32_t co_sms, double co_gbs, double* thr, double* bw, double* dur,
+                                       double* mem);
 
 /* ----------------------------------------------------------- pipelines */
 typedef enum {

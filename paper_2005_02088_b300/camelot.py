@@ -53,6 +53,11 @@ class Options(C.Structure):
                 ("qos_margin_ns", C.c_int64), ("batch_latency_ns", C.c_int64 * 32)]
 
 
+class StageCost(C.Structure):
+    _fields_ = [("stage_id", C.c_int32), ("pad_", C.c_int32), ("flop_per_query", C.c_double), ("bytes_per_batch", C.c_double),
+                ("bytes_per_query", C.c_double), ("mem_bytes", C.c_double)]
+
+
 class Completion(C.Structure):
     _fields_ = [("query_id", C.c_uint64), ("stream_id", C.c_uint32), ("status", C.c_int32),
                 ("idx", C.c_int32 * MAX_TOPK), ("val", C.c_float * MAX_TOPK),
@@ -127,6 +132,11 @@ _SIGS = {
     "camelot_predictor_grad": (C.c_int, [P, P, P, P, C.c_uint32, P, P, P]),
     "camelot_predictor_train_step": (C.c_int, [P, P, P, P, C.c_uint32, C.c_float, P, P]),
     "camelot_predictor_destroy": (C.c_int, [P]),
+    "camelot_predictor_features": (C.c_int, [P, C.c_int, C.c_uint32, P, P, P, P, P, P]),
+    "camelot_profile_from_latency": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P]),
+    "camelot_profile_predict": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_int, C.c_int, C.c_int32, C.c_double,
+                                          P, P, P, P]),
+    "camelot_fp8_scale": (C.c_int, [P, C.c_size_t, P, P]),
     "camelot_options_default": (None, [P]),
     "camelot_pipeline_create": (C.c_int, [P, C.c_int, P, C.c_int, P, P]),
     "camelot_submit": (C.c_int, [P, C.c_uint32, P, C.c_uint32, P, P]),
@@ -319,6 +329,64 @@ def camelot_predictor_train_step(p: int, X, t, idx, n: int, lr: float, loss=None
 
 def camelot_predictor_destroy(p: int) -> None:
     _check(load().camelot_predictor_destroy(p))
+
+
+def _costs(costs):
+    arr = (StageCost * len(costs))()
+    for i, c in enumerate(costs):
+        arr[i] = StageCost(int(c[0]), 0, float(c[1]), float(c[2]), float(c[3]), float(c[4]))
+    return arr
+
+
+def camelot_predictor_features(costs, stage, batch, sms, co_sms, co_gbs):
+    """costs: sequence of (stage_id, flop_per_query, bytes_per_batch,
+    bytes_per_query, mem_bytes); `stage` indexes it; the other arguments are
+    arrays of the same length (or scalars).  Returns float32 [n, 12]."""
+    import numpy as np
+    stage = np.ascontiguousarray(stage, np.int32)
+    n = stage.size
+    batch = np.ascontiguousarray(np.broadcast_to(batch, (n,)), np.int32)
+    sms = np.ascontiguousarray(np.broadcast_to(sms, (n,)), np.int32)
+    co_sms = np.ascontiguousarray(np.broadcast_to(co_sms, (n,)), np.int32)
+    co_gbs = np.ascontiguousarray(np.broadcast_to(co_gbs, (n,)), np.float64)
+    X = np.empty((n, PRED_FEATURES), np.float32)
+    _check(load().camelot_predictor_features(_costs(costs), len(costs), n, stage.ctypes.data, batch.ctypes.data,
+                                             sms.ctypes.data, co_sms.ctypes.data, co_gbs.ctypes.data,
+                                             X.ctypes.data))
+    return X
+
+
+def camelot_profile_from_latency(costs, batch_sizes, lat_s):
+    """lat_s [n_batches, n_stages, n_levels] seconds -> (thr, bw, dur, mem) arrays."""
+    import numpy as np
+    lat = np.ascontiguousarray(lat_s, np.float64)
+    nb, n, L = lat.shape
+    bs = np.ascontiguousarray(batch_sizes, np.int32)
+    thr, bw, dur = (np.empty_like(lat) for _ in range(3))
+    mem = np.empty((nb, n), np.float64)
+    _check(load().camelot_profile_from_latency(_costs(costs), n, bs.ctypes.data, nb, L, lat.ctypes.data,
+                                               thr.ctypes.data, bw.ctypes.data, dur.ctypes.data, mem.ctypes.data))
+    return thr, bw, dur, mem
+
+
+def camelot_profile_predict(pred: int, costs, batch_sizes, unit: int, n_levels: int, co_sms: int = 0,
+                            co_gbs: float = 0.0):
+    """Predicted (thr, bw, dur, mem) arrays for every batch size, stage and level."""
+    import numpy as np
+    bs = np.ascontiguousarray(batch_sizes, np.int32)
+    nb, n = bs.size, len(costs)
+    thr, bw, dur = (np.empty((nb, n, n_levels), np.float64) for _ in range(3))
+    mem = np.empty((nb, n), np.float64)
+    _check(load().camelot_profile_predict(pred, _costs(costs), n, bs.ctypes.data, nb, unit, n_levels, co_sms,
+                                          float(co_gbs), thr.ctypes.data, bw.ctypes.data, dur.ctypes.data,
+                                          mem.ctypes.data))
+    return thr, bw, dur, mem
+
+
+def camelot_fp8_scale(x, n: int, stream=None) -> float:
+    s = C.c_float()
+    _check(load().camelot_fp8_scale(_ptr(x), n, _ptr(stream), C.byref(s)))
+    return s.value
 
 
 def camelot_options_default() -> Options:

@@ -18,6 +18,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "../../include/camelot.h"
 
@@ -281,4 +282,101 @@ extern "C" camelot_status camelot_predictor_train_step(camelot_predictor* p, con
                                                        void* stream) {
     if (!(lr > 0.f)) return camelot_internal_fail(CAMELOT_EINVAL, "lr must be positive");
     return grad_step(p, X, t, idx, n, nullptr, loss, true, lr, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// The predictor inside the allocator: features, table conversion, and the
+// predicted camelot_profile (Sec. 7.1-7.2).
+// ---------------------------------------------------------------------------
+static bool cost_ok(const camelot_stage_cost& c) {
+    return c.flop_per_query >= 0.0 && c.bytes_per_batch >= 0.0 && c.bytes_per_query >= 0.0 && c.mem_bytes >= 0.0 &&
+           c.bytes_per_batch + c.bytes_per_query > 0.0;
+}
+
+static void feature_row(const camelot_stage_cost& c, int s, int b, int p, int co, double g, float* x) {
+    const double F = (double)b * c.flop_per_query;
+    const double Y = c.bytes_per_batch + (double)b * c.bytes_per_query;
+    (void)s;
+    const double v[kIn] = {(double)c.stage_id, (double)b, (double)p, F, Y, F / Y, (double)co, co > 0 ? g : 0.0,
+                           co > 0 ? 1.0 : 0.0, (double)(p + co), std::log2((double)b), 1.0 / (double)p};
+    for (int k = 0; k < kIn; ++k) x[k] = (float)v[k];
+}
+
+extern "C" camelot_status camelot_predictor_features(const camelot_stage_cost* costs, int n_stages, uint32_t n,
+                                                     const int32_t* stage, const int32_t* batch, const int32_t* sms,
+                                                     const int32_t* co_sms, const double* co_gbs, float* X) {
+    if (!costs || !stage || !batch || !sms || !co_sms || !co_gbs || !X)
+        return camelot_internal_fail(CAMELOT_EINVAL, "null argument");
+    if (n_stages < 1) return camelot_internal_fail(CAMELOT_EINVAL, "n_stages must be >= 1");
+    for (int i = 0; i < n_stages; ++i)
+        if (!cost_ok(costs[i])) return camelot_internal_fail(CAMELOT_EINVAL, "negative or empty stage cost");
+    for (uint32_t r = 0; r < n; ++r) {
+        if (stage[r] < 0 || stage[r] >= n_stages || batch[r] < 1 || sms[r] < 1 || co_sms[r] < 0)
+            return camelot_internal_fail(CAMELOT_EINVAL, "stage index, batch, SMs or co-runner SMs out of range");
+        feature_row(costs[stage[r]], stage[r], batch[r], sms[r], co_sms[r], co_gbs[r], X + (size_t)r * kIn);
+    }
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_profile_from_latency(const camelot_stage_cost* costs, int n_stages,
+                                                       const int32_t* batch_sizes, int n_batches, int n_levels,
+                                                       const double* lat_s, double* thr, double* bw, double* dur,
+                                                       double* mem) {
+    if (!costs || !batch_sizes || !lat_s || !thr || !bw || !dur || !mem)
+        return camelot_internal_fail(CAMELOT_EINVAL, "null argument");
+    if (n_stages < 1 || n_batches < 1 || n_levels < 1)
+        return camelot_internal_fail(CAMELOT_EINVAL, "empty table");
+    for (int i = 0; i < n_stages; ++i)
+        if (!cost_ok(costs[i])) return camelot_internal_fail(CAMELOT_EINVAL, "negative or empty stage cost");
+    for (int b = 0; b < n_batches; ++b) {
+        if (batch_sizes[b] < 1) return camelot_internal_fail(CAMELOT_EINVAL, "batch size < 1");
+        const double B = (double)batch_sizes[b];
+        for (int i = 0; i < n_stages; ++i) {
+            const double Y = costs[i].bytes_per_batch + B * costs[i].bytes_per_query;
+            mem[(size_t)b * n_stages + i] = costs[i].mem_bytes;
+            for (int l = 0; l < n_levels; ++l) {
+                const size_t k = ((size_t)b * n_stages + i) * n_levels + l;
+                const double d = lat_s[k];
+                if (!(d > 0.0) || !std::isfinite(d))
+                    return camelot_internal_fail(CAMELOT_EINVAL, "latencies must be positive and finite");
+                dur[k] = d;
+                thr[k] = B / d;
+                bw[k] = Y / d / 1e9;
+            }
+        }
+    }
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_profile_predict(camelot_predictor* p, const camelot_stage_cost* costs,
+                                                  int n_stages, const int32_t* batch_sizes, int n_batches, int unit,
+                                                  int n_levels, int32_t co_sms, double co_gbs, double* thr,
+                                                  double* bw, double* dur, double* mem) {
+    if (!p || !costs || !batch_sizes) return camelot_internal_fail(CAMELOT_EINVAL, "null argument");
+    if (n_stages < 1 || n_batches < 1 || n_levels < 1 || unit < 1 || co_sms < 0)
+        return camelot_internal_fail(CAMELOT_EINVAL, "empty table, unit < 1 or co_sms < 0");
+    const size_t rows = (size_t)n_batches * n_stages * n_levels;
+    // X and y live in the predictor's record scratch (kRec x kMaxTrainBatch floats)
+    if (rows > kMaxTrainBatch) return camelot_internal_fail(CAMELOT_EINVAL, "more than 65536 table rows");
+    std::vector<float> X(rows * kIn), y(rows);
+    for (int b = 0; b < n_batches; ++b) {
+        if (batch_sizes[b] < 1) return camelot_internal_fail(CAMELOT_EINVAL, "batch size < 1");
+        for (int i = 0; i < n_stages; ++i) {
+            if (!cost_ok(costs[i])) return camelot_internal_fail(CAMELOT_EINVAL, "negative or empty stage cost");
+            for (int l = 0; l < n_levels; ++l) {
+                const size_t r = ((size_t)b * n_stages + i) * n_levels + l;
+                feature_row(costs[i], i, batch_sizes[b], (l + 1) * unit, co_sms, co_gbs, X.data() + r * kIn);
+            }
+        }
+    }
+    float* dX = p->rec;
+    float* dy = p->rec + rows * kIn;
+    PTRY(cudaMemcpy(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice));
+    camelot_status st = camelot_predictor_forward(p, dX, (uint32_t)rows, dy, nullptr);
+    if (st != CAMELOT_OK) return st;
+    PTRY(cudaMemcpy(y.data(), dy, rows * sizeof(float), cudaMemcpyDeviceToHost));
+    std::vector<double> lat(rows);
+    for (size_t r = 0; r < rows; ++r) lat[r] = std::exp((double)y[r]) * 1e-6;   // log(us) -> s
+    return camelot_profile_from_latency(costs, n_stages, batch_sizes, n_batches, n_levels, lat.data(), thr, bw,
+                                        dur, mem);
 }

@@ -91,3 +91,29 @@ camelot_status camelot_internal_quantize_e4m3(const float* w, int N, int K, int 
     *scale = s;
     return CAMELOT_OK;
 }
+
+extern "C" camelot_status camelot_fp8_scale(const float* x, size_t n, void* stream, float* scale) {
+    if (!x || !scale || n == 0) return camelot_internal_fail(CAMELOT_EINVAL, "null argument or n = 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* d_max = nullptr;
+    if (cudaMalloc(&d_max, sizeof(unsigned int)) != cudaSuccess)
+        return camelot_internal_fail(CAMELOT_ENOMEM, "result word allocation failed");
+    unsigned int bits = 0;
+    camelot_status rc = CAMELOT_OK;
+    if (cudaMemsetAsync(d_max, 0, sizeof(unsigned int), st) != cudaSuccess) rc = CAMELOT_ECUDA;
+    if (rc == CAMELOT_OK) {
+        absmax_kernel<<<592, 256, 0, st>>>(x, n, d_max);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&bits, d_max, sizeof bits, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = CAMELOT_ECUDA;
+    }
+    cudaFree(d_max);
+    if (rc != CAMELOT_OK) return camelot_internal_fail(rc, "activation absmax failed");
+    float amax = 0.f;
+    memcpy(&amax, &bits, sizeof amax);
+    if (!(amax > 0.f) || !std::isfinite(amax))
+        return camelot_internal_fail(CAMELOT_EINVAL, "calibration values must be finite and not all zero");
+    *scale = amax / 448.0f;
+    return CAMELOT_OK;
+}

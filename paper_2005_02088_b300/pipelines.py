@@ -107,7 +107,7 @@ def calibrate_fp8_scales(weights, images_u8: np.ndarray, n_ctas: int = 16) -> li
     """Static activation scales of the FP8 arm for a ReLU MLP behind the u8
     normalisation: max |input of layer l| / 448 (l >= 1) over calibration images,
     with the activations computed by the library's FP32 stages, one layer at a
-    time.  Returns [s_1, ..., s_{L-1}]."""
+    time, and each scale by camelot_fp8_scale.  Returns [s_1, ..., s_{L-1}]."""
     n = images_u8.shape[0]
     H, W, Cc = images_u8.shape[1:4]
     x = torch.from_numpy(np.ascontiguousarray(images_u8.reshape(n, -1))).cuda()
@@ -122,8 +122,7 @@ def calibrate_fp8_scales(weights, images_u8: np.ndarray, n_ctas: int = 16) -> li
             stages.append(st)
             h = torch.empty((n, w.shape[0]), dtype=torch.float32, device="cuda")
             _run_stage(st, y, n, h, n_ctas)
-            torch.cuda.synchronize()
-            scales.append(float(np.float32(np.abs(h.cpu().numpy()).max() / 448.0)))
+            scales.append(cm.camelot_fp8_scale(h, h.numel()))
             y = h
         return scales
     finally:

@@ -7,10 +7,11 @@ trees, and feeds the predictions to the allocator (Sec. 7.2-7.3).  Here one
 MLP (12 -> 64 -> 64 -> 1, FP32) predicts log p99 latency of a stage batch
 from features that also describe a memory-bandwidth co-runner, so contention
 (Sec. 4.2) enters the prediction.  Training and inference run in the
-library's kernels (``camelot_predictor_*``); this module builds feature rows,
+library's kernels (``camelot_predictor_*``), and the library also builds the
+feature rows (``camelot_predictor_features``) and the allocator's table
+(``camelot_profile_from_latency``, ``camelot_profile_predict``); this module
 drives the profiling runs (``camelot_stage_time`` with and without
-``camelot_corunner_*``) and turns predictions into the allocator's table
-(``camelot_profile``).  Host-side work here is bookkeeping only.
+``camelot_corunner_*``) and marshals arrays.
 """
 from __future__ import annotations
 
@@ -49,20 +50,23 @@ def dense_cost(stage_id: int, dims, in_bytes: int, out_bytes: int, weight_bytes:
     return StageCost(stage_id, 2.0 * macs, float(weight_bytes * macs), float(in_bytes + out_bytes))
 
 
+def c_costs(costs: dict, mem_bytes: float = 64e6) -> tuple:
+    """The stages' costs in stage-id order, as camelot_stage_cost tuples."""
+    return tuple((int(k), c.flop_per_query, c.bytes_per_batch, c.bytes_per_query, mem_bytes)
+                 for k, c in sorted(costs.items()))
+
+
 def feature_rows(costs: dict, stage, B, p, co_sms, co_gbs) -> np.ndarray:
     """Raw feature matrix [n, 12] (float32) for arrays of stage ids, batch
-    sizes, SM quotas, co-runner SMs (0 = none) and co-runner solo GB/s."""
+    sizes, SM quotas, co-runner SMs (0 = none) and co-runner solo GB/s, built
+    by camelot_predictor_features."""
+    ids = sorted(costs)
     stage = np.atleast_1d(np.asarray(stage, np.int64))
-    n = stage.size
-    B = np.broadcast_to(np.asarray(B, np.float64), (n,))
-    p = np.broadcast_to(np.asarray(p, np.float64), (n,))
-    c = np.broadcast_to(np.asarray(co_sms, np.float64), (n,))
-    g = np.broadcast_to(np.asarray(co_gbs, np.float64), (n,))
-    flop = np.array([costs[int(s)].flop(b) for s, b in zip(stage, B)])
-    byt = np.array([costs[int(s)].bytes(b) for s, b in zip(stage, B)])
-    X = np.stack([stage.astype(np.float64), B, p, flop, byt, flop / byt, c, np.where(c > 0, g, 0.0),
-                  (c > 0).astype(np.float64), p + c, np.log2(B), 1.0 / p], axis=1)
-    return np.ascontiguousarray(X, np.float32)
+    index = np.searchsorted(np.asarray(ids), stage)
+    assert np.all(np.asarray(ids)[index] == stage), "unknown stage id"
+    return cm.camelot_predictor_features(c_costs(costs), index, np.asarray(B, np.int64),
+                                         np.asarray(p, np.int64), np.asarray(co_sms, np.int64),
+                                         np.asarray(co_gbs, np.float64))
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -277,27 +281,33 @@ def solo_table(runners: dict, stages, batches, levels, runs: int) -> np.ndarray:
 
 def predicted_table(pred: LatencyPredictor, costs: dict, stages, batches, levels,
                     co_sms: int = 0, co_gbs: float = 0.0) -> np.ndarray:
-    """Predicted p99 (us), same shape as ``solo_table``, in one forward launch."""
-    S, Bs, Ls = np.meshgrid(np.asarray(stages), np.asarray(batches), np.asarray(levels), indexing="ij")
-    X = feature_rows(costs, S.ravel(), Bs.ravel(), Ls.ravel(), co_sms, co_gbs)
-    return np.exp(pred.predict(X).astype(np.float64)).reshape(S.shape)
+    """Predicted p99 (us), same shape as ``solo_table`` ([stage][batch][level]),
+    from camelot_profile_predict (one forward launch inside the library).
+    ``levels`` must be unit, 2 unit, ... ."""
+    unit = levels[0]
+    assert list(levels) == [unit * (i + 1) for i in range(len(levels))]
+    ids = sorted(costs)
+    _, _, dur, _ = cm.camelot_profile_predict(pred.h, c_costs(costs), list(batches), unit, len(levels),
+                                              co_sms, co_gbs)
+    # [batch][stage][level] seconds -> [stage][batch][level] us, stages in the order asked
+    d = np.transpose(dur, (1, 0, 2)) * 1e6
+    return d[[ids.index(int(s)) for s in stages]]
 
 
 class AllocTable:
     """The allocator's per-instance table (Table 2 quantities) from p99 batch
-    latencies: f = B / d, bandwidth = bytes(B) / d, duration d."""
+    latencies, converted by camelot_profile_from_latency: f = B / d,
+    bandwidth = bytes(B) / d, duration d."""
 
     def __init__(self, costs: dict, stages, batches, levels, lat_us: np.ndarray, unit: int = 8,
                  mem_bytes: float = 64e6):
         n, nb, L = len(stages), len(batches), len(levels)
-        d = np.transpose(lat_us, (1, 0, 2)) * 1e-6                          # [nb][n][L]
-        Bv = np.asarray(batches, np.float64)[:, None, None]
-        by = np.array([[costs[int(s)].bytes(B) for s in stages] for B in batches])[:, :, None]
+        sub = {int(s): costs[int(s)] for s in stages}
+        assert sorted(sub) == [int(s) for s in stages], "stages in ascending id order"
+        lat_s = np.transpose(np.asarray(lat_us, np.float64), (1, 0, 2)) * 1e-6      # [nb][n][L]
         self.batches = np.ascontiguousarray(batches, np.int32)
-        self.thr = np.ascontiguousarray(Bv / d, np.float64)
-        self.bw = np.ascontiguousarray(by / d / 1e9, np.float64)
-        self.dur = np.ascontiguousarray(d, np.float64)
-        self.mem = np.ascontiguousarray(np.full((nb, n), mem_bytes), np.float64)
+        self.thr, self.bw, self.dur, self.mem = cm.camelot_profile_from_latency(
+            c_costs(sub, mem_bytes), self.batches, lat_s)
         self.levels = list(levels)
         self.prof = cm.Profile(n, L, nb, unit, self.batches.ctypes.data, self.thr.ctypes.data,
                                self.bw.ctypes.data, self.dur.ctypes.data, self.mem.ctypes.data)

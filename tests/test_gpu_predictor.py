@@ -7,6 +7,8 @@ most 65 terms, so |y - y64| <= (13 + 65 + 65) 2^-24 |y|_abs with |y|_abs the
 network evaluated on |theta| and |x|; the test allows 2e-5 |y|_abs.
 Gradient: within 1e-4 of the FP64 gradient's norm.  Adam: the oracle's FP64
 step applied to the GPU's own gradient agrees to 1e-6 relative."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -249,3 +251,60 @@ def test_predictor_study_small():
     # apart), which measures ~9 % below the brute-force choice on this GPU
     assert r["allocation"]["max_peak"]["ratio_to_brute_force"] >= 0.90, r["allocation"]["max_peak"]
     assert r["inference"]["seconds"] < 0.05
+
+
+def test_allocation_from_predictor_through_the_c_abi(tmp_path):
+    """camelot_profile_predict (features, forward kernel and Table 2 inside the
+    library) gives the same table as the separate calls, the features equal
+    their definition recomputed here, Eq. 1 picks the same allocation from
+    either, and a C program linked only against libcamelot.so allocates from
+    the predictor with the same result."""
+    import subprocess
+    from paper_2005_02088_b300 import build, camelot as cm, predictor as pr
+    costs = {1: pr.StageCost(1, 2 * 12288, 0.0, 12288 + 49152),
+             2: pr.dense_cost(2, [12288, 512, 256, 10], 49152, 8)}
+    params = pr.init_params(3)
+    batches, levels = [8, 16, 32, 64], list(range(8, 145, 8))
+    S, Bs, Ls = np.meshgrid([1, 2], batches, levels, indexing="ij")
+    X = pr.feature_rows(costs, S.ravel(), Bs.ravel(), Ls.ravel(), 0, 0.0)
+    # untrained weights on z-scored features: outputs of order one (log us)
+    mean = X.mean(axis=0).astype(np.float32)
+    sd = X.std(axis=0)
+    inv = np.where(sd > 0, 1.0 / np.maximum(sd, 1e-30), 1.0).astype(np.float32)
+    pred = pr.LatencyPredictor(params)
+    pred.set_norm(mean, inv)
+    try:
+        thr, bw, dur, mem = cm.camelot_profile_predict(pred.h, pr.c_costs(costs), batches, 8, len(levels))
+        # the same through features -> forward -> from_latency
+        flop = np.array([costs[s].flop(b) for s, b in zip(S.ravel(), Bs.ravel())])
+        byt = np.array([costs[s].bytes(b) for s, b in zip(S.ravel(), Bs.ravel())])
+        ref = np.stack([S.ravel(), Bs.ravel(), Ls.ravel(), flop, byt, flop / byt, 0 * flop, 0 * flop, 0 * flop,
+                        Ls.ravel(), np.log2(Bs.ravel()), 1.0 / Ls.ravel()], axis=1).astype(np.float32)
+        assert np.array_equal(X, ref)
+        lat_us = np.exp(pred.predict(X).astype(np.float64)).reshape(S.shape)
+        t = pr.AllocTable(costs, [1, 2], batches, levels, lat_us)
+        assert np.allclose(t.dur, dur, rtol=1e-12, atol=0) and np.allclose(t.thr, thr, rtol=1e-12, atol=0)
+        assert np.allclose(t.bw, bw, rtol=1e-12, atol=0)
+        a_py, o_py = pr.allocate(t, 144, 6500.0, 20e-3)
+        prof = cm.Profile(2, len(levels), 4, 8, t.batches.ctypes.data, thr.ctypes.data, bw.ctypes.data,
+                          dur.ctypes.data, mem.ctypes.data)
+        cons = cm.Constraints(144, 18, 6500.0, 1e12, 20e-3, 0.0, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
+        a_c, o_c = cm.camelot_allocate(prof, cm.POLICY_MAX_PEAK, cons)
+        assert (list(a_py.instances[:2]), list(a_py.sm_quota[:2]), a_py.batch) == \
+               (list(a_c.instances[:2]), list(a_c.sm_quota[:2]), a_c.batch)
+        assert o_c == pytest.approx(o_py, rel=1e-12)
+    finally:
+        pred.close()
+    # a C-only caller
+    (tmp_path / "params.f32").write_bytes(params.astype(np.float32).tobytes())
+    (tmp_path / "norm.f32").write_bytes(np.concatenate([mean, inv]).astype(np.float32).tobytes())
+    exe = tmp_path / "alloc_from_predictor"
+    src = os.path.join(os.path.dirname(__file__), "c", "alloc_from_predictor.c")
+    libdir = os.path.dirname(build.LIB)
+    subprocess.run(["gcc", "-O2", "-I", os.path.join(os.path.dirname(libdir), "include"), src, "-o", str(exe),
+                    "-L", libdir, "-lcamelot", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe), str(tmp_path / "params.f32"), str(tmp_path / "norm.f32"), "144"],
+                         check=True, capture_output=True, text=True).stdout.split()
+    assert out[0] == "instances" and [int(v) for v in out[1:3]] == list(a_py.instances[:2])
+    assert [int(v) for v in out[4:6]] == list(a_py.sm_quota[:2]) and int(out[7]) == a_py.batch
+    assert float(out[9]) == pytest.approx(o_py, rel=1e-12)

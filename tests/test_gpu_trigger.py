@@ -99,31 +99,6 @@ def test_qos_trigger_matches_simulator(orc):
     assert np.sum(bs < B) >= 9 and lag_sim.max() < 3.5 * MS
 
 
-def test_trigger_latency_from_profile():
-    # host-only helper: the latency table the QoS rule reads, from a profile
-    import ctypes as C
-    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
-    bsz = np.array([8, 16, 32], np.int32)
-    n, L = 2, 4
-    dur = np.zeros((3, n, L))
-    for j, b in enumerate(bsz):
-        for i in range(n):
-            for l in range(L):
-                dur[j, i, l] = (i + 1) * 1e-4 * b / (l + 1)
-    z = np.zeros((3, n, L))
-    mem = np.zeros((3, n))
-    prof = cm.Profile(n, L, 3, 8, bsz.ctypes.data, z.ctypes.data, z.ctypes.data, dur.ctypes.data,
-                      mem.ctypes.data)
-    a = pl.alloc([2, 1], [16, 32], 16)
-    lat = cm.camelot_trigger_latency(prof, a)
-    # stage 0 at level 1 (16 SMs), stage 1 at level 3 (32 SMs): b 1e-4 / 2 + 2 b 1e-4 / 4 = b 1e-4 s
-    for b in range(1, 33):
-        ref = (8 if b < 8 else b) * 1e-4
-        assert lat[b - 1] == round(ref * 1e9), (b, lat[b - 1], ref)
-    with pytest.raises(cm.CamelotError):
-        cm.camelot_trigger_latency(prof, pl.alloc([1, 1], [12, 8], 16))   # 12 SMs: not a level
-
-
 def test_device_wait_times_out_on_stalled_relay(orc):
     from paper_2005_02088_b300 import camelot as cm, pipelines as pl
     x, ws = cfg1_data(256)
