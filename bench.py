@@ -590,25 +590,68 @@ class Workload:
         best = max(table, key=lambda r: r["saturation_qps"])
         return best["instances"], best["sm_quota"], table
 
-    def allocate(self, levels, dur, qos_s=QOS_NS * 1e-9):
+    def costs(self):
+        """camelot_stage_cost tuples of the stages: algorithmic FLOPs and bytes
+        (weights once per batch, input and output rows per query), 64 MB each."""
+        out = []
+        for si in range(len(self.stages)):
+            c = self.w.get("stage_costs")
+            if c:
+                out.append((si, float(c[si]["flop"]), float(c[si]["weight_bytes"]), float(c[si]["io_bytes"]), 64e6))
+            else:
+                inb = self.io[si][0]
+                outb = self.io[si + 1][0] if si + 1 < len(self.io) else 40
+                out.append((si, 0.0, 0.0, float(inb + outb), 64e6))
+        return out
+
+    def table(self, levels, batches, dur, handover=None):
+        """camelot_profile (Table 2 quantities by camelot_profile_from_latency)
+        from durations dur [n_batches][n_stages][n_levels] (s); with `handover`
+        (s per stage) the per-batch hand-over time is added to every entry."""
         cm = self.cm
-        n, L, B = len(self.stages), len(levels), self.B
-        f = np.ascontiguousarray((B / dur)[None], np.float64)
-        stage_bytes = []
-        for si in range(n):
-            inb = self.io[si][0]
-            outb = self.io[si + 1][0] if si + 1 < len(self.io) else 40
-            stage_bytes.append(B * (inb + outb))
-        bw = np.ascontiguousarray((np.array(stage_bytes)[:, None] / dur / 1e9)[None], np.float64)
-        d = np.ascontiguousarray(dur[None], np.float64)
-        mem = np.ascontiguousarray(np.full((1, n), 64e6), np.float64)
-        bs = np.array([B], np.int32)
-        pr = cm.Profile(n, L, 1, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, d.ctypes.data,
+        bs = np.ascontiguousarray(batches, np.int32)
+        thr, bw, d, mem = cm.camelot_profile_from_latency(self.costs(), bs, np.asarray(dur, np.float64))
+        n, L = d.shape[1], d.shape[2]
+        pr = cm.Profile(n, L, len(bs), 8, bs.ctypes.data, thr.ctypes.data, bw.ctypes.data, d.ctypes.data,
                         mem.ctypes.data)
+        if handover is not None:
+            cm.camelot_profile_add_handover(pr, handover, thr, bw, d)
+        return pr, (bs, thr, bw, d, mem)
+
+    def allocate(self, levels, dur, qos_s=QOS_NS * 1e-9, handover=None):
+        """Eq. 1 on the solo profile at batch B (dur [n_stages][n_levels]),
+        optionally with the measured per-batch hand-over time added."""
+        cm = self.cm
+        n = len(self.stages)
+        pr, keep = self.table(levels, [self.B], np.asarray(dur, np.float64)[None], handover)
         cons = cm.Constraints(self.sms, self.sms // 8, _peaks().get("hbm_gbs", 6400.0), 200e9, qos_s,
                               0.0, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
         a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
         return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)], obj
+
+    def handover(self, inst, quota, dur_at, batch=0):
+        """Per-batch hand-over time of every stage inside the pipeline (s): one
+        saturated trace on the allocation; the in-pipeline service time per
+        batch (camelot_stats.busy_ns / batches) minus the stage's solo duration
+        at its quota (negative where the solo time's launch overhead exceeds
+        the hand-over).  Returns (hand-over s, in-pipeline s, saturation q/s)."""
+        cm = self.cm
+        n = len(self.stages)
+        p = self.pipeline(0, inst, quota, batch=batch)
+        try:
+            s0 = cm.camelot_pipeline_stats(p)
+            _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
+            s1 = cm.camelot_pipeline_stats(p)
+        finally:
+            cm.camelot_pipeline_destroy(p)
+        t_in = [(s1.busy_ns[i] - s0.busy_ns[i]) / max(1, s1.batches[i] - s0.batches[i]) * 1e-9 for i in range(n)]
+        return [t_in[i] - dur_at[i] for i in range(n)], t_in, Q_STEP / (ms * 1e-3)
+
+    def simulated(self, levels, dur, inst, quota, handover, rate):
+        """The library's pipeline simulator on the (hand-over) profile: (p50 s, p99 s, q/s)."""
+        pr, keep = self.table(levels, [self.B], np.asarray(dur, np.float64)[None])
+        return self.cm.camelot_simulate_profile(pr, self.pl.alloc(inst, quota, self.B), handover, 200e-6, rate,
+                                                n_queries=20000, seed=11)
 
 
     def profile_batches(self, batches, runs=20):
@@ -638,22 +681,9 @@ class Workload:
                     dur[bi, si, li] = float(np.percentile(ms, 99)) * 1e-3
         return levels, dur
 
-    def alloc_table(self, levels, batches, dur):
-        """camelot_profile of Table 2 quantities from a duration table."""
-        cm = self.cm
-        n, L, nb = len(self.stages), len(levels), len(batches)
-        Bv = np.array(batches, np.float64)[:, None, None]
-        f = np.ascontiguousarray(Bv / dur, np.float64)
-        by = np.array([[B * (self.io[si][0] + (self.io[si + 1][0] if si + 1 < len(self.io) else 40))
-                        for si in range(n)] for B in batches], np.float64)[:, :, None]
-        bw = np.ascontiguousarray(by / dur / 1e9, np.float64)
-        d = np.ascontiguousarray(dur, np.float64)
-        mem = np.ascontiguousarray(np.full((nb, n), 64e6), np.float64)
-        bs = np.array(batches, np.int32)
-        keep = (f, bw, d, mem, bs)
-        pr = cm.Profile(n, L, nb, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, d.ctypes.data,
-                        mem.ctypes.data)
-        return pr, keep
+    def alloc_table(self, levels, batches, dur, handover=None):
+        """camelot_profile of Table 2 quantities from a duration table (library conversion)."""
+        return self.table(levels, batches, dur, handover)
 
     def solve(self, pr, policy, load=0.0, qos_s=QOS_NS * 1e-9):
         cm = self.cm
@@ -671,9 +701,24 @@ def measure_workload(name, args, local, headline: bool):
     timed = None
     try:
         levels, dur = wl.profile()
-        inst_c, quota_c, obj = wl.allocate(levels, dur)
+        inst_s, quota_s, obj_s = wl.allocate(levels, dur)
         out["profile_ms"] = {"levels": levels, "stage_batch_ms": (dur * 1e3).round(4).tolist()}
-        out["allocator"] = {"instances": inst_c, "sm_quota": quota_c, "predicted_min_thr_qps": obj}
+        # the solo profile misses the per-batch hand-over inside the pipeline:
+        # measure it on the solo choice, add it to the table, solve Eq. 1 again
+        dur_at = lambda q: [float(dur[i][levels.index(q[i])]) for i in range(len(q))]
+        h, t_in, sat_s = wl.handover(inst_s, quota_s, dur_at(quota_s))
+        inst_c, quota_c, obj = wl.allocate(levels, dur, handover=h)
+        if (inst_c, quota_c) == (inst_s, quota_s):
+            sat_c = sat_s
+        else:
+            _, _, sat_c = wl.handover(inst_c, quota_c, dur_at(quota_c))
+        out["allocator"] = {"instances": inst_c, "sm_quota": quota_c, "predicted_min_thr_qps": obj,
+                            "measured_saturation_qps": sat_c, "measured_over_predicted": sat_c / obj,
+                            "handover_us": [v * 1e6 for v in h],
+                            "in_pipeline_batch_us": [v * 1e6 for v in t_in],
+                            "solo_profile_only": {"instances": inst_s, "sm_quota": quota_s,
+                                                  "predicted_min_thr_qps": obj_s, "measured_saturation_qps": sat_s,
+                                                  "measured_over_predicted": sat_s / obj_s}}
         inst_r, quota_r, table = wl.refine(inst_c, quota_c)
         out["refined"] = {"instances": inst_r, "sm_quota": quota_r, "measured_neighbours": table}
         main_alloc = (inst_r, quota_r) if name == "bf16-3stage" else wl.w["even"]
@@ -700,8 +745,14 @@ def measure_workload(name, args, local, headline: bool):
         out["host_staged"] = res[("main", 1)]
         out["other_alloc_global"] = res[("other", 0)]
         out["other_alloc_host_staged"] = res[("other", 1)]
-        g, h = out["global"]["value"], out["host_staged"]["value"]
-        out["global_over_host_staged"] = g / h if h else None
+        gv, hv = out["global"]["value"], out["host_staged"]["value"]
+        out["global_over_host_staged"] = gv / hv if hv else None
+        # the library's simulator on the hand-over profile beside the measurement
+        if all(q in levels for q in main_alloc[1]) and out["global"]["peak_rate"]:
+            sim = wl.simulated(levels, dur, main_alloc[0], main_alloc[1], h, out["global"]["peak_rate"])
+            out["simulated_at_peak"] = {"rate_qps": out["global"]["peak_rate"], "p50_ms": sim[0] * 1e3,
+                                        "p99_ms": sim[1] * 1e3, "throughput_qps": sim[2],
+                                        "measured_p99_ms": out["global"]["p99_ms"]}
         if headline:
             out["load_curve"], out["batch_sweep"] = load_and_batch_sweep(wl, main_alloc, res)
     except Exception:
@@ -914,8 +965,9 @@ def run_diurnal(args):
     plain 2-stage pipeline: a diurnal day of sinusoidal Poisson arrivals from 10 %
     to 100 % of the measured peak, compressed into `--diurnal` seconds and cut
     into 60 windows; per window camelot_allocate (MIN_SM) picks the fewest SMs
-    whose profiled throughput, scaled by the measured efficiency of the peak
-    allocation, covers the window's highest rate with 15 % headroom; the pipeline
+    whose profiled throughput (solo-run p99 plus the per-batch hand-over time
+    measured inside the pipeline) covers the window's highest rate with 15 %
+    headroom; the pipeline
     is rebuilt when the allocation changes and the window's arrivals replay on
     the device clock.  The same windows replay on the static peak allocation
     (Eq. 1).  value = 1 - SM-time(Eq. 3) / SM-time(static)."""
@@ -930,13 +982,20 @@ def run_diurnal(args):
     try:
         batches = [8, 16, 32]
         levels, dur = wl.profile_batches(batches)
-        pr, keep = wl.alloc_table(levels, batches, dur)
+        pr0, keep0 = wl.alloc_table(levels, batches, dur)
+        inst_0, quota_0, B_0, obj_0 = wl.solve(pr0, cm.POLICY_MAX_PEAK)
+        # the per-batch hand-over inside the pipeline, measured on the solo
+        # choice and added to every entry of the table (at its batch size)
+        bi0 = batches.index(B_0)
+        h, t_in, sat_0 = wl.handover(inst_0, quota_0, [float(dur[bi0, i, levels.index(q)])
+                                                       for i, q in enumerate(quota_0)], batch=B_0)
+        pr, keep = wl.alloc_table(levels, batches, dur, handover=h)
         inst_p, quota_p, B_p, obj_p = wl.solve(pr, cm.POLICY_MAX_PEAK)
         lam_peak, p, sat = wl.peak(0, inst_p, quota_p, batch=B_p)
         cm.camelot_pipeline_destroy(p)
         lam_hs, p, _ = wl.peak(1, inst_p, quota_p, batch=B_p)
         cm.camelot_pipeline_destroy(p)
-        eff = lam_peak / obj_p
+        eff = sat["qps"] / obj_p
         arrivals = synth.diurnal_arrivals_ns(7, lam_peak, T)
         edges = (np.arange(nwin + 1) * W * 1e9).astype(np.int64)
         counts = np.diff(np.searchsorted(arrivals, edges))
@@ -979,7 +1038,7 @@ def run_diurnal(args):
         def dynamic(w):
             t0, t1 = w * W, (w + 1) * W
             lam = max(rate(t0), rate(t1), rate(min(max(T / 2, t0), t1)))
-            load = lam * 1.15 / eff
+            load = lam * 1.15
             if load >= obj_p:
                 return inst_p, quota_p, B_p       # the peak windows keep the peak allocation
             try:
@@ -1010,7 +1069,10 @@ def run_diurnal(args):
         "peak_qps": lam_peak, "peak_qps_host_staged": lam_hs, "saturation_qps": sat["qps"],
         "static_alloc": {"instances": inst_p, "sm_quota": quota_p, "batch": B_p,
                          "predicted_min_thr_qps": obj_p},
-        "allocator_efficiency": eff,
+        "allocator_measured_over_predicted": eff,
+        "handover_us": [v * 1e6 for v in h], "in_pipeline_batch_us": [v * 1e6 for v in t_in],
+        "solo_profile_only": {"instances": inst_0, "sm_quota": quota_0, "batch": B_0, "predicted_min_thr_qps": obj_0,
+                              "measured_saturation_qps": sat_0, "measured_over_predicted": sat_0 / obj_0},
         "sm_seconds": {"eq3": sm_dyn, "static": sm_stat},
         "qos_violating_windows": {"eq3": viol_d, "static": viol_s},
         "p99_ms_max": {"eq3": max(r.get("p99_ms", 0) for r in dyn),
@@ -1269,15 +1331,17 @@ def run_artifact(args):
             out["stages"][k]["batch_ms_at_8_sms"] = d[0] * 1e3
             out["stages"][k]["gbs_at_8_sms"] = hbm_bytes[k] / d[0] / 1e9
 
-        def solve(names, bw_budget):
+        def solve(names, bw_budget, handover=None):
+            # Table 2 quantities by the library (bytes per query: rows in and out
+            # plus the table bytes it streams), optionally with hand-over times
             n = len(names)
-            f = np.ascontiguousarray(np.stack([B / dur[k] for k in names])[None], np.float64)
-            bw = np.ascontiguousarray(np.stack([hbm_bytes[k] / dur[k] / 1e9 for k in names])[None], np.float64)
-            dd = np.ascontiguousarray(np.stack([dur[k] for k in names])[None], np.float64)
-            mem = np.ascontiguousarray(np.full((1, n), 64e6), np.float64)
+            costs = [(i, 0.0, 0.0, hbm_bytes[k] / B, 64e6) for i, k in enumerate(names)]
             bs = np.array([B], np.int32)
-            pr = cm.Profile(n, len(levels), 1, 8, bs.ctypes.data, f.ctypes.data, bw.ctypes.data, dd.ctypes.data,
+            thr, bw, dd, mem = cm.camelot_profile_from_latency(costs, bs, np.stack([dur[k] for k in names])[None])
+            pr = cm.Profile(n, len(levels), 1, 8, bs.ctypes.data, thr.ctypes.data, bw.ctypes.data, dd.ctypes.data,
                             mem.ctypes.data)
+            if handover is not None:
+                cm.camelot_profile_add_handover(pr, handover, thr, bw, dd)
             cons = cm.Constraints(sms, sms // 8, bw_budget, 200e9, QOS_NS * 1e-9, 0.0, cm.SOLVER_EXHAUSTIVE, 0,
                                   0.0, 0.0, 0)
             a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
@@ -1310,6 +1374,24 @@ def run_artifact(args):
             run_trace.last[p] = ms
             return c, dt
         run_trace.last = {}
+
+        def handover_of(names, inst, quota):
+            """In-pipeline service time per batch minus the solo duration, per
+            stage, from one saturated trace (camelot_stats.busy_ns)."""
+            o = pl.options(exit_after_trace=1, query_slots=1 << 16, idle_exit_ns=20_000_000)
+            p = cm.camelot_pipeline_create([st[k] for k in names], pl.alloc(inst, quota, B), 0, o)
+            run_trace.last[p] = 0.0
+            try:
+                data = base.repeat(3, 1)[:20_000].contiguous()
+                s0 = cm.camelot_pipeline_stats(p)
+                run_trace(p, np.zeros(20_000, np.int64), data)
+                s1 = cm.camelot_pipeline_stats(p)
+                del data
+            finally:
+                cm.camelot_pipeline_destroy(p)
+            t_in = [(s1.busy_ns[i] - s0.busy_ns[i]) / max(1, s1.batches[i] - s0.batches[i]) * 1e-9
+                    for i in range(len(names))]
+            return [t_in[i] - float(dur[k][quota[i] // 8 - 1]) for i, k in enumerate(names)]
 
         def measure(names, inst, quota, lam):
             stages = [st[k] for k in names]
@@ -1345,6 +1427,12 @@ def run_artifact(args):
                        "nc": {"instances": nc[0], "sm_quota": nc[1], "predicted_peak_qps": nc[2],
                               "predicted_gbs": nc[3]}}
                 row["camelot"].update(measure(names, ca[0], ca[1], 0.9 * ca[2]))
+                # the same solver on the profile with the measured per-batch hand-over
+                h = handover_of(names, ca[0], ca[1])
+                ch = solve(names, hbm, handover=h)
+                row["camelot_handover"] = {"handover_us": [v * 1e6 for v in h], "instances": ch[0],
+                                           "sm_quota": ch[1], "predicted_peak_qps": ch[2], "predicted_gbs": ch[3]}
+                row["camelot_handover"].update(measure(names, ch[0], ch[1], 0.9 * ch[2]))
                 if (nc[0], nc[1]) == (ca[0], ca[1]):
                     row["nc"]["same_as_camelot"] = True
                 else:
@@ -1409,6 +1497,12 @@ def run_artifact(args):
             "pipelines": len(cases), "nc_allocation_differs": len(diff),
             "nc_qos_violations": sum(viol(c["nc"]) for c in diff),
             "camelot_qos_violations": sum(viol(c["camelot"]) for c in cases),
+            "camelot_handover_qos_violations": sum(viol(c["camelot_handover"]) for c in cases),
+            "camelot_measured_over_predicted_median": float(np.median(
+                [c["camelot"]["saturation_qps"] / c["camelot"]["predicted_peak_qps"] for c in cases])),
+            "camelot_handover_measured_over_predicted_median": float(np.median(
+                [c["camelot_handover"]["saturation_qps"] / c["camelot_handover"]["predicted_peak_qps"]
+                 for c in cases])),
             "nc_worst_p99_over_qos": max([c["nc"]["p99_ms"] / (QOS_NS * 1e-6) for c in diff] or [0.0]),
             "camelot_worst_p99_over_qos": max(c["camelot"]["p99_ms"] / (QOS_NS * 1e-6) for c in cases)}
     finally:
@@ -1539,6 +1633,57 @@ def run_stage_case(args):
     return 0
 
 
+def run_mlp_layers(args):
+    """Direct-launch time of the FP32 MLP stage of the plain 2-stage pipeline
+    and of its parts (layer 1 alone; layers 2 + 3), batch 16, at several SM
+    quotas (median of 20 back-to-back launches after 3 warm-up ones, CUDA
+    events), beside the launch overhead (a one-query normalise stage)."""
+    import torch
+    import synth
+    from paper_2005_02088_b300 import camelot as cm, pipelines as pl
+    x, ws = synth.cfg1_inputs(0, n_queries=64)
+    wd = [torch.from_numpy(w).cuda() for w in ws]
+    B = 16
+    y = torch.from_numpy(((x[:B].reshape(B, -1).astype(np.float32) - 127.5) / 64)).cuda()
+    h1 = torch.zeros((B, 512), device="cuda")
+
+    def median_us(st, inp, n, out, idx, val, ctas):
+        _, _, sb = cm.camelot_stage_info(st, n)
+        scr = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(21)]
+        for _ in range(3):
+            cm.camelot_stage_launch(st, ctas, inp, n, out, idx, val, None, scr, sb, None)
+        for i in range(20):
+            ev[i].record()
+            cm.camelot_stage_launch(st, ctas, inp, n, out, idx, val, None, scr, sb, None)
+        ev[20].record()
+        torch.cuda.synchronize()
+        return float(np.median([ev[i].elapsed_time(ev[i + 1]) for i in range(20)])) * 1e3
+
+    idx = torch.empty((B, 5), dtype=torch.int32, device="cuda")
+    val = torch.empty((B, 5), dtype=torch.float32, device="cuda")
+    parts = {"layer1": ([wd[0]], [1], 0, y, torch.empty((B, 512), device="cuda")),
+             "layers2_3": ([wd[1], wd[2]], [1, 0], 1, h1, None),
+             "whole": (wd, [1, 1, 0], 1, y, None)}
+    ctas = [int(c) for c in args.ctas_list.split(",")]
+    res = {}
+    for name, (w, acts, k, inp, out) in parts.items():
+        st = pl.stage_dense(cm.STAGE_MLP_FP32, w, acts, top_k=k, max_batch=32)
+        try:
+            res[name] = {c: median_us(st, inp, B, out, idx if k else None, val if k else None, c) for c in ctas}
+        finally:
+            cm.camelot_stage_release(st)
+    s0 = pl.stage_normalize(64, 64, 3, max_batch=32)
+    try:
+        xi = torch.from_numpy(np.ascontiguousarray(x[:1].reshape(1, -1))).cuda()
+        res["launch_overhead"] = {c: median_us(s0, xi, 1, torch.empty((1, 12288), device="cuda"), None, None, c)
+                                  for c in (ctas[0], ctas[-1])}
+    finally:
+        cm.camelot_stage_release(s0)
+    print(json.dumps({"mlp_layers_us_per_batch_of_16": res}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1552,6 +1697,9 @@ def main():
     ap.add_argument("--stage", type=int, default=1)
     ap.add_argument("--ctas", type=int, default=8)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--mlp-layers", action="store_true",
+                    help="time the FP32 MLP stage and its layers by direct launches at --ctas-list SM quotas")
+    ap.add_argument("--ctas-list", default="8,16,72,144")
     ap.add_argument("--predictor", action="store_true",
                     help="run the latency-predictor study (profiling, GPU training, allocation) instead")
     ap.add_argument("--pred-samples", type=int, default=20000)
@@ -1573,6 +1721,8 @@ def main():
         return run_profile_case(args)
     if args.stage_case:
         return run_stage_case(args)
+    if args.mlp_layers:
+        return run_mlp_layers(args)
     if args.predictor:
         return run_predictor(args)
     if args.diurnal > 0:

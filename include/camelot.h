@@ -507,6 +507,11 @@ typedef struct {
     int32_t device_status, device_where;    /* first device error (0 = none)              */
     double last_launch_ms;                  /* CUDA-event duration of the last finished launch */
     double total_launch_ms;                 /* sum over finished launches                  */
+    uint64_t busy_ns[CAMELOT_MAX_STAGES];   /* per stage, summed over its batches (device clock):
+                                               from the instance holding a batch's work (input
+                                               and output slots) to the batch published, so
+                                               busy_ns / batches is the in-pipeline service time
+                                               of one batch, hand-over included              */
 } camelot_stats;
 
 camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);
@@ -687,6 +692,35 @@ camelot_status camelot_allocate(const camelot_profile* prof, camelot_policy poli
  * largest it grows in proportion to b.  Host-only.  Errors: EINVAL. */
 camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelot_alloc* alloc,
                                        int64_t* out_ns);
+
+/* The per-batch hand-over cost of a pipeline in the allocator's table: a
+ * stage inside a pipeline spends a different time per batch than when it is
+ * timed alone by separate launches: the batch's work is acquired from a ring,
+ * posted to the instance's CTAs, counted back and published, co-located
+ * stages share the memory system, and no launch overhead is paid.  With
+ * handover_s[i] the measured difference for stage i (camelot_stats.busy_ns /
+ * batches in a pipeline minus the solo duration at the same quota; it may be
+ * negative), every entry becomes d' = d + handover_s[i], f' = B / d',
+ * bandwidth' = bandwidth d / d' (the same bytes in the new time).  Outputs are
+ * arrays shaped like the profile's (they may be the profile's own).
+ * Host-only.  Errors: EINVAL (also when a corrected duration is not > 0). */
+camelot_status camelot_profile_add_handover(const camelot_profile* prof, const double* handover_s,
+                                            double* thr, double* bw, double* dur);
+
+/* Event-driven simulation of the pipeline on its profile (the allocator's
+ * model of Sec. 5.2 and Eq. 1): n_queries Poisson arrivals at rate_qps (a
+ * SplitMix64 stream from seed), the batch trigger (B = alloc->batch, or the
+ * oldest waited max_wait_s), alloc->instances[i] instances of stage i, each
+ * batch of b queries served in the profiled duration at the stage's quota
+ * (interpolated as camelot_trigger_latency does) plus handover_s[i] (NULL =
+ * 0; the sum must stay > 0); unbounded buffers between stages.  Reports the p50 and p99 latency
+ * (arrival to last stage done) over the queries after the first 10 %, and the
+ * throughput: completions per second after the first 10 % of them.
+ * Host-only.  Errors: EINVAL. */
+camelot_status camelot_simulate_profile(const camelot_profile* prof, const camelot_alloc* alloc,
+                                        const double* handover_s, double max_wait_s, double rate_qps,
+                                        uint32_t n_queries, uint64_t seed, double* p50_s, double* p99_s,
+                                        double* thr_qps);
 
 #ifdef __cplusplus
 }

@@ -71,7 +71,7 @@ class Stats(C.Structure):
                 ("relayed_bytes", C.c_uint64), ("device_bytes_per_batch_slot", C.c_uint64),
                 ("device_ring_bytes", C.c_uint64), ("device_status", C.c_int32),
                 ("device_where", C.c_int32), ("last_launch_ms", C.c_double),
-                ("total_launch_ms", C.c_double)]
+                ("total_launch_ms", C.c_double), ("busy_ns", C.c_uint64 * MAX_STAGES)]
 
 
 class ServerOptions(C.Structure):
@@ -147,6 +147,8 @@ _SIGS = {
     "camelot_pipeline_stall_relay": (C.c_int, [P, C.c_int]),
     "camelot_allocate": (C.c_int, [P, C.c_int, P, P, P]),
     "camelot_trigger_latency": (C.c_int, [P, P, P]),
+    "camelot_profile_add_handover": (C.c_int, [P, P, P, P, P]),
+    "camelot_simulate_profile": (C.c_int, [P, P, P, C.c_double, C.c_double, C.c_uint32, C.c_uint64, P, P, P]),
     "camelot_server_options_default": (None, [P]),
     "camelot_server_create": (C.c_int, [P, C.c_int, P, P]),
     "camelot_server_submit": (C.c_int, [P, C.c_int, C.c_uint32, P, C.c_uint32, P]),
@@ -452,6 +454,25 @@ def camelot_trigger_latency(prof: Profile, alloc: Alloc):
     out = (C.c_int64 * 32)()
     _check(load().camelot_trigger_latency(C.byref(prof), C.byref(alloc), out))
     return list(out)
+
+
+def camelot_profile_add_handover(prof: Profile, handover_s, thr, bw, dur) -> None:
+    """In place on the float64 arrays thr, bw, dur (which may be the profile's own)."""
+    import numpy as np
+    h = np.ascontiguousarray(handover_s, np.float64)
+    _check(load().camelot_profile_add_handover(C.byref(prof), h.ctypes.data, _ptr(thr), _ptr(bw), _ptr(dur)))
+
+
+def camelot_simulate_profile(prof: Profile, alloc: Alloc, handover_s, max_wait_s: float, rate_qps: float,
+                             n_queries: int = 20000, seed: int = 1):
+    """(p50 s, p99 s, throughput q/s) of the simulated pipeline."""
+    import numpy as np
+    h = None if handover_s is None else np.ascontiguousarray(handover_s, np.float64)
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(load().camelot_simulate_profile(C.byref(prof), C.byref(alloc), None if h is None else h.ctypes.data,
+                                           max_wait_s, rate_qps, n_queries, seed, C.byref(a), C.byref(b),
+                                           C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def camelot_server_options_default() -> ServerOptions:

@@ -10,6 +10,8 @@
 // accepted with a probability that decays with a geometric temperature,
 // from several starting states.  Host code only.
 #include <algorithm>
+#include <deque>
+#include <queue>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -230,43 +232,199 @@ extern "C" camelot_status camelot_allocate(const camelot_profile* prof, camelot_
     return CAMELOT_OK;
 }
 
-extern "C" camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelot_alloc* alloc,
-                                                  int64_t* out_ns) {
-    if (!prof || !alloc || !out_ns || !prof->batch_sizes || !prof->dur_s)
-        return set_err(CAMELOT_EINVAL, "null argument");
+namespace {
+// Checks a profile against an allocation and returns each stage's quota level.
+camelot_status profile_levels(const camelot_profile* prof, const camelot_alloc* alloc, int* level) {
+    if (!prof || !alloc || !prof->batch_sizes || !prof->dur_s) return set_err(CAMELOT_EINVAL, "null argument");
     const int n = prof->n_stages, L = prof->n_levels, nb = prof->n_batches, unit = prof->unit;
     if (n < 1 || n > CAMELOT_MAX_STAGES || L < 1 || nb < 1 || unit < 1 || alloc->n_stages != n)
         return set_err(CAMELOT_EINVAL, "profile and allocation shapes disagree");
     for (int j = 0; j < nb; ++j)
         if (prof->batch_sizes[j] < 1 || (j > 0 && prof->batch_sizes[j] <= prof->batch_sizes[j - 1]))
             return set_err(CAMELOT_EINVAL, "batch_sizes must be positive and increasing");
-    int level[CAMELOT_MAX_STAGES];
     for (int i = 0; i < n; ++i) {
         const int q = alloc->sm_quota[i];
         if (q < unit || q % unit != 0 || q / unit > L)
             return set_err(CAMELOT_EINVAL, "an SM quota is not a level of the profile");
         level[i] = q / unit - 1;
     }
-    auto dur = [&](int j, int i) { return prof->dur_s[((size_t)j * n + i) * L + level[i]]; };
+    return CAMELOT_OK;
+}
+
+// Duration of a b-query batch of stage i at its level: linear between the
+// profiled batch sizes, the smallest one's below them, in proportion to b above.
+double stage_duration(const camelot_profile* prof, const int* level, int i, int b) {
+    const int n = prof->n_stages, L = prof->n_levels, nb = prof->n_batches;
+    const int* bs = prof->batch_sizes;
+    auto dur = [&](int j) { return prof->dur_s[((size_t)j * n + i) * L + level[i]]; };
+    if (b <= bs[0]) return dur(0);
+    if (b >= bs[nb - 1]) return dur(nb - 1) * (double)b / (double)bs[nb - 1];
+    int j = 0;
+    while (bs[j + 1] < b) ++j;
+    const double f = (double)(b - bs[j]) / (double)(bs[j + 1] - bs[j]);
+    return dur(j) + f * (dur(j + 1) - dur(j));
+}
+}  // namespace
+
+extern "C" camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelot_alloc* alloc,
+                                                  int64_t* out_ns) {
+    if (!out_ns) return set_err(CAMELOT_EINVAL, "null argument");
+    int level[CAMELOT_MAX_STAGES];
+    const camelot_status st = profile_levels(prof, alloc, level);
+    if (st != CAMELOT_OK) return st;
     for (int b = 1; b <= 32; ++b) {
         double t = 0.0;
-        for (int i = 0; i < n; ++i) {
-            const int* bs = prof->batch_sizes;
-            double d;
-            if (b <= bs[0]) {
-                d = dur(0, i);
-            } else if (b >= bs[nb - 1]) {
-                d = dur(nb - 1, i) * (double)b / (double)bs[nb - 1];
-            } else {
-                int j = 0;
-                while (bs[j + 1] < b) ++j;
-                const double f = (double)(b - bs[j]) / (double)(bs[j + 1] - bs[j]);
-                d = dur(j, i) + f * (dur(j + 1, i) - dur(j, i));
-            }
+        for (int i = 0; i < prof->n_stages; ++i) {
+            const double d = stage_duration(prof, level, i, b);
             if (!(d >= 0.0)) return set_err(CAMELOT_EINVAL, "negative or NaN duration in the profile");
             t += d;
         }
         out_ns[b - 1] = (int64_t)std::llround(t * 1e9);
     }
+    return CAMELOT_OK;
+}
+
+extern "C" camelot_status camelot_profile_add_handover(const camelot_profile* prof, const double* handover_s,
+                                                       double* thr, double* bw, double* dur) {
+    if (!prof || !handover_s || !thr || !bw || !dur || !prof->thr_qps || !prof->bw_gbs || !prof->dur_s ||
+        !prof->batch_sizes)
+        return set_err(CAMELOT_EINVAL, "null argument");
+    const int n = prof->n_stages, L = prof->n_levels, nb = prof->n_batches;
+    if (n < 1 || L < 1 || nb < 1) return set_err(CAMELOT_EINVAL, "empty profile");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(handover_s[i])) return set_err(CAMELOT_EINVAL, "hand-over times must be finite");
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < n; ++i)
+            for (int l = 0; l < L; ++l) {
+                const size_t k = ((size_t)b * n + i) * L + l;
+                const double d = prof->dur_s[k];
+                if (!(d > 0.0)) return set_err(CAMELOT_EINVAL, "durations must be positive");
+                const double bytes = prof->bw_gbs[k] * d;     // GB moved by one batch
+                const double d2 = d + handover_s[i];
+                if (!(d2 > 0.0)) return set_err(CAMELOT_EINVAL, "a corrected duration is not positive");
+                dur[k] = d2;
+                thr[k] = (double)prof->batch_sizes[b] / d2;
+                bw[k] = bytes / d2;
+            }
+    return CAMELOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pipeline simulation on the profile: Poisson arrivals, the batch trigger and
+// N_i instances per stage, each batch's service time the profiled duration of
+// its size at the stage's quota plus the stage's hand-over time.
+// ---------------------------------------------------------------------------
+namespace {
+struct SimBatch {
+    uint64_t first;
+    int n;
+};
+struct SimEvent {
+    double t;
+    int stage;
+    uint64_t batch;
+    bool operator<(const SimEvent& o) const { return t > o.t || (t == o.t && stage < o.stage); }
+};
+}  // namespace
+
+extern "C" camelot_status camelot_simulate_profile(const camelot_profile* prof, const camelot_alloc* alloc,
+                                                   const double* handover_s, double max_wait_s, double rate_qps,
+                                                   uint32_t n_queries, uint64_t seed, double* p50_s,
+                                                   double* p99_s, double* thr_qps) {
+    if (!p50_s || !p99_s || !thr_qps) return set_err(CAMELOT_EINVAL, "null argument");
+    int level[CAMELOT_MAX_STAGES];
+    const camelot_status st = profile_levels(prof, alloc, level);
+    if (st != CAMELOT_OK) return st;
+    const int n = prof->n_stages, B = alloc->batch;
+    if (B < 1 || B > 32 || !(rate_qps > 0.0) || n_queries < 10 || !(max_wait_s >= 0.0))
+        return set_err(CAMELOT_EINVAL, "batch 1..32, rate > 0, >= 10 queries, max_wait >= 0 required");
+    std::vector<std::vector<double>> svc(n, std::vector<double>(B + 1, 0.0));
+    for (int i = 0; i < n; ++i) {
+        if (alloc->instances[i] < 1) return set_err(CAMELOT_EINVAL, "instances must be >= 1");
+        const double h = handover_s ? handover_s[i] : 0.0;
+        if (!std::isfinite(h)) return set_err(CAMELOT_EINVAL, "hand-over times must be finite");
+        for (int b = 1; b <= B; ++b) {
+            svc[i][b] = stage_duration(prof, level, i, b) + h;
+            if (!(svc[i][b] > 0.0)) return set_err(CAMELOT_EINVAL, "a corrected duration is not positive");
+        }
+    }
+    // arrivals: exponential gaps from a SplitMix64 stream
+    std::vector<double> arr(n_queries), done(n_queries, 0.0);
+    uint64_t x = seed;
+    double t = 0.0;
+    for (uint32_t q = 0; q < n_queries; ++q) {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double u = ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        t += -std::log(u) / rate_qps;
+        arr[q] = t;
+    }
+    std::vector<SimBatch> batches;
+    std::vector<std::deque<uint64_t>> queue(n);   // batches waiting for stage i (i >= 1)
+    std::vector<int> free_inst(alloc->instances, alloc->instances + n);
+    std::priority_queue<SimEvent> ev;
+    uint64_t next = 0, taken = 0, completed = 0;   // next arrival; first query not yet batched
+    double now = 0.0;
+    while (completed < n_queries) {
+        // start whatever can start now: later stages first, then the trigger
+        for (int i = n - 1; i >= 1; --i)
+            while (free_inst[i] > 0 && !queue[i].empty()) {
+                const uint64_t bi = queue[i].front();
+                queue[i].pop_front();
+                --free_inst[i];
+                ev.push({now + svc[i][batches[bi].n], i, bi});
+            }
+        while (next < n_queries && arr[next] <= now) ++next;
+        while (free_inst[0] > 0 && taken < next) {
+            const uint64_t waiting = next - taken;
+            const bool full = waiting >= (uint64_t)B;
+            if (!full && now < arr[taken] + max_wait_s) break;
+            const int b = (int)std::min<uint64_t>(waiting, (uint64_t)B);
+            batches.push_back({taken, b});
+            taken += b;
+            --free_inst[0];
+            ev.push({now + svc[0][b], 0, batches.size() - 1});
+        }
+        // the next moment something changes
+        double t_next = INFINITY;
+        if (!ev.empty()) t_next = ev.top().t;
+        if (next < n_queries) t_next = std::min(t_next, arr[next]);
+        if (taken < next && free_inst[0] > 0) t_next = std::min(t_next, arr[taken] + max_wait_s);
+        if (!(t_next < INFINITY)) return set_err(CAMELOT_EINVAL, "simulation stalled");
+        now = std::max(now, t_next);
+        while (!ev.empty() && ev.top().t <= now) {
+            const SimEvent e = ev.top();
+            ev.pop();
+            ++free_inst[e.stage];
+            if (e.stage + 1 < n) {
+                queue[e.stage + 1].push_back(e.batch);
+            } else {
+                const SimBatch& sb = batches[e.batch];
+                for (int k = 0; k < sb.n; ++k) done[sb.first + k] = e.t;
+                completed += sb.n;
+            }
+        }
+    }
+    // latencies after the first 10 % (warm-up)
+    const uint32_t skip = n_queries / 10;
+    std::vector<double> lat;
+    lat.reserve(n_queries - skip);
+    for (uint32_t q = skip; q < n_queries; ++q) lat.push_back(done[q] - arr[q]);
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) {
+        const double pos = p * (double)(lat.size() - 1);
+        const size_t lo = (size_t)pos;
+        const size_t hi = std::min(lo + 1, lat.size() - 1);
+        return lat[lo] + (pos - (double)lo) * (lat[hi] - lat[lo]);
+    };
+    *p50_s = pct(0.50);
+    *p99_s = pct(0.99);
+    // completions per second after the first 10 % of them
+    std::vector<double> fin(done);
+    std::sort(fin.begin(), fin.end());
+    *thr_qps = (double)(n_queries - skip) / (fin[n_queries - 1] - fin[skip > 0 ? skip - 1 : 0]);
     return CAMELOT_OK;
 }

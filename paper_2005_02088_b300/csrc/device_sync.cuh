@@ -36,6 +36,8 @@ struct alignas(128) Ctl {
     Line64 trace_t0;                 // device time the running trace started (0 = not yet)
     Line64 exited[8];                // instances of stage s that have exited this launch
     Line64 batches[8];               // batches finished by stage s (statistics)
+    Line64 busy_ns[8];               // stage s: summed over its batches, the time from the
+                                     // instance holding its work to the batch published
 };
 
 // Flags the host writes and the device reads (pinned, mapped host memory).

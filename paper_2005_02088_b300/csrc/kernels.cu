@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     __shared__ unsigned int sh_cmd, sh_n, sh_trace, sh_ok;
     __shared__ unsigned long long sh_in, sh_first, sh_out;
     __shared__ long long sh_tb;
+    __shared__ unsigned long long sh_t_work;   // leader: when this batch's work was held
     LeaderState ls{~0ull, 0, gtime(), 0u};
     const bool tensor_stage = is_tensor_kind(SP.kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                 if (threadIdx.x == 0) {
                     if (cmd == CMD_WORK && !final_stage && !reserve_out(P, P.out_ring[s], s, &out_t))
                         cmd = CMD_EXIT;
+                    sh_t_work = gtime();
                     sh_cmd = cmd;
                     sh_n = n;
                     sh_in = in_t;
@@ -369,7 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
             st_release_gpu(&r.seq[slot], sh_in + r.slots);
             if (r.note_free != nullptr) st_release_sys(&r.note_free[slot], sh_in + r.slots);
         }
-        if (threadIdx.x == 0) atomicAdd(&P.ctl->batches[s].v, 1ull);
+        if (threadIdx.x == 0) {
+            atomicAdd(&P.ctl->batches[s].v, 1ull);
+            atomicAdd(&P.ctl->busy_ns[s].v, (unsigned long long)(gtime() - sh_t_work));
+        }
         __syncthreads();   // the leader's shared mailbox copy is rewritten next
     }
     __syncthreads();

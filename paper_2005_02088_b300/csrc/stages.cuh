@@ -253,6 +253,16 @@ __device__ __forceinline__ void pool_setup(float* smem) {
     __syncthreads();
 }
 
+// (sum / 4 - 127.5) / 64 = sum / 256 - 510 / 256 for an integer sum of four
+// bytes (<= 1020): the float of sum comes from its bits under the exponent of
+// 2^23 (0x4B000000 | sum is 2^23 + sum exactly; subtracting 2^23 is exact), and
+// the fused multiply-add is exact too (the result needs at most 18 bits), so
+// the value is the exact one, as (float(sum) * 0.25 - 127.5) * 0.015625 is.
+__device__ __forceinline__ float pooled_value(uint32_t sum) {
+    const float f = __uint_as_float(0x4B000000u | sum) - 8388608.0f;
+    return fmaf(f, 0.00390625f, -1.9921875f);
+}
+
 static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                      RowRef out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -314,6 +324,7 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
             // three 8-byte loads and storing three 8-byte runs
             const int k4 = (P.W / 2) / 4;                       // items per output row
             const int items = min(G, Ho - ho0) * k4;
+#pragma unroll 2
             for (int it = lane; it < items; it += 32) {
                 const int r = it / k4, k = it - r * k4;
                 const uint2* a0 = reinterpret_cast<const uint2*>(sm + r * pair_bytes + 24 * k);
@@ -335,7 +346,7 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
                         const int j = (v + h) / 3, cch = (v + h) % 3;   // output pixel, channel
                         const int o = 6 * j + cch;                      // pixel 2j, then 2j + 1 at + 3
                         const uint32_t sum = byte(w0, o) + byte(w0, o + 3) + byte(w1, o) + byte(w1, o + 3);
-                        y2[h] = (static_cast<float>(sum) * 0.25f - 127.5f) * 0.015625f;
+                        y2[h] = pooled_value(sum);
                     }
                     const __nv_bfloat162 pr = __floats2bfloat162_rn(y2[0], y2[1]);
                     packed[v / 2] = *reinterpret_cast<const uint32_t*>(&pr);
@@ -395,25 +406,31 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
 // FP32 dense layers (MLP_FP32).
 // Task layer: y[q][j] = act(sum_k W[j][k] x[q][k]).  The K axis is cut into
 // fixed chunks of KC, and chunks into fixed groups of 8 (one per warp).  CTA
-// task (query group of 16, 128-neuron block, chunk group g): warp w accumulates
-// chunk 8g+w for the 16 x 128 outputs, each in ascending k with FMA; the 8 chunk
+// task (query group of 16, neuron block, chunk group g): warp w accumulates
+// chunk 8g+w for the block's outputs, each in ascending k with FMA; the 8 chunk
 // partials are added in chunk order in shared memory and stored as the group
-// partial P[g][q][j]; the reduce phase adds the groups in ascending order.  Each lane owns neurons lane,
-// lane+32, lane+64, lane+96 of the block: the packed weights [K/4][Npad][4]
-// give one coalesced 512-byte load per neuron slot and k-quad.  Weights
-// stream into a per-warp shared-memory ring kWRing quads ahead with cp.async;
-// the query activations are broadcast from the warp's copy of the chunk.
+// partial P[g][q][j]; the reduce phase adds the groups in ascending order.  Each
+// lane owns NL neurons of the block (lane, lane+32, ...): the packed weights
+// [K/4][Npad][4] give one coalesced 512-byte load per neuron slot and k-quad.
+// Weights stream into a per-warp shared-memory ring kWRing quads ahead with
+// cp.async; the query activations are broadcast from the warp's copy of the
+// chunk.  Blocks are 128 neurons (NL = 4); when an instance has more CTAs than
+// such tasks, 64-neuron blocks (NL = 2) double the tasks.  Either way every
+// output sums the same chunks in the same order, so the block width, like the
+// SM quota, leaves the results unchanged.
 // ---------------------------------------------------------------------------
-static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
-                            float* Pbuf) {
+template <int NL>
+static __device__ void dense_tasks_nl(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
+                                      float* Pbuf) {
+    constexpr int NB = 32 * NL;                        // neurons per task
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // per-warp shared memory: the query chunk [16][KC] and a ring of kWRing
-    // weight quads (each lane's 4 x 16 bytes, written and read by that lane)
+    // weight quads (each lane's NL x 16 bytes, written and read by that lane)
     constexpr int kXs = kQGroup * kMaxKC / 4;          // float4 per warp
     constexpr int kWs = kWRing * kNBlock;              // float4 per warp
     float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kXs + kWs);
     float4* wr = xs + kXs;
-    const int QG = (n + kQGroup - 1) / kQGroup, NBLK = L.Npad / kNBlock;
+    const int QG = (n + kQGroup - 1) / kQGroup, NBLK = L.Npad / NB;
     const int G = (L.C + kWarps - 1) / kWarps;         // chunk groups
     const int ntask = QG * NBLK * G;
     const float4* wp = reinterpret_cast<const float4*>(L.w);
@@ -423,15 +440,15 @@ static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, Row
         const int r = t / G;
         const int nb = r % NBLK, qg = r / NBLK;
         const int c = g * kWarps + warp;               // this warp's chunk
-        float acc[kQGroup][4];
+        float acc[kQGroup][NL];
 #pragma unroll
         for (int q = 0; q < kQGroup; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
+            for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
         if (c < L.C) {
             const int k0 = c * L.KC;
             const int kq_n = min(L.KC, L.K - k0) >> 2;
-            const float4* wq = wp + (size_t)(k0 >> 2) * ws + nb * kNBlock + lane;
+            const float4* wq = wp + (size_t)(k0 >> 2) * ws + nb * NB + lane;
             // group 0: the query chunk (zero rows past the batch) and weight quad 0
             for (int e = lane; e < kQGroup * kq_n; e += 32) {
                 const int q = e / kq_n, kq = e - q * kq_n;
@@ -444,7 +461,7 @@ static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, Row
             for (int d = 0; d < kWRing - 1; ++d) {
                 if (d < kq_n) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < NL; ++i)
                         cp_async16(wr + d * kNBlock + 32 * i + lane, wq + (size_t)d * ws + 32 * i);
                 }
                 cp_async_commit();
@@ -454,30 +471,31 @@ static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, Row
                 if (nxt < kq_n) {
                     float4* dst = wr + (nxt % kWRing) * kNBlock + lane;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < NL; ++i)
                         cp_async16(dst + 32 * i, wq + (size_t)nxt * ws + 32 * i);
                 }
                 cp_async_commit();
                 cp_async_wait<kWRing - 1>();      // this lane's copies up to quad kq have landed
                 if (kq == 0) __syncwarp();        // ... and every lane's part of the query chunk
                 const float4* wv = wr + (kq % kWRing) * kNBlock + lane;
-                const float4 a0 = wv[0], a1 = wv[32], a2 = wv[64], a3 = wv[96];
+                float4 a[NL];
+#pragma unroll
+                for (int i = 0; i < NL; ++i) a[i] = wv[32 * i];
 #pragma unroll
                 for (int q = 0; q < kQGroup; ++q) {
                     const float4 xv = xs[q * (kMaxKC / 4) + kq];
-                    acc[q][0] = fmaf(xv.x, a0.x, acc[q][0]); acc[q][0] = fmaf(xv.y, a0.y, acc[q][0]);
-                    acc[q][0] = fmaf(xv.z, a0.z, acc[q][0]); acc[q][0] = fmaf(xv.w, a0.w, acc[q][0]);
-                    acc[q][1] = fmaf(xv.x, a1.x, acc[q][1]); acc[q][1] = fmaf(xv.y, a1.y, acc[q][1]);
-                    acc[q][1] = fmaf(xv.z, a1.z, acc[q][1]); acc[q][1] = fmaf(xv.w, a1.w, acc[q][1]);
-                    acc[q][2] = fmaf(xv.x, a2.x, acc[q][2]); acc[q][2] = fmaf(xv.y, a2.y, acc[q][2]);
-                    acc[q][2] = fmaf(xv.z, a2.z, acc[q][2]); acc[q][2] = fmaf(xv.w, a2.w, acc[q][2]);
-                    acc[q][3] = fmaf(xv.x, a3.x, acc[q][3]); acc[q][3] = fmaf(xv.y, a3.y, acc[q][3]);
-                    acc[q][3] = fmaf(xv.z, a3.z, acc[q][3]); acc[q][3] = fmaf(xv.w, a3.w, acc[q][3]);
+#pragma unroll
+                    for (int i = 0; i < NL; ++i) {
+                        acc[q][i] = fmaf(xv.x, a[i].x, acc[q][i]);
+                        acc[q][i] = fmaf(xv.y, a[i].y, acc[q][i]);
+                        acc[q][i] = fmaf(xv.z, a[i].z, acc[q][i]);
+                        acc[q][i] = fmaf(xv.w, a[i].w, acc[q][i]);
+                    }
                 }
             }
             cp_async_wait<0>();
         }
-        // the warp's chunk partial [16][128] goes to its (now free) query and
+        // the warp's chunk partial [16][NB] goes to its (now free) query and
         // weight areas
         static_assert(kQGroup * kNBlock <= 4 * (kXs + kWs), "partial does not fit");
         __syncwarp();
@@ -485,20 +503,33 @@ static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, Row
 #pragma unroll
         for (int q = 0; q < kQGroup; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) part[q * kNBlock + 32 * i + lane] = acc[q][i];
+            for (int i = 0; i < NL; ++i) part[q * NB + 32 * i + lane] = acc[q][i];
         __syncthreads();
         // group partial = chunk partials added in warp (= chunk) order
-        for (int o = threadIdx.x; o < kQGroup * kNBlock; o += kThreads) {
-            const int q = o / kNBlock, j = o - q * kNBlock;
+        for (int o = threadIdx.x; o < kQGroup * NB; o += kThreads) {
+            const int q = o / NB, j = o - q * NB;
             const int gq = qg * kQGroup + q;
             float sum = 0.f;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w)
-                sum += reinterpret_cast<const float*>(cx.smem)[w * (kXs + kWs) * 4 + q * kNBlock + j];
-            if (gq < n) __stcg(Pbuf + ((size_t)g * n + gq) * L.Npad + nb * kNBlock + j, sum);
+                sum += reinterpret_cast<const float*>(cx.smem)[w * (kXs + kWs) * 4 + q * NB + j];
+            if (gq < n) __stcg(Pbuf + ((size_t)g * n + gq) * L.Npad + nb * NB + j, sum);
         }
         __syncthreads();
     }
+}
+
+static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
+                                   float* Pbuf) {
+    // half-width blocks when they shorten the slowest CTA's work: their 2T
+    // tasks take fewer rounds over the instance's CTAs than twice the rounds
+    // of the T full tasks
+    const int QG = (n + kQGroup - 1) / kQGroup;
+    const int G = (L.C + kWarps - 1) / kWarps;
+    const int T = QG * (L.Npad / kNBlock) * G;
+    const int rounds = (T + cx.nctas - 1) / cx.nctas, rounds2 = (2 * T + cx.nctas - 1) / cx.nctas;
+    if (rounds2 < 2 * rounds) dense_tasks_nl<2>(cx, L, x, n, Pbuf);
+    else dense_tasks_nl<4>(cx, L, x, n, Pbuf);
 }
 
 // Reduction over the G chunk groups, in ascending group order; each thread

@@ -44,7 +44,7 @@ int main(int argc, char** argv) {
         return 6;
     }
     camelot_profile prof = {2, L, 4, 8, batches, thr, bw, dur, mem};
-    camelot_constraints c = {total, total / 8, 6500.0, 1e12, 20e-3, 0.0, CAMELOT_SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0};
+    camelot_constraints c = {total, total / 8, 1e9, 1e12, 20e-3, 0.0, CAMELOT_SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0};
     camelot_alloc a;
     double obj = 0.0;
     if (camelot_allocate(&prof, CAMELOT_POLICY_MAX_PEAK, &c, &a, &obj) != CAMELOT_OK) {

@@ -3,8 +3,8 @@
 The GEMM stages accumulate in f32 on the tensor cores: an output is the sum of
 its K products taken one MMA instruction at a time (16 bf16 or 32 e4m3
 products per instruction, in k order) into an accumulator that starts at zero
-at the beginning of every K-chunk (the whole K up to 1024 columns, else 1024
-columns); the chunk partials are then added in chunk order in f32.
+at the beginning of every K-chunk (chunk_cols below); the chunk partials are
+then added in chunk order in f32.
 
 Model of one instruction (products of bf16 or e4m3 operands are exact in f32):
 the accumulator d and the t products are aligned to the largest of them and
@@ -28,8 +28,15 @@ U = 2.0 ** -24
 C_MMA = {16: 36.0, 32: 68.0}
 
 
-def chunk_cols(K: int) -> int:
-    return K if K <= 1024 else 1024
+def chunk_cols(K: int, N: int) -> int:
+    """The K-chunk the stage uses for a layer of N outputs: the whole K up to
+    1024 columns, else as few equal chunks (rounded up to 128 columns) as give
+    about 64 units of 128 output rows, at most one per 1024 columns."""
+    if K <= 1024:
+        return K
+    mt = (N + 127) // 128
+    c = max(1, min((K + 1023) // 1024, (64 + mt - 1) // mt))
+    return ((K + c - 1) // c + 127) // 128 * 128
 
 
 def mma_bound(x, xe, w, kstep: int):
@@ -44,7 +51,7 @@ def mma_bound(x, xe, w, kstep: int):
     w = np.asarray(w, np.float64)
     n, K = x.shape
     N = w.shape[0]
-    kc = chunk_cols(K)
+    kc = chunk_cols(K, N)
     c = C_MMA[kstep] * U
     aw = np.abs(w)
     A = np.zeros((n, N))

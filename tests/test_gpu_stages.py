@@ -124,7 +124,7 @@ def test_mlp_stage_independent_of_sm_quota_and_batch(orc):
     st = _mlp_stage(ws, top_k=3)
     try:
         base = _run_mlp(st, y, n, 1, k=3)
-        for n_ctas in (8, 37, 148):
+        for n_ctas in (8, 37, 64, 72, 144, 148):   # 128- and 64-neuron task blocks
             got = _run_mlp(st, y, n, n_ctas, k=3)
             for a, b in zip(base, got):
                 assert np.array_equal(a, b), n_ctas
