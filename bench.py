@@ -66,7 +66,7 @@ WORKLOADS = {
               "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
               "arrivals; p99 QoS 20 ms"),
         batch=32, row=224 * 224 * 3, even=([1, 1, 1], [48, 48, 48]),
-        profile_alloc=([3, 11, 4], [8, 8, 8]),
+        profile_alloc=([4, 11, 3], [8, 8, 8]),
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024),
@@ -120,9 +120,11 @@ def _peaks():
         return {}
 
 
-def stage_roofline(name, levels, dur, inst, quota, sm_count, sm_mhz):
+def stage_roofline(name, levels, dur, inst, quota, sm_count, sm_mhz, in_pipeline_s=None):
     """Each stage's achieved fraction of its roofline at the allocated quota,
-    from the solo profile (one batch of B on p SMs, CUDA events): algorithmic
+    from the solo profile (one batch of B on p SMs, CUDA events around direct
+    launches, so each includes the launch's own overhead) and, when given, from
+    the stage's service time per batch inside the pipeline: algorithmic
     bytes (weights once per batch + input and output rows per query) per
     second against the measured HBM copy bandwidth, both of the whole GPU and
     of the stage's share of the SMs (p / SM count); FLOPs per second against
@@ -152,6 +154,20 @@ def stage_roofline(name, levels, dur, inst, quota, sm_count, sm_mhz):
                 pk = peaks.get("bf16_tflops", 1800.0) * p / sm_count
                 r["tensor_peak_tflops_sm_share"] = pk
                 r["tensor_frac_of_sm_share"] = tf / pk
+        if in_pipeline_s is not None:
+            # the same quantities from the stage's service time per batch inside
+            # the pipeline (camelot_stats.busy_ns / batches: no launch overhead)
+            t = float(in_pipeline_s[si])
+            r["in_pipeline_batch_us"] = t * 1e6
+            r["in_pipeline_gbs"] = byts / t / 1e9
+            r["in_pipeline_hbm_frac_of_sm_share"] = byts / t / 1e9 / (hbm * p / sm_count)
+            if c["flop"]:
+                tf = B * c["flop"] / t / 1e12
+                r["in_pipeline_tflops"] = tf
+                if c["bound"] == "ffma":
+                    r["in_pipeline_ffma_frac"] = tf / (p * 128 * 2 * sm_mhz * 1e6 / 1e12)
+                else:
+                    r["in_pipeline_tensor_frac_of_sm_share"] = tf / (peaks.get("bf16_tflops", 1800.0) * p / sm_count)
         out.append(r)
     return out
 
@@ -738,7 +754,8 @@ def measure_workload(name, args, local, headline: bool):
         out["main_alloc"] = {"instances": main_alloc[0], "sm_quota": main_alloc[1]}
         sm_mhz = _peaks().get("sm_max_mhz", 2032.0)
         out["stage_roofline"] = {
-            tag: stage_roofline(name, levels, dur, a[0], a[1], wl.sms, sm_mhz)
+            tag: stage_roofline(name, levels, dur, a[0], a[1], wl.sms, sm_mhz,
+                                t_in if list(a[1]) == list(quota_s) else None)
             for tag, a in (("main_alloc", main_alloc), ("other_alloc", other_alloc))
             if all(q in levels for q in a[1])}
         out["global"] = res[("main", 0)]
@@ -1608,12 +1625,16 @@ def run_stage_case(args):
     """Small self-contained case for ncu: one stage of a workload run alone by
     direct launches (camelot_stage_launch) on --ctas SMs over one batch of
     --batch queries (default: the workload's batch), three times."""
-    wl = Workload(args.workload, 0, n_rows=256)
+    wl = Workload(args.workload, 0, n_rows=256, device_rows=8192 if args.cold else 0)
     torch, cm = wl.torch, wl.cm
     si = args.stage
     B = args.batch or wl.B
     st = wl.stages[si]
     ins = [wl.xq] + [torch.zeros(B * nb, dtype=torch.uint8, device="cuda") for (nb, _) in wl.io[1:]]
+    if args.cold and si == 0:
+        # each launch reads its batch from rows no earlier launch touched (from
+        # HBM, as in a pipeline replaying a long trace), not from L2
+        ins[0] = [wl.xq[(2048 * i) % 8192:(2048 * i) % 8192 + B] for i in range(3)]
     last = si == len(wl.stages) - 1
     out = None if last else torch.zeros(B * wl.io[si + 1][0], dtype=torch.uint8, device="cuda")
     idx = torch.empty((B, 5), dtype=torch.int32, device="cuda")
@@ -1623,7 +1644,8 @@ def run_stage_case(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for i in range(3):
         ev[i].record()
-        cm.camelot_stage_launch(st, args.ctas, ins[si], B, out, idx if last else None, val if last else None,
+        inp = ins[si][i] if isinstance(ins[si], list) else ins[si]
+        cm.camelot_stage_launch(st, args.ctas, inp, B, out, idx if last else None, val if last else None,
                                 None, scr, sb, None)
     ev[3].record()
     torch.cuda.synchronize()
@@ -1697,6 +1719,7 @@ def main():
     ap.add_argument("--stage", type=int, default=1)
     ap.add_argument("--ctas", type=int, default=8)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--cold", action="store_true", help="--stage-case: stage-0 inputs from HBM, not L2")
     ap.add_argument("--mlp-layers", action="store_true",
                     help="time the FP32 MLP stage and its layers by direct launches at --ctas-list SM quotas")
     ap.add_argument("--ctas-list", default="8,16,72,144")

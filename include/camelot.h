@@ -512,6 +512,10 @@ typedef struct {
                                                and output slots) to the batch published, so
                                                busy_ns / batches is the in-pipeline service time
                                                of one batch, hand-over included              */
+    uint64_t body_ns[CAMELOT_MAX_STAGES];   /* per stage, summed over its batches: the time the
+                                               instance's first CTA spent in the stage's own
+                                               computation (busy_ns - body_ns is the batch
+                                               protocol and the wait for the other CTAs)    */
 } camelot_stats;
 
 camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);

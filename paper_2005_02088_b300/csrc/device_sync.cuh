@@ -38,6 +38,8 @@ struct alignas(128) Ctl {
     Line64 batches[8];               // batches finished by stage s (statistics)
     Line64 busy_ns[8];               // stage s: summed over its batches, the time from the
                                      // instance holding its work to the batch published
+    Line64 body_ns[8];               // stage s: summed over its batches, the time the
+                                     // leader CTA spent in the stage body itself
 };
 
 // Flags the host writes and the device reads (pinned, mapped host memory).

@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                     RowRef{reinterpret_cast<char*>(P.sink), first, P.cmask, P.sink_ld * sizeof(float)}};
         if (P.sink == nullptr) fo.logits.base = nullptr;
 
+        const uint64_t t_body = leader && threadIdx.x == 0 ? gtime() : 0;
         if (!stage_body<KINDS>(cx, SP, in, n, out, fo)) break;
+        if (leader && threadIdx.x == 0) atomicAdd(&P.ctl->body_ns[s].v, (unsigned long long)(gtime() - t_body));
 
         // ---- end of the batch: the other CTAs report, the leader collects
         __syncthreads();
