@@ -120,6 +120,19 @@ def _peaks():
         return {}
 
 
+def in_pipeline_times(s0, s1, n):
+    """Each stage's service time per batch inside the pipeline (s), from two
+    camelot_stats taken around a saturated trace: the time from holding a
+    batch's work to its publication (busy_ns / batches) plus the per-batch
+    cost of finding the work.  That cost is the smallest acquisition time of
+    any stage: stage 0 of a saturated trace never waits for arrivals, while a
+    later stage's acquisition time also holds its waits for upstream batches."""
+    nb = [max(1, s1.batches[i] - s0.batches[i]) for i in range(n)]
+    busy = [(s1.busy_ns[i] - s0.busy_ns[i]) / nb[i] * 1e-9 for i in range(n)]
+    acq = min((s1.acquire_ns[i] - s0.acquire_ns[i]) / nb[i] * 1e-9 for i in range(n))
+    return [b + acq for b in busy]
+
+
 def stage_roofline(name, levels, dur, inst, quota, sm_count, sm_mhz, in_pipeline_s=None):
     """Each stage's achieved fraction of its roofline at the allocated quota,
     from the solo profile (one batch of B on p SMs, CUDA events around direct
@@ -648,9 +661,9 @@ class Workload:
     def handover(self, inst, quota, dur_at, batch=0):
         """Per-batch hand-over time of every stage inside the pipeline (s): one
         saturated trace on the allocation; the in-pipeline service time per
-        batch (camelot_stats.busy_ns / batches) minus the stage's solo duration
-        at its quota (negative where the solo time's launch overhead exceeds
-        the hand-over).  Returns (hand-over s, in-pipeline s, saturation q/s)."""
+        batch (in_pipeline_times) minus the stage's solo duration at its quota
+        (negative where the solo time's launch overhead exceeds the hand-over).
+        Returns (hand-over s, in-pipeline s, saturation q/s)."""
         cm = self.cm
         n = len(self.stages)
         p = self.pipeline(0, inst, quota, batch=batch)
@@ -660,7 +673,7 @@ class Workload:
             s1 = cm.camelot_pipeline_stats(p)
         finally:
             cm.camelot_pipeline_destroy(p)
-        t_in = [(s1.busy_ns[i] - s0.busy_ns[i]) / max(1, s1.batches[i] - s0.batches[i]) * 1e-9 for i in range(n)]
+        t_in = in_pipeline_times(s0, s1, n)
         return [t_in[i] - dur_at[i] for i in range(n)], t_in, Q_STEP / (ms * 1e-3)
 
     def simulated(self, levels, dur, inst, quota, handover, rate):
@@ -1406,8 +1419,7 @@ def run_artifact(args):
                 del data
             finally:
                 cm.camelot_pipeline_destroy(p)
-            t_in = [(s1.busy_ns[i] - s0.busy_ns[i]) / max(1, s1.batches[i] - s0.batches[i]) * 1e-9
-                    for i in range(len(names))]
+            t_in = in_pipeline_times(s0, s1, len(names))
             return [t_in[i] - float(dur[k][quota[i] // 8 - 1]) for i, k in enumerate(names)]
 
         def measure(names, inst, quota, lam):

@@ -516,6 +516,11 @@ typedef struct {
                                                instance's first CTA spent in the stage's own
                                                computation (busy_ns - body_ns is the batch
                                                protocol and the wait for the other CTAs)    */
+    uint64_t acquire_ns[CAMELOT_MAX_STAGES];/* per stage, summed over its batches: the time its
+                                               instances' leaders spent finding a batch's work
+                                               (for stage 0 the batch trigger, which includes
+                                               waiting for arrivals; for later stages waiting
+                                               for a published input batch)                  */
 } camelot_stats;
 
 camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_stats* out);
@@ -702,9 +707,10 @@ camelot_status camelot_trigger_latency(const camelot_profile* prof, const camelo
  * timed alone by separate launches: the batch's work is acquired from a ring,
  * posted to the instance's CTAs, counted back and published, co-located
  * stages share the memory system, and no launch overhead is paid.  With
- * handover_s[i] the measured difference for stage i (camelot_stats.busy_ns /
- * batches in a pipeline minus the solo duration at the same quota; it may be
- * negative), every entry becomes d' = d + handover_s[i], f' = B / d',
+ * handover_s[i] the measured difference for stage i (its service time per
+ * batch in a saturated pipeline -- camelot_stats.busy_ns / batches plus the
+ * per-batch acquisition cost -- minus the solo duration at the same quota; it
+ * may be negative), every entry becomes d' = d + handover_s[i], f' = B / d',
  * bandwidth' = bandwidth d / d' (the same bytes in the new time).  Outputs are
  * arrays shaped like the profile's (they may be the profile's own).
  * Host-only.  Errors: EINVAL (also when a corrected duration is not > 0). */

@@ -72,7 +72,7 @@ class Stats(C.Structure):
                 ("device_ring_bytes", C.c_uint64), ("device_status", C.c_int32),
                 ("device_where", C.c_int32), ("last_launch_ms", C.c_double),
                 ("total_launch_ms", C.c_double), ("busy_ns", C.c_uint64 * MAX_STAGES),
-                ("body_ns", C.c_uint64 * MAX_STAGES)]
+                ("body_ns", C.c_uint64 * MAX_STAGES), ("acquire_ns", C.c_uint64 * MAX_STAGES)]
 
 
 class ServerOptions(C.Structure):

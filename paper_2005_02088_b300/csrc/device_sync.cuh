@@ -40,6 +40,8 @@ struct alignas(128) Ctl {
                                      // instance holding its work to the batch published
     Line64 body_ns[8];               // stage s: summed over its batches, the time the
                                      // leader CTA spent in the stage body itself
+    Line64 acq_ns[8];                // stage s: summed over its batches, the time its
+                                     // leaders spent finding each batch's work
 };
 
 // Flags the host writes and the device reads (pinned, mapped host memory).

@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                 unsigned long long in_t = 0, first = 0, out_t = 0;
                 bool tr = false;
                 long long tb = 0;
+                const uint64_t t_acq = gtime();
                 if (s == 0) {
                     cmd = stage0_acquire(P, ls, &first, &n, &tr, &tb);
                     in_t = first;
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                     cmd = __shfl_sync(0xffffffffu, cmd, 0);
                 }
                 if (threadIdx.x == 0) {
+                    if (cmd == CMD_WORK) atomicAdd(&P.ctl->acq_ns[s].v, (unsigned long long)(gtime() - t_acq));
                     if (cmd == CMD_WORK && !final_stage && !reserve_out(P, P.out_ring[s], s, &out_t))
                         cmd = CMD_EXIT;
                     sh_t_work = gtime();

@@ -1219,6 +1219,9 @@ extern "C" camelot_status camelot_pipeline_stats(camelot_pipeline* p, camelot_st
     CUDA_TRY(cudaMemcpyAsync(b, &p->ctl->body_ns[0], sizeof b, cudaMemcpyDeviceToHost, p->side));
     CUDA_TRY(cudaStreamSynchronize(p->side));
     for (int s = 0; s < kMaxStages; ++s) out->body_ns[s] = b[s].v;
+    CUDA_TRY(cudaMemcpyAsync(b, &p->ctl->acq_ns[0], sizeof b, cudaMemcpyDeviceToHost, p->side));
+    CUDA_TRY(cudaStreamSynchronize(p->side));
+    for (int s = 0; s < kMaxStages; ++s) out->acquire_ns[s] = b[s].v;
     out->kernel_launches = p->launches;
     out->relayed_bytes = p->relayed_bytes.load();
     size_t slot = 0, ring = 0;
