@@ -609,14 +609,40 @@ class Workload:
                 seen.add(key)
                 uniq.append((c, q))
         table = []
-        for c, q in uniq:
+
+        def measure(c, q):
             p = self.pipeline(0, c, q)
             try:
                 _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
-                table.append({"instances": c, "sm_quota": q, "saturation_qps": Q_STEP / (ms * 1e-3)})
+                table.append({"instances": list(c), "sm_quota": list(q), "saturation_qps": Q_STEP / (ms * 1e-3)})
             finally:
                 self.cm.camelot_pipeline_destroy(p)
+            return table[-1]
+
+        for c, q in uniq:
+            measure(c, q)
         best = max(table, key=lambda r: r["saturation_qps"])
+        # SMs the allocation leaves idle (the bandwidth constraint counts every
+        # instance's weight reads as HBM traffic, though the instances share
+        # them through L2): add one instance at a time where it measures best
+        budget = (self.sms // 8) * 8
+        while True:
+            used = sum(a * b for a, b in zip(best["instances"], best["sm_quota"]))
+            cands = []
+            for i in range(n):
+                if used + best["sm_quota"][i] <= budget:
+                    c = list(best["instances"])
+                    c[i] += 1
+                    key = (tuple(c), tuple(best["sm_quota"]))
+                    if key not in seen:
+                        seen.add(key)
+                        cands.append(measure(c, best["sm_quota"]))
+            if not cands:
+                break
+            top = max(cands, key=lambda r: r["saturation_qps"])
+            if top["saturation_qps"] <= best["saturation_qps"]:
+                break
+            best = top
         return best["instances"], best["sm_quota"], table
 
     def costs(self):

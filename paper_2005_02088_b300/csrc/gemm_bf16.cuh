@@ -247,9 +247,23 @@ __device__ __forceinline__ bool for_each_stage(int u0, int u1, uint32_t ring0, I
     return true;
 }
 
+// A layer of exactly two K-chunks whose units pair up inside every CTA: each
+// CTA's units start at an even unit and come in an even number, and units are
+// then ordered chunk-minor, so that the pair (2i, 2i + 1) is chunks 0 and 1 of
+// one weight tile, run by the CTA's two issuers into two accumulators.  The
+// epilogue adds the pair itself, (0 + p0) + p1 in f32 as the reduce pass would,
+// so the layer writes no partials and needs no reduce pass: the result is the
+// same bits as the unpaired path's.
+__device__ __forceinline__ bool gemm_pairs_fused(const LayerParams& L, int rows, int nctas, int nt) {
+    if (L.C != 2) return false;
+    const int U = (L.Npad / 128) * 2 * ((rows + nt - 1) / nt);
+    return (U / 2) % nctas == 0;
+}
+
 // One layer over `rows` input rows (queries, or tokens of a token-level
 // stage), taken 32 at a time.  Work units u = (row tile rt, chunk c, 128-row
-// weight tile mt) in that order (u = (rt * C + c) * MT + mt); CTA r takes the
+// weight tile mt) in that order (u = (rt * C + c) * MT + mt; in a layer whose
+// chunk pairs are fused, u = (rt * MT + mt) * 2 + c); CTA r takes the
 // contiguous units [r U / p, (r+1) U / p).
 // Every unit accumulates the same K range in the same MMA order, issued by
 // one thread into one accumulator, whichever CTA or issuer runs it.  Each ring
@@ -295,11 +309,12 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
     constexpr int esz = ESZ;
     auto chunk_kb = [=](int c) { return min(KC, K - c * KC) * esz / 128; };
     const size_t kc_bytes = (size_t)KC * esz;
+    const bool fused = gemm_pairs_fused(L, rows, cx.nctas, NT);
     auto info = [=](int u) {
         UnitInfo ui;
         const int rt = u / CM, v = u - rt * CM;
-        ui.c = v / MT;
-        ui.mt = v - ui.c * MT;
+        ui.c = fused ? (v & 1) : v / MT;
+        ui.mt = fused ? (v >> 1) : v - ui.c * MT;
         ui.row0 = rt * kGemmN;
         ui.nkb = chunk_kb(ui.c);
         ui.ns = (ui.nkb + kKbPerStage - 1) / kKbPerStage;
@@ -402,30 +417,54 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             uint32_t kw[kIssuers];
 #pragma unroll
             for (int w = 0; w < kIssuers; ++w) kw[w] = accb[w];
-            for (int u = u0; u < u1; ++u) {
+            // a fused pair: issuer 0's accumulator holds chunk 0, issuer 1's chunk 1
+            for (int u = u0; u < u1; u += fused ? 2 : 1) {
                 const int w = (u - u0) & 1;
                 const uint32_t k = kw[w]++;
+                const uint32_t k1 = fused ? kw[1]++ : 0u;
                 const UnitInfo ui = info(u);
                 const int c = ui.c, mt = ui.mt, row0 = ui.row0;
-                const int acc = acc_of(w, k);
+                const int acc = acc_of(w, k), acc1 = acc_of(1, k1);
                 if (!mbar_wait_bounded(&g.tfull[acc], (k >> 1) & 1, cx, 6)) break;
+                if (fused && !mbar_wait_bounded(&g.tfull[acc1], (k1 >> 1) & 1, cx, 6)) break;
                 tc_fence_after();
                 const int m = mt * 128 + 32 * sub + lane;
 #pragma unroll 1
                 for (int q0 = 0; q0 < NT; q0 += 32) {
                     uint32_t r0[16], r1[16];
                     const uint32_t ta = tmem + ((uint32_t)(32 * sub) << 16) + acc * NT + q0;
-                    tmem_ld16(ta, r0);
-                    tmem_ld16(ta + 16, r1);
-                    tmem_ld_wait();
-                    if (q0 + 32 >= NT) {           // the accumulator has been read out
+                    if (fused) {
+                        // (0 + p0) + p1, each addition rounded once, as the reduce pass adds
+                        const uint32_t tb = tmem + ((uint32_t)(32 * sub) << 16) + acc1 * NT + q0;
+                        uint32_t t[16];
+                        tmem_ld16(ta, r0);
+                        tmem_ld16(tb, t);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            r0[i] = __float_as_uint(__fadd_rn(__fadd_rn(0.f, __uint_as_float(r0[i])), __uint_as_float(t[i])));
+                        tmem_ld16(ta + 16, r1);
+                        tmem_ld16(tb + 16, t);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            r1[i] = __float_as_uint(__fadd_rn(__fadd_rn(0.f, __uint_as_float(r1[i])), __uint_as_float(t[i])));
+                    } else {
+                        tmem_ld16(ta, r0);
+                        tmem_ld16(ta + 16, r1);
+                        tmem_ld_wait();
+                    }
+                    if (q0 + 32 >= NT) {           // the accumulator(s) have been read out
                         tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&g.tfree[acc]);
+                        if (lane == 0) {
+                            mbar_arrive(&g.tfree[acc]);
+                            if (fused) mbar_arrive(&g.tfree[acc1]);
+                        }
                     }
                     const int jn = min(32, rows - (row0 + q0));   // real rows of this block
                     if (jn > 0) {   // (warp-uniform)
-                        if (C > 1) {
+                        if (C > 1 && !fused) {
                             if (m < N) epi_partials(Pbuf + ((size_t)c * rows + row0 + q0) * Npad + m, Npad, r0, r1, jn);
                         } else {
                             epi_direct(direct, row0 + q0, m, N, r0, r1, jn, g.stage_out + sub * kEpiStageBytes);
@@ -435,7 +474,7 @@ static __device__ bool gemm_layer_tasks(const StageCtx& cx, const LayerParams& L
             }
         }
     }
-    // direct (C == 1) outputs may be the next layer's bulk-copied operand
+    // direct (C == 1 or fused) outputs may be the next layer's bulk-copied operand
     fence_proxy_async_global();
     __syncthreads();
     if (threadIdx.x == 0 && u0 < u1) {
@@ -578,7 +617,7 @@ static __device__ bool gemm_body_nt(const StageCtx& cx, const StageParams& P, Ro
                                    : gemm_layer_tasks<2, NT>(cx, L, xt, rows, Pbuf, o);
         if (!ok) return false;
         if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
-        if (L.C > 1) {
+        if (L.C > 1 && !gemm_pairs_fused(L, rows, cx.nctas, NT)) {
             gemm_reduce(cx, L, rows, Pbuf, o);
             if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         }

@@ -103,16 +103,20 @@ static void stage_free(camelot_stage* st) {
 }
 
 // K-chunk of a tensor-core layer with MT 128-row weight tiles: the whole K up
-// to 1024 columns (one chunk: no partial sums and no reduce pass); for long K,
-// as few equal chunks as give about 64 units per row tile (MT x chunks), at
-// most one per 1024 columns, rounded up to 128 columns (whole 128-byte
-// k-blocks for bf16 and e4m3 alike).  Fewer, longer chunks mean fewer chunk
-// partials to write and add (37632 columns: 8 chunks of 4736 instead of 37 of
-// 1024, 15 % less time per batch of the stage in the pipeline), while 64
-// units still spread over the widest instances the allocator picks.
+// to 1024 columns (one chunk: no partial sums and no reduce pass).  For long K
+// and 8 or more row tiles, two chunks: 2 MT units per row tile of queries,
+// which pair up inside each CTA when the instance's CTA count divides MT times
+// the row tiles (chunks 0 and 1 of a weight tile on the CTA's two issuers,
+// added in its epilogue), so the layer writes no partials and runs no reduce
+// pass (37632 -> 1024 at batch 32 on 8 SMs: saves
+// the ~10 us reduce pass of a ~144 us batch); one chunk would leave one issuer
+// of each CTA idle and run a single accumulator chain.  Fewer row tiles: as
+// few equal chunks as give about 64 units, at most one per 1024 columns.
+// Chunks are rounded up to 128 columns (whole 128-byte k-blocks for bf16 and
+// e4m3 alike).
 static int choose_kc_gemm(int K, int MT) {
     if (K <= 1024) return K;
-    const int C = std::max(1, std::min((K + 1023) / 1024, (64 + MT - 1) / MT));
+    const int C = MT >= 8 ? 2 : std::max(1, std::min((K + 1023) / 1024, (64 + MT - 1) / MT));
     return ((K + C - 1) / C + 127) / 128 * 128;
 }
 

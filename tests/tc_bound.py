@@ -30,12 +30,13 @@ C_MMA = {16: 36.0, 32: 68.0}
 
 def chunk_cols(K: int, N: int) -> int:
     """The K-chunk the stage uses for a layer of N outputs: the whole K up to
-    1024 columns, else as few equal chunks (rounded up to 128 columns) as give
-    about 64 units of 128 output rows, at most one per 1024 columns."""
+    1024 columns; else two chunks for 8 or more tiles of 128 output rows, and
+    for fewer as few equal chunks as give about 64 units of 128 output rows, at
+    most one per 1024 columns; chunks rounded up to 128 columns."""
     if K <= 1024:
         return K
     mt = (N + 127) // 128
-    c = max(1, min((K + 1023) // 1024, (64 + mt - 1) // mt))
+    c = 2 if mt >= 8 else max(1, min((K + 1023) // 1024, (64 + mt - 1) // mt))
     return ((K + c - 1) // c + 127) // 128 * 128
 
 
