@@ -657,13 +657,16 @@ static __device__ void topk_rows(const StageCtx& cx, RowRef z, int n, int N, int
                     if (j >= je) break;
                     const float v = vv[u];
                     if (fo.logits.base != nullptr) reinterpret_cast<float*>(fo.logits.row(q))[j] = v;
-                    // insert (v, j): j grows along the lane's scan, so ties keep the earlier index first
-                    if (v > bv[k - 1] || bi[k - 1] == 0x7fffffff) {
+                    // insert (v, j) into the lane's top kMaxTopK (a superset of its
+                    // top k; indexes known at compile time keep the list in
+                    // registers): j grows along the lane's scan, so ties keep the
+                    // earlier index first
+                    if (v > bv[kMaxTopK - 1] || bi[kMaxTopK - 1] == 0x7fffffff) {
                         float cv = v;
                         int ci = j;
 #pragma unroll
                         for (int r = 0; r < kMaxTopK; ++r) {
-                            if (r < k && (cv > bv[r] || bi[r] == 0x7fffffff)) {
+                            if (cv > bv[r] || bi[r] == 0x7fffffff) {
                                 const float tv = bv[r];
                                 const int ti = bi[r];
                                 bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
