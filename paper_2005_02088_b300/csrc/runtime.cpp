@@ -102,21 +102,23 @@ static void stage_free(camelot_stage* st) {
     delete st;
 }
 
-// K-chunk of a tensor-core layer with MT 128-row weight tiles: the whole K up
-// to 1024 columns (one chunk: no partial sums and no reduce pass).  For long K
-// and 8 or more row tiles, two chunks: 2 MT units per row tile of queries,
+// K-chunk of a tensor-core layer with MT 128-row weight tiles.  With 8 or more
+// row tiles and K >= 512, two chunks: 2 MT units per row tile of queries,
 // which pair up inside each CTA when the instance's CTA count divides MT times
 // the row tiles (chunks 0 and 1 of a weight tile on the CTA's two issuers,
 // added in its epilogue), so the layer writes no partials and runs no reduce
 // pass (37632 -> 1024 at batch 32 on 8 SMs: saves
 // the ~10 us reduce pass of a ~144 us batch); one chunk would leave one issuer
-// of each CTA idle and run a single accumulator chain.  Fewer row tiles: as
-// few equal chunks as give about 64 units, at most one per 1024 columns.
+// of each CTA idle and run a single accumulator chain (1024 -> 1024 and
+// 1024 -> 1000 at batch 32 on 8 SMs: ~2 us less per layer of ~8-10 us).  Fewer row tiles: the whole
+// K up to 1024 columns (one chunk: no partial sums and no reduce pass), above
+// that as few equal chunks as give about 64 units, at most one per 1024 columns.
 // Chunks are rounded up to 128 columns (whole 128-byte k-blocks for bf16 and
 // e4m3 alike).
 static int choose_kc_gemm(int K, int MT) {
+    if (MT >= 8 && K >= 512) return ((K + 1) / 2 + 127) / 128 * 128;
     if (K <= 1024) return K;
-    const int C = MT >= 8 ? 2 : std::max(1, std::min((K + 1023) / 1024, (64 + MT - 1) / MT));
+    const int C = std::max(1, std::min((K + 1023) / 1024, (64 + MT - 1) / MT));
     return ((K + C - 1) / C + 127) / 128 * 128;
 }
 

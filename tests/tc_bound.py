@@ -29,14 +29,17 @@ C_MMA = {16: 36.0, 32: 68.0}
 
 
 def chunk_cols(K: int, N: int) -> int:
-    """The K-chunk the stage uses for a layer of N outputs: the whole K up to
-    1024 columns; else two chunks for 8 or more tiles of 128 output rows, and
-    for fewer as few equal chunks as give about 64 units of 128 output rows, at
-    most one per 1024 columns; chunks rounded up to 128 columns."""
+    """The K-chunk the stage uses for a layer of N outputs: two chunks for 8 or
+    more tiles of 128 output rows and K >= 512; otherwise the whole K up to 1024
+    columns, above that as few equal chunks as give about 64 units of 128
+    output rows, at most one per 1024 columns; chunks rounded up to 128
+    columns."""
+    mt = (N + 127) // 128
+    if mt >= 8 and K >= 512:
+        return ((K + 1) // 2 + 127) // 128 * 128
     if K <= 1024:
         return K
-    mt = (N + 127) // 128
-    c = 2 if mt >= 8 else max(1, min((K + 1023) // 1024, (64 + mt - 1) // mt))
+    c = max(1, min((K + 1023) // 1024, (64 + mt - 1) // mt))
     return ((K + c - 1) // c + 127) // 128 * 128
 
 
