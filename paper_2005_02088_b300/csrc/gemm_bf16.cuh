@@ -581,6 +581,200 @@ __device__ __forceinline__ RowRef token_rows(const RowRef& q, int T) {
     return RowRef{q.base + q.first * q.stride, 0, ~0ull, q.stride / (size_t)T};
 }
 
+// Top-k of a final query stage (32-row tiles) whose last layer leaves each of
+// its 128-logit weight tiles complete in one CTA (one K-chunk, or fused chunk
+// pairs): each CTA reduces its own tiles to k candidates per query right after
+// its epilogue (no group barrier between the layer and the top-k), and the
+// candidates are merged afterwards: by the pipeline's leader once the other
+// CTAs have reported, or after one group barrier in a direct launch.  The
+// order is total (value descending, index ascending), so the result is the
+// row-wise top-k's.
+__device__ __forceinline__ bool gemm_topk_cands(const StageParams& P, int rows, int nctas) {
+    const LayerParams& L = P.layer[P.n_layers - 1];
+    return P.top_k > 0 && P.rows <= 1 && P.tile_h == 32 && (L.C == 1 || gemm_pairs_fused(L, rows, nctas, 32));
+}
+
+// Candidate (value bits, index) of query q, tile mt, rank r.
+__device__ __forceinline__ int2* gemm_cand(const StageCtx& cx, const StageParams& P, int q, int mt, int r) {
+    const int MT = P.layer[P.n_layers - 1].Npad / 128;
+    return reinterpret_cast<int2*>(cx.scratch + P.cand_off) + ((size_t)q * MT + mt) * kMaxTopK + r;
+}
+
+// Warp-wide best of four independent (value, index) pairs at once (value
+// descending, index ascending on ties): the four shuffle chains interleave.
+__device__ __forceinline__ void warp_best4(float (&v)[4], int (&i)[4]) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        float ov[4];
+        int oi[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            ov[g] = __shfl_xor_sync(0xffffffffu, v[g], off);
+            oi[g] = __shfl_xor_sync(0xffffffffu, i[g], off);
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (ov[g] > v[g] || (ov[g] == v[g] && oi[g] < i[g])) { v[g] = ov[g]; i[g] = oi[g]; }
+    }
+}
+
+// This CTA's tiles (the tiles of its units, in the unit order of
+// gemm_layer_tasks): warp w takes queries w, w + 8, w + 16, w + 24 of a 32-row
+// tile together (four logits per lane and query, all loads in flight at once),
+// then k rounds of warp-wide best.  The logits rows are copied to the sink on
+// the way.
+static __device__ void gemm_tile_cands(const StageCtx& cx, const StageParams& P, RowRef z, int n,
+                                       const FinalOut& fo) {
+    const LayerParams& L = P.layer[P.n_layers - 1];
+    const int MT = L.Npad / 128, k = P.top_k;
+    const int per = L.C == 1 ? 1 : 2;                     // units per tile
+    const int U = MT * per * ((n + 31) / 32);
+    const int u0 = (int)((long long)cx.rank * U / cx.nctas);
+    const int u1 = (int)((long long)(cx.rank + 1) * U / cx.nctas);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    static_assert(kWarps * 4 == 32, "four queries per warp cover a 32-row tile");
+    for (int t = u0 / per; t < u1 / per; ++t) {
+        const int rt = t / MT, mt = t - rt * MT;
+        float v[4][4];
+        int ix[4][4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int q = rt * 32 + warp + kWarps * g;
+            const float* zr = q < n ? reinterpret_cast<const float*>(z.row(q)) : nullptr;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m = mt * 128 + 32 * j + lane;
+                const bool ok = zr != nullptr && m < L.N;
+                v[g][j] = ok ? __ldcg(zr + m) : -INFINITY;
+                ix[g][j] = ok ? m : 0x7fffffff;
+            }
+        }
+        if (fo.logits.base != nullptr) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int q = rt * 32 + warp + kWarps * g;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (q < n && ix[g][j] != 0x7fffffff) reinterpret_cast<float*>(fo.logits.row(q))[ix[g][j]] = v[g][j];
+            }
+        }
+        for (int r = 0; r < k; ++r) {
+            float bv[4];
+            int bi[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                bv[g] = v[g][0];
+                bi[g] = ix[g][0];
+#pragma unroll
+                for (int j = 1; j < 4; ++j)
+                    if (v[g][j] > bv[g] || (v[g][j] == bv[g] && ix[g][j] < bi[g])) { bv[g] = v[g][j]; bi[g] = ix[g][j]; }
+            }
+            warp_best4(bv, bi);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int q = rt * 32 + warp + kWarps * g;
+                if (lane == 0 && q < n) *gemm_cand(cx, P, q, mt, r) = make_int2(__float_as_int(bv[g]), bi[g]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (ix[g][j] == bi[g]) { v[g][j] = -INFINITY; ix[g][j] = 0x7fffffff; }
+            }
+        }
+    }
+}
+
+// Merge of the candidates into the final top-k of queries first_q + w,
+// first_q + w + q_stride, ... (w the warp; `first_q` counts the calling CTA's
+// warps), four queries per warp at once.  A lane takes candidates lane and
+// lane + 32 of each (at most 64: MT k <= 64) or scans lane, lane + 32, ... (a
+// query at a time) for wider layers, in (tile, rank) order, which for equal
+// values is index order, into its sorted top kMaxTopK.
+__device__ __forceinline__ void cand_insert(float (&bv)[kMaxTopK], int (&bi)[kMaxTopK], float cv, int ci) {
+    if (cv > bv[kMaxTopK - 1] || bi[kMaxTopK - 1] == 0x7fffffff) {
+#pragma unroll
+        for (int r = 0; r < kMaxTopK; ++r) {
+            if (cv > bv[r] || bi[r] == 0x7fffffff) {
+                const float tv = bv[r];
+                const int ti = bi[r];
+                bv[r] = cv; bi[r] = ci; cv = tv; ci = ti;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void cand_pop(float (&bv)[kMaxTopK], int (&bi)[kMaxTopK]) {
+#pragma unroll
+    for (int t = 0; t + 1 < kMaxTopK; ++t) { bv[t] = bv[t + 1]; bi[t] = bi[t + 1]; }
+    bv[kMaxTopK - 1] = -INFINITY;
+    bi[kMaxTopK - 1] = 0x7fffffff;
+}
+
+static __device__ void gemm_cand_merge(const StageCtx& cx, const StageParams& P, int n, const FinalOut& fo,
+                                       int first_q, int q_stride) {
+    const int MT = P.layer[P.n_layers - 1].Npad / 128, k = P.top_k, NC = MT * k;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (NC <= 64) {
+        for (int q0 = first_q + warp; q0 < n; q0 += 4 * q_stride) {
+            int2 e[4][2];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int q = q0 + g * q_stride;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h, mt = c / k;
+                    e[g][h] = (q < n && c < NC) ? __ldcg(gemm_cand(cx, P, q, mt, c - mt * k))
+                                                : make_int2(__float_as_int(-INFINITY), 0x7fffffff);
+                }
+            }
+            float bv[4][kMaxTopK];
+            int bi[4][kMaxTopK];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+#pragma unroll
+                for (int r = 0; r < kMaxTopK; ++r) { bv[g][r] = -INFINITY; bi[g][r] = 0x7fffffff; }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) cand_insert(bv[g], bi[g], __int_as_float(e[g][h].x), e[g][h].y);
+            }
+            for (int r = 0; r < k; ++r) {
+                float v[4];
+                int i[4];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) { v[g] = bv[g][0]; i[g] = bi[g][0]; }
+                warp_best4(v, i);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int q = q0 + g * q_stride;
+                    if (lane == 0 && q < n) {
+                        fo.idx[(size_t)q * k + r] = i[g];
+                        fo.val[(size_t)q * k + r] = v[g];
+                    }
+                    if (bi[g][0] == i[g]) cand_pop(bv[g], bi[g]);
+                }
+            }
+        }
+        return;
+    }
+    for (int q = first_q + warp; q < n; q += q_stride) {
+        float bv[kMaxTopK];
+        int bi[kMaxTopK];
+#pragma unroll
+        for (int r = 0; r < kMaxTopK; ++r) { bv[r] = -INFINITY; bi[r] = 0x7fffffff; }
+        for (int c = lane; c < NC; c += 32) {
+            const int mt = c / k;
+            const int2 e = __ldcg(gemm_cand(cx, P, q, mt, c - mt * k));
+            cand_insert(bv, bi, __int_as_float(e.x), e.y);
+        }
+        for (int r = 0; r < k; ++r) {
+            float v = bv[0];
+            int i = bi[0];
+            warp_best(v, i);
+            if (lane == 0) {
+                fo.idx[(size_t)q * k + r] = i;
+                fo.val[(size_t)q * k + r] = v;
+            }
+            if (bi[0] == i) cand_pop(bv, bi);
+        }
+    }
+}
+
 template <int NT>
 static __device__ bool gemm_body_nt(const StageCtx& cx, const StageParams& P, RowRef in, int n,
                                     RowRef out, const FinalOut& fo) {
@@ -616,6 +810,13 @@ static __device__ bool gemm_body_nt(const StageCtx& cx, const StageParams& P, Ro
         const bool ok = L.esz == 1 ? gemm_layer_tasks<1, NT>(cx, L, xt, rows, Pbuf, o)
                                    : gemm_layer_tasks<2, NT>(cx, L, xt, rows, Pbuf, o);
         if (!ok) return false;
+        if (last && NT == 32 && gemm_topk_cands(P, rows, cx.nctas)) {
+            gemm_tile_cands(cx, P, o.rows, n, fo);
+            if (cx.defer_topk) return true;            // the pipeline's leader merges
+            if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
+            gemm_cand_merge(cx, P, n, fo, cx.rank * kWarps, cx.nctas * kWarps);
+            return true;
+        }
         if (!group_barrier(cx.gs, cx.nctas, cx.ctl, cx.limit_ns, cx.where)) return false;
         if (L.C > 1 && !gemm_pairs_fused(L, rows, cx.nctas, NT)) {
             gemm_reduce(cx, L, rows, Pbuf, o);

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
                 reinterpret_cast<float*>(smem4)};
     const StageParams& SP = P.st[s];
     const bool final_stage = (s == P.n_stages - 1);
+    cx.defer_topk = final_stage;
     const bool leader = (rank == 0);
 
     __shared__ unsigned int sh_cmd, sh_n, sh_trace, sh_ok;
@@ -315,6 +316,11 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
         if (!sh_ok) break;
 
         // ---- the leader publishes the result and releases the input
+        if (final_stage && cx.defer_topk && tensor_stage && gemm_topk_cands(SP, n, cx.nctas)) {
+            // the top-k candidates of every CTA are in (their done counts ordered them)
+            gemm_cand_merge(cx, SP, n, fo, 0, kWarps);
+            __syncthreads();
+        }
         if (final_stage) {
             // completion records: data and flag in every 8-byte word (no
             // system-scope fence); the logits rows are ordered before them

@@ -163,6 +163,9 @@ static size_t layout_scratch(StageParams& sp, int B) {
     off = align_up(off + (size_t)B * kMaxTopK * 8, 256);
     sp.tile_off = off;
     off = align_up(off + t_bytes, 256);
+    sp.cand_off = off;
+    if (is_tensor_kind(sp.kind) && sp.top_k > 0 && sp.n_layers > 0)
+        off = align_up(off + (size_t)B * (sp.layer[sp.n_layers - 1].Npad / 128) * kMaxTopK * 8, 256);
     return off;
 }
 

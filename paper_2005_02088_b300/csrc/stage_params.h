@@ -78,6 +78,8 @@ struct StageParams {
     size_t scratch_bytes;   // per instance (for max_batch)
     size_t res_off;         // scratch offset of final results: idx [B][5] int32, val [B][5] f32
     size_t tile_off;        // tensor-core kinds: scratch offset of a layer's input in tiled form
+    size_t cand_off;        // final tensor-core kinds: scratch offset of the top-k candidates,
+                            // (value bits, index) int32 pairs [rows][last layer's 128-row tiles][kMaxTopK]
     LayerParams layer[kMaxLayers];
 };
 

@@ -26,6 +26,7 @@ struct StageCtx {
     uint32_t where;    // stage index, for error reports
     char* scratch;     // the instance's scratch memory
     float* smem;       // dynamic shared memory of this CTA
+    bool defer_topk = false;   // a final GEMM stage leaves its top-k merge to the pipeline's leader
 };
 
 struct FinalOut {
