@@ -1646,13 +1646,16 @@ def run_ipc(args):
 
 
 def run_profile_case(args):
-    """Small self-contained case for ncu: two saturated 2,000-query launches."""
-    wl = Workload(args.workload, 0, n_rows=2000)
+    """Self-contained case for ncu: two saturated launches of --queries queries
+    each (8,000 by default: 1.2 GB of images for the 3-stage pipeline, larger
+    than L2, and long enough that pipeline fill and drain are a few percent)."""
+    nq = args.queries
+    wl = Workload(args.workload, 0, n_rows=nq)
     # the split the allocator chose in the full benchmark on this GPU
     inst, quota = WORKLOADS[args.workload]["profile_alloc"]
     p = wl.pipeline(0, inst, quota)
     for _ in range(2):
-        wl.trace(p, np.zeros(2000, np.int64))
+        wl.trace(p, np.zeros(nq, np.int64))
     wl.cm.camelot_pipeline_destroy(p)
     wl.close()
     print("profile case done")
@@ -1751,7 +1754,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="camelot", choices=["camelot", "reference"])
     ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
-    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="ncu case: two saturated pipeline launches of --queries queries of --workload")
+    ap.add_argument("--queries", type=int, default=8000)
     ap.add_argument("--stage-case", action="store_true",
                     help="ncu case: direct launches of one stage (--stage, --ctas, --batch) of --workload")
     ap.add_argument("--stage", type=int, default=1)
