@@ -1331,7 +1331,9 @@ def run_artifact(args):
 
     Every stage is profiled alone (p99 of one batch at each 8-SM quota); the
     Eq. 1 allocation is solved with the global-memory bandwidth constraint
-    (Camelot: budget = measured HBM copy bandwidth) and without it (Camelot-NC).
+    (Camelot: budget = measured HBM copy bandwidth) and without it (Camelot-NC),
+    both with the host-link constraint on the p_i stages (budget = the host
+    link's measured read bandwidth, from the p_3 sweep run first).
     Each distinct allocation then runs a device-resident Poisson trace of about
     0.25 s at 90 % of the peak its solver predicts, and its p99 is compared
     with the QoS.  The sweep copies 1 GB host -> device on k streams at once
@@ -1389,7 +1391,10 @@ def run_artifact(args):
 
         def solve(names, bw_budget, handover=None):
             # Table 2 quantities by the library (bytes per query: rows in and out
-            # plus the table bytes it streams), optionally with hand-over times
+            # plus the table bytes it streams), optionally with hand-over times;
+            # stages reading the pinned host table also demand host-link
+            # bandwidth (their table bytes per query x their throughput) against
+            # the link's measured budget
             n = len(names)
             costs = [(i, 0.0, 0.0, hbm_bytes[k] / B, 64e6) for i, k in enumerate(names)]
             bs = np.array([B], np.int32)
@@ -1398,8 +1403,13 @@ def run_artifact(args):
                             mem.ctypes.data)
             if handover is not None:
                 cm.camelot_profile_add_handover(pr, handover, thr, bw, dd)
+            host = np.zeros_like(thr)
+            for i, k in enumerate(names):
+                host[0, i, :] = thr[0, i, :] * host_bytes.get(k, 0) / 1e9
+            pr.host_gbs = host.ctypes.data
             cons = cm.Constraints(sms, sms // 8, bw_budget, 200e9, QOS_NS * 1e-9, 0.0, cm.SOLVER_EXHAUSTIVE, 0,
                                   0.0, 0.0, 0)
+            cons.host_gbs = host_link_gbs
             a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
             inst, quota = [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)]
             demand = sum(inst[i] * float(bw[0, i, quota[i] // 8 - 1]) for i in range(n))
@@ -1467,32 +1477,9 @@ def run_artifact(args):
             finally:
                 cm.camelot_pipeline_destroy(p)
 
-        # ---- Camelot vs Camelot-NC on the 27 pipelines
-        cases = []
-        combos = [[f"c{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
-        combos += [[f"n{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
-        combos += [[f"p{i}", f"c{j}", f"m{k}"] for i in (1, 2, 3) for j in (1, 2, 3) for k in (1, 2, 3)]
-        with ClockSampler(0) as clk:
-            for names in combos:
-                ca = solve(names, hbm)
-                nc = solve(names, 1e12)
-                row = {"pipeline": "+".join(names),
-                       "camelot": {"instances": ca[0], "sm_quota": ca[1], "predicted_peak_qps": ca[2],
-                                   "predicted_gbs": ca[3]},
-                       "nc": {"instances": nc[0], "sm_quota": nc[1], "predicted_peak_qps": nc[2],
-                              "predicted_gbs": nc[3]}}
-                row["camelot"].update(measure(names, ca[0], ca[1], 0.9 * ca[2]))
-                # the same solver on the profile with the measured per-batch hand-over
-                h = handover_of(names, ca[0], ca[1])
-                ch = solve(names, hbm, handover=h)
-                row["camelot_handover"] = {"handover_us": [v * 1e6 for v in h], "instances": ch[0],
-                                           "sm_quota": ch[1], "predicted_peak_qps": ch[2], "predicted_gbs": ch[3]}
-                row["camelot_handover"].update(measure(names, ch[0], ch[1], 0.9 * ch[2]))
-                if (nc[0], nc[1]) == (ca[0], ca[1]):
-                    row["nc"]["same_as_camelot"] = True
-                else:
-                    row["nc"].update(measure(names, nc[0], nc[1], 0.9 * nc[2]))
-                cases.append(row)
+        # ---- the host link first: its measured read bandwidth is the budget of
+        # the host-link constraint in the allocations below
+        with ClockSampler(0) as clk0:
             # ---- host-link contention: k concurrent 1 GB host -> device copies
             src = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
             dsts = [torch.empty(1 << 30, dtype=torch.uint8, device="cuda") for _ in range(8)]
@@ -1544,8 +1531,37 @@ def run_artifact(args):
                         cm.camelot_pipeline_destroy(p)
             finally:
                 cm.camelot_stage_release(fin)
+        host_link_gbs = max(r["host_link_gbs"] for r in pst)
+        host_bytes = {f"p{i}": ART_P_R[i] * 4 for i in (1, 2, 3)}
+        # ---- Camelot vs Camelot-NC on the 45 pipelines
+        cases = []
+        combos = [[f"c{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
+        combos += [[f"n{j}", f"m{k}"] for j in (1, 2, 3) for k in (1, 2, 3)]
+        combos += [[f"p{i}", f"c{j}", f"m{k}"] for i in (1, 2, 3) for j in (1, 2, 3) for k in (1, 2, 3)]
+        with ClockSampler(0) as clk:
+            for names in combos:
+                ca = solve(names, hbm)
+                nc = solve(names, 1e12)
+                row = {"pipeline": "+".join(names),
+                       "camelot": {"instances": ca[0], "sm_quota": ca[1], "predicted_peak_qps": ca[2],
+                                   "predicted_gbs": ca[3]},
+                       "nc": {"instances": nc[0], "sm_quota": nc[1], "predicted_peak_qps": nc[2],
+                              "predicted_gbs": nc[3]}}
+                row["camelot"].update(measure(names, ca[0], ca[1], 0.9 * ca[2]))
+                # the same solver on the profile with the measured per-batch hand-over
+                h = handover_of(names, ca[0], ca[1])
+                ch = solve(names, hbm, handover=h)
+                row["camelot_handover"] = {"handover_us": [v * 1e6 for v in h], "instances": ch[0],
+                                           "sm_quota": ch[1], "predicted_peak_qps": ch[2], "predicted_gbs": ch[3]}
+                row["camelot_handover"].update(measure(names, ch[0], ch[1], 0.9 * ch[2]))
+                if (nc[0], nc[1]) == (ca[0], ca[1]):
+                    row["nc"]["same_as_camelot"] = True
+                else:
+                    row["nc"].update(measure(names, nc[0], nc[1], 0.9 * nc[2]))
+                cases.append(row)
         out["cases"] = cases
-        out["host_link"] = {"concurrent_copies": copies, "p3_instances": pst}
+        out["host_link"] = {"concurrent_copies": copies, "p3_instances": pst, "budget_gbs": host_link_gbs,
+                            "clocks": clk0.summary()}
         viol = lambda r: r.get("p99_ms", 0.0) > QOS_NS * 1e-6
         diff = [c for c in cases if not c["nc"].get("same_as_camelot")]
         out["summary"] = {
@@ -1568,7 +1584,8 @@ def run_artifact(args):
             "value": out["summary"]["nc_qos_violations"], "unit": "pipelines violating p99 <= QoS",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "artifact pipelines c_j + m_k, m_j + m_k and p_i + c_j + m_k, rows of 4096 f32, batch 16",
-                       "qos_p99_ms": QOS_NS / 1e6, "hbm_budget_gbs": hbm},
+                       "qos_p99_ms": QOS_NS / 1e6, "hbm_budget_gbs": hbm,
+                       "host_link_budget_gbs": out["host_link"]["budget_gbs"]},
             "artifact": out, "clocks": clk.summary()}
     print(json.dumps(line, default=float), flush=True)
     return 0

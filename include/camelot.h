@@ -664,6 +664,8 @@ typedef struct {
     const double* bw_gbs;        /* its global-memory bandwidth demand, GB/s            */
     const double* dur_s;         /* its duration for one batch, s                        */
     const double* mem_bytes;     /* its global-memory footprint, bytes                   */
+    const double* host_gbs;      /* its host-link bandwidth demand, GB/s (stages reading
+                                    pinned host memory); NULL = none for every stage      */
 } camelot_profile;
 
 typedef struct {
@@ -678,13 +680,16 @@ typedef struct {
     double anneal_t0;       /* initial temperature (relative; default 1.0 if 0)           */
     double anneal_alpha;    /* geometric cooling factor (default 0.995 if 0)              */
     uint64_t seed;          /* annealing random stream (SplitMix64)                        */
+    double host_gbs;        /* host-link budget, Constraint-3's form applied to the link
+                               that host-memory stages share (0 = no budget)              */
 } camelot_constraints;
 
 /* Solve the chosen policy.  On success fills out (n_stages, instances,
  * sm_quota, batch = batch_sizes[chosen]) and *objective (the min-throughput for
  * MAX_PEAK, the SM count for MIN_SM).  Constraints: sum N_i p_i <= S, sum N_i <=
- * I, N_i >= 1, sum N_i bw_i <= BW, sum N_i mem_i <= F, sum_i dur_i <= QoS, and for
- * MIN_SM min_i N_i f_i >= load.  Ties: better objective, then fewer SMs (MAX_PEAK)
+ * I, N_i >= 1, sum N_i bw_i <= BW, sum N_i mem_i <= F, sum_i dur_i <= QoS, when
+ * both prof->host_gbs and c->host_gbs are given sum N_i host_i <= c->host_gbs,
+ * and for MIN_SM min_i N_i f_i >= load.  Ties: better objective, then fewer SMs (MAX_PEAK)
  * or higher throughput (MIN_SM), then the lexicographically smallest
  * (batch index, N, level).  Errors: EINVAL, EINFEASIBLE.  Host-only; no GPU use. */
 camelot_status camelot_allocate(const camelot_profile* prof, camelot_policy policy,

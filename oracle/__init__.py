@@ -78,6 +78,8 @@ def _declare(L):
                                    P, P, P]),
         "orc_allocate_exhaustive": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
                                     + [C.c_int] + [P] * 5),
+        "orc_allocate_exhaustive_hl": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
+                                       + [C.c_int, P, C.c_double] + [P] * 5),
         "orc_allocate_anneal": (C.c_int, [C.c_int] * 6 + [P] * 4 + [C.c_double] * 4
                                 + [C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64]
                                 + [P] * 5),
@@ -389,7 +391,9 @@ def allocate(prob: dict, policy: int, solver: str = "exhaustive", iters: int = 5
     """Solve Eq. 1 (policy 0) or Eq. 3 (policy 1) on a profile table.
 
     ``prob`` keys: f, bw, d ([nb, n, L]), mem ([nb, n]), unit, S, I, BW, F, qos,
-    load.  Returns None if infeasible, else dict(bi, N, l, p, thr, sms)."""
+    load, and optionally hb ([nb, n, L] host-link demand) with HB (its budget;
+    exhaustive solver only).  Returns None if infeasible, else dict(bi, N, l, p,
+    thr, sms)."""
     f, bw, d, mem, nb, n, L = _alloc_args(prob)
     bi = C.c_int(0)
     N = np.zeros(n, np.int32)
@@ -400,7 +404,10 @@ def allocate(prob: dict, policy: int, solver: str = "exhaustive", iters: int = 5
               _p(d), _p(mem), float(prob["BW"]), float(prob["F"]), float(prob["qos"]),
               float(prob.get("load", 0.0)), int(policy))
     outs = (C.byref(bi), _p(N), _p(lv), C.byref(thr), C.byref(sms))
-    if solver == "exhaustive":
+    if solver == "exhaustive" and prob.get("hb") is not None:
+        hb = _f64(prob["hb"])
+        ok = lib().orc_allocate_exhaustive_hl(*common, _p(hb), float(prob["HB"]), *outs)
+    elif solver == "exhaustive":
         ok = lib().orc_allocate_exhaustive(*common, *outs)
     else:
         ok = lib().orc_allocate_anneal(*common, int(iters), float(T0), float(alpha),

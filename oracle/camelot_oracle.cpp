@@ -505,17 +505,24 @@ int64_t orc_simulate(const double* arr, int64_t nq, int B, double t_wait, int n_
 // needs to be meaningful) and sum N_i p_i <= S.  Ties: policy 0 prefers the
 // larger objective, then fewer SMs; policy 1 the fewer SMs, then larger
 // throughput; then the lexicographically smallest (bi, N_1..N_n, l_1..l_n).
+// Host link (optional): stages that read pinned host memory share the host
+// link the way all stages share HBM; with hb[(bi*n + i)*L + l] an instance's
+// host-link demand (GB/s) the same form as Constraint-3 applies to it:
+// sum N_i hb_i(p_i) <= HB (Sec. 6.1 names the link's contention; Eq. 1 itself
+// has no term for it).
 struct OrcProblem {
     int n, L, nb, unit, S, I;
     const double *f, *bw, *d, *mem;
     double BW, F, qos, load;
     int policy;
+    const double* hb = nullptr;
+    double HB = 0.0;
 };
 
 static bool orc_eval(const OrcProblem& P, int bi, const int* N, const int* l, double* thr,
                      int* sms) {
     int64_t sm = 0, ninst = 0;
-    double bws = 0.0, mems = 0.0, dsum = 0.0, tmin = INFINITY;
+    double bws = 0.0, mems = 0.0, dsum = 0.0, tmin = INFINITY, hbs = 0.0;
     for (int i = 0; i < P.n; ++i) {
         if (N[i] < 1 || l[i] < 0 || l[i] >= P.L) return false;
         int64_t k = ((int64_t)bi * P.n + i) * P.L + l[i];
@@ -524,9 +531,11 @@ static bool orc_eval(const OrcProblem& P, int bi, const int* N, const int* l, do
         bws += N[i] * P.bw[k];
         mems += N[i] * P.mem[(int64_t)bi * P.n + i];
         dsum += P.d[k];
+        if (P.hb) hbs += N[i] * P.hb[k];
         tmin = std::min(tmin, N[i] * P.f[k]);
     }
     if (sm > P.S || ninst > P.I || bws > P.BW || mems > P.F || dsum > P.qos) return false;
+    if (P.hb && hbs > P.HB) return false;
     if (P.policy == 1 && tmin < P.load) return false;
     *thr = tmin;
     *sms = (int)sm;
@@ -546,11 +555,27 @@ static bool orc_better(int policy, double thr, int sms, double bthr, int bsms) {
 
 // Exhaustive enumeration.  Writes the best (bi, N[], l[]) and returns 1, or 0
 // if no allocation is feasible.
+static int orc_exhaustive(const OrcProblem& P, int* best_bi, int* best_N, int* best_l, double* best_thr,
+                          int* best_sms);
 int orc_allocate_exhaustive(int n, int L, int nb, int unit, int S, int I, const double* f,
                             const double* bw, const double* d, const double* mem, double BW,
                             double F, double qos, double load, int policy, int* best_bi,
                             int* best_N, int* best_l, double* best_thr, int* best_sms) {
     OrcProblem P{n, L, nb, unit, S, I, f, bw, d, mem, BW, F, qos, load, policy};
+    return orc_exhaustive(P, best_bi, best_N, best_l, best_thr, best_sms);
+}
+// The same with the host-link constraint (hb as f, HB the link's budget).
+int orc_allocate_exhaustive_hl(int n, int L, int nb, int unit, int S, int I, const double* f,
+                               const double* bw, const double* d, const double* mem, double BW,
+                               double F, double qos, double load, int policy, const double* hb,
+                               double HB, int* best_bi, int* best_N, int* best_l, double* best_thr,
+                               int* best_sms) {
+    OrcProblem P{n, L, nb, unit, S, I, f, bw, d, mem, BW, F, qos, load, policy, hb, HB};
+    return orc_exhaustive(P, best_bi, best_N, best_l, best_thr, best_sms);
+}
+static int orc_exhaustive(const OrcProblem& P, int* best_bi, int* best_N, int* best_l, double* best_thr,
+                          int* best_sms) {
+    const int n = P.n, L = P.L, nb = P.nb, unit = P.unit, S = P.S, I = P.I, policy = P.policy;
     std::vector<int> N(n, 1), l(n, 0);
     bool found = false;
     double bthr = 0.0;

@@ -100,14 +100,15 @@ class XringHandle(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("n_levels", C.c_int32), ("n_batches", C.c_int32),
                 ("unit", C.c_int32), ("batch_sizes", C.c_void_p), ("thr_qps", C.c_void_p),
-                ("bw_gbs", C.c_void_p), ("dur_s", C.c_void_p), ("mem_bytes", C.c_void_p)]
+                ("bw_gbs", C.c_void_p), ("dur_s", C.c_void_p), ("mem_bytes", C.c_void_p),
+                ("host_gbs", C.c_void_p)]
 
 
 class Constraints(C.Structure):
     _fields_ = [("total_sms", C.c_int32), ("max_instances", C.c_int32), ("bw_gbs", C.c_double),
                 ("mem_bytes", C.c_double), ("qos_s", C.c_double), ("load_qps", C.c_double),
                 ("solver", C.c_int32), ("anneal_iters", C.c_int32), ("anneal_t0", C.c_double),
-                ("anneal_alpha", C.c_double), ("seed", C.c_uint64)]
+                ("anneal_alpha", C.c_double), ("seed", C.c_uint64), ("host_gbs", C.c_double)]
 
 
 # Every symbol include/camelot.h declares, with its ctypes signature.

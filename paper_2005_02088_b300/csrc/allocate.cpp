@@ -34,6 +34,8 @@ struct Problem {
     int n, L, nb, unit, S, I, policy, maxN;
     const double *f, *bw, *d, *mem;
     double BW, F, qos, load;
+    const double* hb;   // host-link demand per instance (nullptr: no host-link constraint)
+    double HB;          // host-link budget
     size_t k(int b, int i, int l) const { return ((size_t)b * n + i) * L + l; }
 };
 
@@ -68,7 +70,7 @@ bool better(const Problem& P, double thr, int sms, int b, const int* N, const in
 // Full evaluation of one state, summing in stage order.
 bool feasible(const Problem& P, int b, const int* N, const int* l, double* thr, int* sms) {
     long long sm = 0, inst = 0;
-    double bws = 0.0, mems = 0.0, dur = 0.0, tmin = INFINITY;
+    double bws = 0.0, mems = 0.0, dur = 0.0, tmin = INFINITY, hbs = 0.0;
     for (int i = 0; i < P.n; ++i) {
         if (N[i] < 1 || N[i] > P.maxN || l[i] < 0 || l[i] >= P.L) return false;
         const size_t k = P.k(b, i, l[i]);
@@ -77,9 +79,11 @@ bool feasible(const Problem& P, int b, const int* N, const int* l, double* thr, 
         bws += N[i] * P.bw[k];
         mems += N[i] * P.mem[(size_t)b * P.n + i];
         dur += P.d[k];
+        if (P.hb) hbs += N[i] * P.hb[k];
         tmin = std::min(tmin, N[i] * P.f[k]);
     }
     if (sm > P.S || inst > P.I || bws > P.BW || mems > P.F || dur > P.qos) return false;
+    if (P.hb && hbs > P.HB) return false;
     if (P.policy == CAMELOT_POLICY_MIN_SM && tmin < P.load) return false;
     *thr = tmin;
     *sms = (int)sm;
@@ -91,7 +95,7 @@ struct Dfs {
     int b;
     std::vector<int> N, l;
     Cand& best;
-    void run(int i, long long sm, long long inst, double bws, double mems, double dur) {
+    void run(int i, long long sm, long long inst, double bws, double mems, double dur, double hbs) {
         if (i == P.n) {
             double thr;
             int sms;
@@ -116,10 +120,11 @@ struct Dfs {
                 const size_t k = P.k(b, i, lv);
                 const double bw2 = bws + n * P.bw[k];
                 const double d2 = dur + P.d[k];
-                if (bw2 > P.BW || d2 > P.qos) continue;
+                const double h2 = P.hb ? hbs + n * P.hb[k] : 0.0;
+                if (bw2 > P.BW || d2 > P.qos || (P.hb && h2 > P.HB)) continue;
                 N[i] = n;
                 l[i] = lv;
-                run(i + 1, sm2, inst + n, bw2, m2, d2);
+                run(i + 1, sm2, inst + n, bw2, m2, d2, h2);
             }
         }
     }
@@ -198,20 +203,23 @@ extern "C" camelot_status camelot_allocate(const camelot_profile* prof, camelot_
     if (c->total_sms < 1 || c->max_instances < 1) return set_err(CAMELOT_EINVAL, "bad constraints");
     const size_t cells = (size_t)prof->n_batches * prof->n_stages * prof->n_levels;
     for (size_t i = 0; i < cells; ++i)
-        if (!(prof->thr_qps[i] >= 0) || !(prof->bw_gbs[i] >= 0) || !(prof->dur_s[i] >= 0))
+        if (!(prof->thr_qps[i] >= 0) || !(prof->bw_gbs[i] >= 0) || !(prof->dur_s[i] >= 0) ||
+            (prof->host_gbs && !(prof->host_gbs[i] >= 0)))
             return set_err(CAMELOT_EINVAL, "profile entries must be finite and >= 0");
+    if (!(c->host_gbs >= 0)) return set_err(CAMELOT_EINVAL, "host_gbs must be >= 0");
     for (size_t i = 0; i < (size_t)prof->n_batches * prof->n_stages; ++i)
         if (!(prof->mem_bytes[i] >= 0)) return set_err(CAMELOT_EINVAL, "memory entries must be >= 0");
     Problem P{prof->n_stages, prof->n_levels, prof->n_batches, prof->unit, c->total_sms,
               c->max_instances, (int)policy,
               std::max(1, std::min(c->max_instances, c->total_sms / prof->unit)),
               prof->thr_qps, prof->bw_gbs, prof->dur_s, prof->mem_bytes,
-              c->bw_gbs, c->mem_bytes, c->qos_s, c->load_qps};
+              c->bw_gbs, c->mem_bytes, c->qos_s, c->load_qps,
+              (prof->host_gbs && c->host_gbs > 0) ? prof->host_gbs : nullptr, c->host_gbs};
     Cand best;
     if (c->solver == CAMELOT_SOLVER_EXHAUSTIVE) {
         for (int b = 0; b < P.nb; ++b) {
             Dfs dfs{P, b, std::vector<int>(P.n, 1), std::vector<int>(P.n, 0), best};
-            dfs.run(0, 0, 0, 0.0, 0.0, 0.0);
+            dfs.run(0, 0, 0, 0.0, 0.0, 0.0, 0.0);
         }
     } else if (c->solver == CAMELOT_SOLVER_ANNEAL) {
         anneal(P, c->anneal_iters > 0 ? c->anneal_iters : 5000,

@@ -56,7 +56,7 @@ static camelot_status fail(camelot_status st, const char* fmt, ...) {
 
 extern "C" const char* camelot_last_error(void) { return g_err.c_str(); }
 void camelot_internal_set_error(const char* msg) { g_err = msg; }
-extern "C" int camelot_version(void) { return 100; }
+extern "C" int camelot_version(void) { return 200; }
 
 static int64_t host_now_ns() {
     timespec ts;

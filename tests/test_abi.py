@@ -83,6 +83,40 @@ def test_allocate_matches_oracle_exhaustive(orc, seed, policy):
 
 
 @pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("policy", [0, 1])
+def test_allocate_host_link_matches_oracle(orc, seed, policy):
+    # the host-link budget (profile host_gbs, constraints host_gbs) against the
+    # oracle's exhaustive search with the same constraint
+    g = np.random.default_rng(4000 + seed)
+    prob = _random_problem(g, [16, 32, 64, 96][seed % 4], n=2 + seed % 2, nb=1 + seed % 2)
+    prob["hb"] = g.integers(0, 8, size=prob["f"].shape).astype(np.float64)
+    prob["HB"] = float(g.integers(4, 24))
+    ref = orc.allocate(prob, policy)
+    pr, keep = _profile(prob)
+    hb = np.ascontiguousarray(prob["hb"], np.float64)
+    pr.host_gbs = hb.ctypes.data
+    cons = _cons(prob)
+    cons.host_gbs = prob["HB"]
+    if ref is None:
+        with pytest.raises(cm.CamelotError) as e:
+            cm.camelot_allocate(pr, policy, cons)
+        assert e.value.status == cm.EINFEASIBLE
+        return
+    a, obj = cm.camelot_allocate(pr, policy, cons)
+    n = prob["f"].shape[1]
+    assert [a.instances[i] for i in range(n)] == ref["N"]
+    assert [a.sm_quota[i] for i in range(n)] == ref["p"]
+    assert obj == (ref["thr"] if policy == 0 else ref["sms"])
+    # without the budget the host demand is ignored
+    a0, obj0 = (None, None)
+    cons.host_gbs = 0.0
+    ref0 = orc.allocate({k: v for k, v in prob.items() if k not in ("hb", "HB")}, policy)
+    if ref0 is not None:
+        a0, obj0 = cm.camelot_allocate(pr, policy, cons)
+        assert obj0 == (ref0["thr"] if policy == 0 else ref0["sms"])
+
+
+@pytest.mark.parametrize("seed", range(10))
 def test_allocate_anneal_reaches_optimum_without_tight_budgets(orc, seed):
     # bandwidth and memory budgets loose: the one-step moves of the annealer
     # connect the whole feasible region, and it finds the exhaustive optimum

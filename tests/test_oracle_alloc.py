@@ -42,6 +42,9 @@ def _brute(prob, policy):
                     continue
                 if sum(d[bi, i, lv[i]] for i in range(n)) > prob["qos"]:
                     continue
+                if prob.get("hb") is not None and \
+                        sum(N[i] * np.asarray(prob["hb"])[bi, i, lv[i]] for i in range(n)) > prob["HB"]:
+                    continue
                 thr = min(N[i] * f[bi, i, lv[i]] for i in range(n))
                 if policy == 1 and thr < prob["load"]:
                     continue
@@ -77,6 +80,40 @@ def test_bandwidth_constraint_binds(orc):
     assert free["thr"] == 32.0
     assert capped["thr"] < free["thr"]
     assert capped == _brute(dict(prob, BW=40.0), 0) | {"p": capped["p"]}
+
+
+def test_host_link_constraint_binds(orc):
+    # Stage 1 reads host memory: 2 GB/s of host-link demand per quota level.
+    # A 6 GB/s link caps it at 24 SMs in total, which caps the min-throughput
+    # at 24 (it was 32 with the link unconstrained); stage 2 is unaffected.
+    prob = _linear_problem(S=64, rates=(1.0, 1.0))
+    L = prob["f"].shape[2]
+    hb = np.zeros_like(prob["f"])
+    hb[0, 0, :] = [2.0 * (l + 1) for l in range(L)]
+    free = orc.allocate(prob, 0)
+    capped = orc.allocate(dict(prob, hb=hb, HB=6.0), 0)
+    assert free["thr"] == 32.0 and capped["thr"] == 24.0
+    assert capped["N"][0] * hb[0, 0, capped["l"][0]] <= 6.0
+    assert capped == _brute(dict(prob, hb=hb, HB=6.0), 0) | {"p": capped["p"]}
+    # a budget that covers every allocation changes nothing
+    assert orc.allocate(dict(prob, hb=hb, HB=1e9), 0) == free
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("policy", [0, 1])
+def test_host_link_exhaustive_equals_brute_force(orc, seed, policy):
+    g = np.random.default_rng(300 + seed)
+    S = [16, 32, 64][seed % 3]
+    prob = _random_problem(g, S, n=2 + seed % 2, nb=1 + seed % 2)
+    prob["hb"] = g.integers(0, 6, size=prob["f"].shape).astype(np.float64)
+    prob["HB"] = float(g.integers(4, 20))
+    r = orc.allocate(prob, policy)
+    b = _brute(prob, policy)
+    if b is None:
+        assert r is None
+    else:
+        r.pop("p")
+        assert r == b
 
 
 def test_infeasible_returns_none(orc):
