@@ -116,7 +116,10 @@ def test_gemm_chain_topk_and_partition_independence(orc):
 
 
 def test_three_stage_pipeline_bf16(orc):
-    """cfg2 end to end through the persistent pipeline, both handoffs."""
+    """cfg2 end to end through the persistent pipeline, both handoffs.  The
+    final stage on 8 SMs takes its top-5 from per-CTA candidates merged by the
+    instance's leader, on 16 SMs (its two K-chunks then unpaired) from the
+    row-wise pass after the reduce: the results must be the same bits."""
     from paper_2005_02088_b300 import camelot as cm, pipelines as pl
     n = 48
     x, ws32 = synth.cfg2_inputs(0, n_queries=n)
@@ -126,19 +129,24 @@ def test_three_stage_pipeline_bf16(orc):
     s2 = pl.stage_dense(cm.STAGE_GEMM_BF16, [wb[2].cuda()], [0], top_k=5, max_batch=32)
     try:
         outs = {}
-        for mode in (0, 1):
+        for mode, fq in ((0, 8), (1, 8), (0, 16)):
             sink = torch.zeros((65536, 1000), dtype=torch.float32, device="cuda")
             torch.cuda.synchronize()
-            p = cm.camelot_pipeline_create([s0, s1, s2], pl.alloc([1, 2, 1], [8, 24, 8], 16), mode,
+            p = cm.camelot_pipeline_create([s0, s1, s2], pl.alloc([1, 2, 1], [8, 24, fq], 16), mode,
                                            pl.options(logits_sink=sink.data_ptr()))
             try:
                 comps = pl.run_all(p, x, stream_id=3, chunk=16, timeout_s=120)
             finally:
                 cm.camelot_pipeline_destroy(p)
-            outs[mode] = (comps, sink[:n].cpu().numpy())
-        comps, lg = outs[0]
+            outs[(mode, fq)] = (comps, sink[:n].cpu().numpy())
+        comps, lg = outs[(0, 8)]
         assert [c.query_id for c in comps] == list(range(n))
-        assert np.array_equal(lg, outs[1][1])                     # handoff-independent
+        for key in ((1, 8), (0, 16)):                             # handoff- and quota-independent
+            c2, lg2 = outs[key]
+            assert np.array_equal(lg.view(np.uint32), lg2.view(np.uint32)), key
+            assert [list(c.idx) for c in comps] == [list(c.idx) for c in c2], key
+            assert np.array_equal(np.array([list(c.val) for c in comps], np.float32).view(np.uint32),
+                                  np.array([list(c.val) for c in c2], np.float32).view(np.uint32)), key
         idx = np.array([[c.idx[r] for r in range(5)] for c in comps])
         ref_idx, _ = orc.topk(lg.astype(np.float64), 5)
         assert np.array_equal(idx, ref_idx)                        # exact on its own logits
