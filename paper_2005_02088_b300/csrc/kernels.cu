@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
     else if (SP.kind == KIND_NORM_POOL2_BF16) pool_setup(reinterpret_cast<float*>(smem4));
     else if (SP.kind == KIND_STREAM_SYNTH) stream_setup(reinterpret_cast<float*>(smem4));
+    else if (SP.kind == KIND_MLP_FP32) mlp_setup(reinterpret_cast<float*>(smem4));
     const bool grouped = cx.nctas > 1;
     // the other CTAs wait for the leader's post for as long as the leader may idle
     const uint64_t post_wait = (uint64_t)P.idle_ns * (uint64_t)(P.n_stages + 2) + 2ull * (uint64_t)P.limit_ns;
@@ -411,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
     else if (sp->kind == KIND_NORM_POOL2_BF16) pool_setup(reinterpret_cast<float*>(smem4));
     else if (sp->kind == KIND_STREAM_SYNTH) stream_setup(reinterpret_cast<float*>(smem4));
+    else if (sp->kind == KIND_MLP_FP32) mlp_setup(reinterpret_cast<float*>(smem4));
     stage_body<KINDS>(cx, *sp, in, n, out, fo);
     if (tensor_stage) gemm_teardown(reinterpret_cast<float*>(smem4));
 }

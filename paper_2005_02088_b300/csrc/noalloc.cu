@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the stages that stream by bulk copies set their mbarriers up first
     if (sp.kind == KIND_NORM_POOL2_BF16) pool_setup(reinterpret_cast<float*>(smem4));
     else if (sp.kind == KIND_STREAM_SYNTH) stream_setup(reinterpret_cast<float*>(smem4));
+    else if (sp.kind == KIND_MLP_FP32) mlp_setup(reinterpret_cast<float*>(smem4));
     stage_body<kAllKinds & ~(kind_bit(KIND_GEMM_BF16) | kind_bit(KIND_GEMM_FP8))>(cx, sp, in, n, out, fo);
 
     // The caller holds no handle on the error word in the static array, so a

@@ -250,11 +250,15 @@ extern "C" camelot_status camelot_stage_prepare(const camelot_stage_desc* d, cam
                     Lp.Npad = (N + kNBlock - 1) / kNBlock * kNBlock;
                     Lp.KC = choose_kc(K);
                     Lp.C = (K + Lp.KC - 1) / Lp.KC;
-                    packed.assign((size_t)(K / 4) * Lp.Npad * 4, 0.f);
-                    for (int kq = 0; kq < K / 4; ++kq)
-                        for (int n = 0; n < N; ++n)
+                    // block-major [Npad/64][K/4][64][4]: a task's chunk of a
+                    // 64-neuron block is one contiguous run (one bulk copy)
+                    const size_t KQ = (size_t)K / 4;
+                    packed.assign(KQ * Lp.Npad * 4, 0.f);
+                    for (int n = 0; n < N; ++n)
+                        for (size_t kq = 0; kq < KQ; ++kq)
                             for (int j = 0; j < 4; ++j)
-                                packed[((size_t)kq * Lp.Npad + n) * 4 + j] = w[(size_t)n * K + 4 * kq + j];
+                                packed[(((size_t)(n / 64) * KQ + kq) * 64 + n % 64) * 4 + j] =
+                                    w[(size_t)n * K + 4 * kq + j];
                 }
                 void* dp = nullptr;
                 if (cudaMalloc(&dp, packed.size() * 4) != cudaSuccess)

@@ -14,7 +14,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kQGroup = 16;            // queries per register tile of the FP32 layers
 constexpr int kNBlock = 128;           // neurons per warp task (4 per lane)
 constexpr int kMaxKC = 128;            // largest K-chunk of a warp task
-constexpr int kWRing = 8;              // weight quads in flight per warp (cp.async ring)
+constexpr int kMRing = 3;              // FP32 layers: bulk-copy ring slots per warp
+constexpr int kMQuads = 3;             // FP32 layers: weight k-quads per ring slot
 constexpr int kMaxRingSlots = 5;       // tensor-core layers: most bulk-copy ring slots
 constexpr size_t kSmemBytes = 216 * 1024;  // dynamic shared memory per CTA: > half an SM,
                                            // so exactly one CTA fits on an SM

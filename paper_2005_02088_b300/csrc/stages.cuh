@@ -411,31 +411,60 @@ static __device__ void normpool_body(const StageCtx& cx, const StageParams& P, R
 // chunk 8g+w for the block's outputs, each in ascending k with FMA; the 8 chunk
 // partials are added in chunk order in shared memory and stored as the group
 // partial P[g][q][j]; the reduce phase adds the groups in ascending order.  Each
-// lane owns NL neurons of the block (lane, lane+32, ...): the packed weights
-// [K/4][Npad][4] give one coalesced 512-byte load per neuron slot and k-quad.
-// Weights stream into a per-warp shared-memory ring kWRing quads ahead with
-// cp.async; the query activations are broadcast from the warp's copy of the
-// chunk.  Blocks are 128 neurons (NL = 4); when an instance has more CTAs than
-// such tasks, 64-neuron blocks (NL = 2) double the tasks.  Either way every
-// output sums the same chunks in the same order, so the block width, like the
-// SM quota, leaves the results unchanged.
+// lane owns NL neurons of the block (lane, lane+32, ...).  The packed weights are
+// block-major, [Npad/64][K/4][64][4] (64-neuron blocks, k-quads inside), so a
+// warp's chunk of one block is one contiguous run of 1 KB per k-quad.  It
+// streams into the warp's ring of kMRing slots of kMQuads quads by bulk copies
+// (mbarrier completion): the copy engine takes in ~200 GB/s per SM where
+// 16-byte cp.async requests from the warps reach ~36 GB/s.  The query
+// activations are broadcast from the warp's copy of the chunk.  Blocks are 128
+// neurons (NL = 4: two 64-neuron halves per slot); when an instance has more
+// CTAs than such tasks, 64-neuron blocks (NL = 2) double the tasks.  Either way
+// every output sums the same chunks in the same order, so the block width, like
+// the SM quota, leaves the results unchanged.
 // ---------------------------------------------------------------------------
+constexpr int kMXs = kQGroup * kMaxKC / 4;           // float4 per warp: the query chunk
+constexpr int kMSlot = 2 * kMQuads * 64;             // float4 per ring slot (two 64-neuron halves)
+constexpr int kMWarp = kMXs + kMRing * kMSlot;       // float4 per warp
+static_assert(kWarps * kMWarp * 16 + kWarps * kMRing * 12 <= (int)kSmemBytes, "FP32 layer smem");
+
+// The ring's mbarriers (one per warp and slot) and their completed fills,
+// after the warps' areas; initialised once per kernel launch by mlp_setup,
+// continued by every later call (never re-initialised in use).
+__device__ __forceinline__ uint64_t* mlp_bars(float* smem) {
+    return reinterpret_cast<uint64_t*>(reinterpret_cast<float4*>(smem) + kWarps * kMWarp);
+}
+__device__ __forceinline__ uint32_t* mlp_fills(float* smem) {
+    return reinterpret_cast<uint32_t*>(mlp_bars(smem) + kWarps * kMRing);
+}
+__device__ __forceinline__ void mlp_setup(float* smem) {
+    if (threadIdx.x < kWarps * kMRing) {
+        mbar_init(&mlp_bars(smem)[threadIdx.x], 1);
+        mlp_fills(smem)[threadIdx.x] = 0u;
+    }
+    if (threadIdx.x == 0) mbar_fence_init();
+    __syncthreads();
+}
+
 template <int NL>
 static __device__ void dense_tasks_nl(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
                                       float* Pbuf) {
     constexpr int NB = 32 * NL;                        // neurons per task
+    constexpr int NH = NL / 2;                         // 64-neuron halves per task
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per-warp shared memory: the query chunk [16][KC] and a ring of kWRing
-    // weight quads (each lane's NL x 16 bytes, written and read by that lane)
-    constexpr int kXs = kQGroup * kMaxKC / 4;          // float4 per warp
-    constexpr int kWs = kWRing * kNBlock;              // float4 per warp
-    float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * (kXs + kWs);
-    float4* wr = xs + kXs;
+    float4* xs = reinterpret_cast<float4*>(cx.smem) + warp * kMWarp;
+    float4* ring = xs + kMXs;
+    uint64_t* bar = mlp_bars(cx.smem) + warp * kMRing;
+    uint32_t* fills = mlp_fills(cx.smem) + warp * kMRing;
+    uint32_t uses[kMRing];                             // completed fills of each slot (all calls)
+#pragma unroll
+    for (int s = 0; s < kMRing; ++s) uses[s] = fills[s];
+    bool ok = true;                                    // false once a ring wait gave up (error recorded)
     const int QG = (n + kQGroup - 1) / kQGroup, NBLK = L.Npad / NB;
     const int G = (L.C + kWarps - 1) / kWarps;         // chunk groups
     const int ntask = QG * NBLK * G;
+    const int KQ = L.K >> 2;
     const float4* wp = reinterpret_cast<const float4*>(L.w);
-    const size_t ws = (size_t)L.Npad;
     for (int t = cx.rank; t < ntask; t += cx.nctas) {
         const int g = t % G;
         const int r = t / G;
@@ -446,11 +475,24 @@ static __device__ void dense_tasks_nl(const StageCtx& cx, const LayerParams& L, 
         for (int q = 0; q < kQGroup; ++q)
 #pragma unroll
             for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
-        if (c < L.C) {
+        if (c < L.C && ok) {
             const int k0 = c * L.KC;
             const int kq_n = min(L.KC, L.K - k0) >> 2;
-            const float4* wq = wp + (size_t)(k0 >> 2) * ws + nb * NB + lane;
-            // group 0: the query chunk (zero rows past the batch) and weight quad 0
+            const int F = (kq_n + kMQuads - 1) / kMQuads;   // ring fills of this chunk
+            // half h of the block: quads k0/4 .. of 64-neuron block nb NH + h
+            const float4* wq = wp + ((size_t)nb * NH * KQ + (k0 >> 2)) * 64;
+            const uint64_t pol = l2_policy_evict_last();   // every batch re-reads the weights
+            auto issue = [&](int j) {   // lane 0: fill j of the chunk into slot j mod kMRing
+                const int q0 = j * kMQuads, nq = min(kMQuads, kq_n - q0);
+                const int s = j % kMRing;
+                mbar_arrive_expect_tx(&bar[s], (uint32_t)(NH * nq * 1024));
+#pragma unroll
+                for (int h = 0; h < NH; ++h)
+                    bulk_load_hint(ring + s * kMSlot + h * kMQuads * 64, wq + ((size_t)h * KQ + q0) * 64,
+                                   (uint32_t)(nq * 1024), &bar[s], pol);
+            };
+            // the query chunk (zero rows past the batch) by cp.async, the first
+            // ring fills by bulk copies
             for (int e = lane; e < kQGroup * kq_n; e += 32) {
                 const int q = e / kq_n, kq = e - q * kq_n;
                 const int gq = qg * kQGroup + q;
@@ -458,47 +500,50 @@ static __device__ void dense_tasks_nl(const StageCtx& cx, const LayerParams& L, 
                                     (k0 >> 2) + kq;
                 cp_async16_zfill(xs + q * (kMaxKC / 4) + kq, src, gq < n ? 16u : 0u);
             }
-#pragma unroll
-            for (int d = 0; d < kWRing - 1; ++d) {
-                if (d < kq_n) {
-#pragma unroll
-                    for (int i = 0; i < NL; ++i)
-                        cp_async16(wr + d * kNBlock + 32 * i + lane, wq + (size_t)d * ws + 32 * i);
+            cp_async_commit();
+            if (lane == 0)
+                for (int j = 0; j < min(kMRing, F); ++j) issue(j);
+            cp_async_wait<0>();
+            __syncwarp();                               // every lane's part of the query chunk
+            for (int j = 0; j < F && ok; ++j) {
+                const int s = j % kMRing;
+                if (!mbar_wait_bounded(&bar[s], uses[s] & 1u, cx, 9)) {
+                    ok = false;
+                    break;
                 }
-                cp_async_commit();
-            }
-            for (int kq = 0; kq < kq_n; ++kq) {
-                const int nxt = kq + kWRing - 1;
-                if (nxt < kq_n) {
-                    float4* dst = wr + (nxt % kWRing) * kNBlock + lane;
+                ++uses[s];
+                const int q0 = j * kMQuads, nq = min(kMQuads, kq_n - q0);
+                for (int qq = 0; qq < nq; ++qq) {
+                    const int kq = q0 + qq;
+                    const float4* wv = ring + s * kMSlot + qq * 64 + lane;
+                    float4 a[NL];
 #pragma unroll
-                    for (int i = 0; i < NL; ++i)
-                        cp_async16(dst + 32 * i, wq + (size_t)nxt * ws + 32 * i);
-                }
-                cp_async_commit();
-                cp_async_wait<kWRing - 1>();      // this lane's copies up to quad kq have landed
-                if (kq == 0) __syncwarp();        // ... and every lane's part of the query chunk
-                const float4* wv = wr + (kq % kWRing) * kNBlock + lane;
-                float4 a[NL];
+                    for (int i = 0; i < NL; ++i) a[i] = wv[(i >> 1) * kMQuads * 64 + 32 * (i & 1)];
 #pragma unroll
-                for (int i = 0; i < NL; ++i) a[i] = wv[32 * i];
+                    for (int q = 0; q < kQGroup; ++q) {
+                        const float4 xv = xs[q * (kMaxKC / 4) + kq];
 #pragma unroll
-                for (int q = 0; q < kQGroup; ++q) {
-                    const float4 xv = xs[q * (kMaxKC / 4) + kq];
-#pragma unroll
-                    for (int i = 0; i < NL; ++i) {
-                        acc[q][i] = fmaf(xv.x, a[i].x, acc[q][i]);
-                        acc[q][i] = fmaf(xv.y, a[i].y, acc[q][i]);
-                        acc[q][i] = fmaf(xv.z, a[i].z, acc[q][i]);
-                        acc[q][i] = fmaf(xv.w, a[i].w, acc[q][i]);
+                        for (int i = 0; i < NL; ++i) {
+                            acc[q][i] = fmaf(xv.x, a[i].x, acc[q][i]);
+                            acc[q][i] = fmaf(xv.y, a[i].y, acc[q][i]);
+                            acc[q][i] = fmaf(xv.z, a[i].z, acc[q][i]);
+                            acc[q][i] = fmaf(xv.w, a[i].w, acc[q][i]);
+                        }
                     }
                 }
+                __syncwarp();                           // every lane is done with slot s
+                if (lane == 0 && j + kMRing < F) issue(j + kMRing);
             }
-            cp_async_wait<0>();
+            // a fill issued but not consumed (only after a failed wait) is
+            // waited for, boundedly, so that no copy lands in a reused slot
+            if (!ok)
+                for (int j = 0; j < min(kMRing, F); ++j) {
+                    const int s = j % kMRing;
+                    (void)mbar_wait_bounded(&bar[s], uses[s] & 1u, cx, 9);
+                }
         }
-        // the warp's chunk partial [16][NB] goes to its (now free) query and
-        // weight areas
-        static_assert(kQGroup * kNBlock <= 4 * (kXs + kWs), "partial does not fit");
+        // the warp's chunk partial [16][NB] goes to its (now free) query area
+        static_assert(kQGroup * kNBlock <= 4 * kMXs, "partial does not fit");
         __syncwarp();
         float* part = reinterpret_cast<float*>(xs);
 #pragma unroll
@@ -513,11 +558,15 @@ static __device__ void dense_tasks_nl(const StageCtx& cx, const LayerParams& L, 
             float sum = 0.f;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w)
-                sum += reinterpret_cast<const float*>(cx.smem)[w * (kXs + kWs) * 4 + q * NB + j];
+                sum += reinterpret_cast<const float*>(cx.smem)[w * kMWarp * 4 + q * NB + j];
             if (gq < n) __stcg(Pbuf + ((size_t)g * n + gq) * L.Npad + nb * NB + j, sum);
         }
         __syncthreads();
     }
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < kMRing; ++s) fills[s] = uses[s];
+    __syncwarp();
 }
 
 static __device__ void dense_tasks(const StageCtx& cx, const LayerParams& L, RowRef x, int n,
