@@ -585,17 +585,22 @@ class Workload:
                 dur[si, li] = ev0.elapsed_time(ev1) * 1e-3 / reps
         return levels, dur
 
-    def refine(self, inst, quota):
-        """The allocation and its one-instance neighbours (an instance moved from
-        one stage to another, or one added where SMs are free), each measured by
-        one saturated trace; returns the fastest and the table.  The solo profile
+    def refine(self, inst, quota, max_rounds=6):
+        """Hill climb from the allocator's choice by measured saturation: the
+        allocation and its one-instance neighbours (an instance moved from one
+        stage to another, or one added where SMs are free), each measured by
+        one saturated trace; then the neighbours of the best so far, until no
+        neighbour is faster (at most max_rounds rounds).  The solo profile
         behind Eq. 1 does not see the per-batch hand-over cost inside the
-        pipeline nor the co-location of the stages, so neighbours of its choice
-        can run faster.  When the choice has instances wider than 8 SMs, the
-        same SMs split into 8-SM instances, and that split's neighbours, are
-        measured too (the solo profile can favour a wide instance whose extra
-        SMs the pipeline does not use)."""
+        pipeline nor the co-location of the stages, and the bandwidth
+        constraint counts every instance's weight reads as HBM traffic though
+        the instances share them through L2, so the solver can leave SMs idle.
+        When the choice has instances wider than 8 SMs, the same SMs split into
+        8-SM instances are a starting point too (the solo profile can favour a
+        wide instance whose extra SMs the pipeline does not use).  Returns the
+        fastest and the table of measurements."""
         n = len(inst)
+        budget = (self.sms // 8) * 8
 
         def neighbours(base, q):
             out = [(list(base), list(q))]
@@ -611,47 +616,35 @@ class Workload:
                 out.append((c, list(q)))
             return out
 
+        table, seen = [], set()
+
+        def measure_new(cands):
+            got = []
+            for c, q in cands:
+                key = (tuple(c), tuple(q))
+                if key in seen or sum(a * b for a, b in zip(c, q)) > budget:
+                    continue
+                seen.add(key)
+                p = self.pipeline(0, c, q)
+                try:
+                    _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
+                    table.append({"instances": list(c), "sm_quota": list(q),
+                                  "saturation_qps": Q_STEP / (ms * 1e-3)})
+                finally:
+                    self.cm.camelot_pipeline_destroy(p)
+                got.append(table[-1])
+            return got
+
         cands = neighbours(inst, quota)
         if any(q != 8 for q in quota):
             cands += neighbours([a * q // 8 for a, q in zip(inst, quota)], [8] * n)
-        seen, uniq = set(), []
-        for c, q in cands:
-            key = (tuple(c), tuple(q))
-            if key not in seen and sum(a * b for a, b in zip(c, q)) <= (self.sms // 8) * 8:
-                seen.add(key)
-                uniq.append((c, q))
-        table = []
-
-        def measure(c, q):
-            p = self.pipeline(0, c, q)
-            try:
-                _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
-                table.append({"instances": list(c), "sm_quota": list(q), "saturation_qps": Q_STEP / (ms * 1e-3)})
-            finally:
-                self.cm.camelot_pipeline_destroy(p)
-            return table[-1]
-
-        for c, q in uniq:
-            measure(c, q)
+        measure_new(cands)
         best = max(table, key=lambda r: r["saturation_qps"])
-        # SMs the allocation leaves idle (the bandwidth constraint counts every
-        # instance's weight reads as HBM traffic, though the instances share
-        # them through L2): add one instance at a time where it measures best
-        budget = (self.sms // 8) * 8
-        while True:
-            used = sum(a * b for a, b in zip(best["instances"], best["sm_quota"]))
-            cands = []
-            for i in range(n):
-                if used + best["sm_quota"][i] <= budget:
-                    c = list(best["instances"])
-                    c[i] += 1
-                    key = (tuple(c), tuple(best["sm_quota"]))
-                    if key not in seen:
-                        seen.add(key)
-                        cands.append(measure(c, best["sm_quota"]))
-            if not cands:
+        for _ in range(max_rounds):
+            got = measure_new(neighbours(best["instances"], best["sm_quota"]))
+            if not got:
                 break
-            top = max(cands, key=lambda r: r["saturation_qps"])
+            top = max(got, key=lambda r: r["saturation_qps"])
             if top["saturation_qps"] <= best["saturation_qps"]:
                 break
             best = top
@@ -910,9 +903,9 @@ def run_gpu(args, rank: int, world: int, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w["desc"], "queries_per_step": Q_STEP, "batch": w["batch"],
                    "alloc": {"instances": inst, "sm_quota": quota,
-                             "chosen_by": "camelot_allocate (Eq. 1 on the solo profile), then the fastest by measured "
-                                          "saturation of that allocation and its one-instance neighbours (and of the same SMs "
-                                          "split into 8-SM instances)"},
+                             "chosen_by": "camelot_allocate (Eq. 1 on the solo profile with measured hand-over times), "
+                                          "then a hill climb by measured saturation over one-instance neighbours (from that "
+                                          "allocation and from the same SMs split into 8-SM instances)"},
                    "handoff": "global", "qos_p99_ms": QOS_NS / 1e6, "peak_rate_qps": lam,
                    "l2": "inputs larger than L2 (22,000 query rows, 3.3 GB per step)",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -40,11 +40,26 @@ def test_refine_neighbours_within_sm_budget():
     assert len(allocs) == len(table)                     # each measured once
     assert ((3, 12, 3), (8, 8, 8)) in allocs             # the allocator's own choice
     assert all(_total(a, q) <= 144 for a, q in allocs)   # 18 units of 8 SMs on 148 SMs
-    # moves of one instance between stages (the +1 moves exceed the budget)
-    assert allocs == {((3, 12, 3), (8, 8, 8)), ((2, 13, 3), (8, 8, 8)), ((2, 12, 4), (8, 8, 8)),
-                      ((4, 11, 3), (8, 8, 8)), ((3, 11, 4), (8, 8, 8)), ((4, 12, 2), (8, 8, 8)),
-                      ((3, 13, 2), (8, 8, 8))}
-    assert (inst, quota) == ([2, 13, 3], [8, 8, 8])       # the fastest under the fake rates
+    # the first round: moves of one instance between stages (the +1 moves
+    # exceed the budget)
+    assert {((3, 12, 3), (8, 8, 8)), ((2, 13, 3), (8, 8, 8)), ((2, 12, 4), (8, 8, 8)),
+            ((4, 11, 3), (8, 8, 8)), ((3, 11, 4), (8, 8, 8)), ((4, 12, 2), (8, 8, 8)),
+            ((3, 13, 2), (8, 8, 8))} <= allocs
+    # then the neighbours of each new best: the fake rate grows with stage 1's
+    # instances, so the climb ends with every other stage at one instance
+    assert (inst, quota) == ([1, 16, 1], [8, 8, 8])
+
+
+def test_refine_climbs_past_a_one_move_optimum():
+    # a 3-stage pipeline whose rate is its slowest stage: from 6 / 9 / 3 the
+    # best one-instance move is 5 / 10 / 3, and 4 / 11 / 3 (two moves away) is
+    # faster still
+    rates = (0.75, 0.26, 1.2)
+    wl = _FakeWorkload(lambda i, q: min(a * r for a, r in zip(i, rates)))
+    inst, quota, table = bench.Workload.refine(wl, [6, 9, 3], [8, 8, 8])
+    allocs = {tuple(r["instances"]) for r in table}
+    assert (5, 10, 3) in allocs
+    assert (inst, quota) == ([4, 11, 3], [8, 8, 8])
 
 
 def test_refine_tries_the_8_sm_split_of_wide_instances():
