@@ -797,11 +797,13 @@ def measure_workload(name, args, local, headline: bool):
                                     "value": (t or {}).get("qps", 0.0), "p99_ms": (t or {}).get("p99_ms")}
         out["main_alloc"] = {"instances": main_alloc[0], "sm_quota": main_alloc[1]}
         sm_mhz = _peaks().get("sm_max_mhz", 2032.0)
-        out["stage_roofline"] = {
-            tag: stage_roofline(name, levels, dur, a[0], a[1], wl.sms, sm_mhz,
-                                t_in if list(a[1]) == list(quota_s) else None)
-            for tag, a in (("main_alloc", main_alloc), ("other_alloc", other_alloc))
-            if all(q in levels for q in a[1])}
+        # per-stage service time inside the pipeline (busy + acquisition per
+        # batch, one saturated trace) of each reported allocation
+        out["stage_roofline"] = {}
+        for tag, a in (("main_alloc", main_alloc), ("other_alloc", other_alloc)):
+            if all(q in levels for q in a[1]):
+                _, t_a, _ = wl.handover(a[0], a[1], dur_at(a[1]))
+                out["stage_roofline"][tag] = stage_roofline(name, levels, dur, a[0], a[1], wl.sms, sm_mhz, t_a)
         out["global"] = res[("main", 0)]
         out["host_staged"] = res[("main", 1)]
         out["other_alloc_global"] = res[("other", 0)]
