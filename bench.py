@@ -29,6 +29,7 @@ the host clock from the scheduled arrival to the poll.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import subprocess
@@ -45,6 +46,10 @@ METRIC = "peak queries/s at p99≤QoS on 1 B300: global-mem vs host-staged hando
 UNIT = "queries/s"
 QOS_NS = 20_000_000
 Q_STEP = 22_000
+# SM-quota unit of the headline and FP32 workloads' profiles and allocations:
+# instances of 4, 8, 12, ... SMs (on 148 SMs, 37 units), so that the light
+# stages can take half-width instances and leave the rest to the GEMM stage
+QUOTA_UNIT = 4
 Q_WARM = 2_000
 HEADLINE = "bf16-3stage"
 
@@ -554,9 +559,10 @@ class Workload:
 
     def profile(self, reps=5):
         """Solo-run profile (Sec. 7.1): duration of one batch of each stage at
-        every 8-SM quota, from direct launches timed with CUDA events."""
+        every quota of QUOTA_UNIT SMs, from direct launches timed with CUDA
+        events."""
         torch, cm = self.torch, self.cm
-        levels = list(range(8, self.sms + 1, 8))
+        levels = list(range(QUOTA_UNIT, self.sms + 1, QUOTA_UNIT))
         B = self.B
         bufs = []
         for (nbytes, _) in self.io[1:]:
@@ -585,7 +591,7 @@ class Workload:
                 dur[si, li] = ev0.elapsed_time(ev1) * 1e-3 / reps
         return levels, dur
 
-    def refine(self, inst, quota, max_rounds=6):
+    def refine(self, inst, quota, max_rounds=16):
         """Hill climb from the allocator's choice by measured saturation: the
         allocation and its one-instance neighbours (an instance moved from one
         stage to another, or one added where SMs are free), each measured by
@@ -597,10 +603,11 @@ class Workload:
         the instances share them through L2, so the solver can leave SMs idle.
         When the choice has instances wider than 8 SMs, the same SMs split into
         8-SM instances are a starting point too (the solo profile can favour a
-        wide instance whose extra SMs the pipeline does not use).  Returns the
-        fastest and the table of measurements."""
+        wide instance whose extra SMs the pipeline does not use).  The SM budget
+        is the GPU's SMs in QUOTA_UNIT steps.  Returns the fastest and the table
+        of measurements."""
         n = len(inst)
-        budget = (self.sms // 8) * 8
+        budget = (self.sms // QUOTA_UNIT) * QUOTA_UNIT
 
         def neighbours(base, q):
             out = [(list(base), list(q))]
@@ -614,6 +621,13 @@ class Workload:
                 c = list(base)
                 c[i] += 1
                 out.append((c, list(q)))
+                # one more instance in each of two stages: where two stages
+                # limit the rate together, a single added instance gains nothing
+                for j in range(i + 1, n):
+                    c = list(base)
+                    c[i] += 1
+                    c[j] += 1
+                    out.append((c, list(q)))
             return out
 
         table, seen = [], set()
@@ -635,9 +649,17 @@ class Workload:
                 got.append(table[-1])
             return got
 
-        cands = neighbours(inst, quota)
-        if any(q != 8 for q in quota):
-            cands += neighbours([a * q // 8 for a, q in zip(inst, quota)], [8] * n)
+        # starting points: the choice, and the same SMs of every stage as
+        # instances of 4 or 8 SMs (the solo profile can favour a width whose
+        # extra SMs the pipeline does not use)
+        starts = [(list(inst), list(quota))]
+        sms_i = [a * q for a, q in zip(inst, quota)]
+        for widths in itertools.product((4, 8), repeat=n):
+            if all(m % w == 0 and m >= w for m, w in zip(sms_i, widths)):
+                starts.append(([m // w for m, w in zip(sms_i, widths)], list(widths)))
+        cands = []
+        for c, q in starts:
+            cands += neighbours(c, q)
         measure_new(cands)
         best = max(table, key=lambda r: r["saturation_qps"])
         for _ in range(max_rounds):
@@ -672,7 +694,9 @@ class Workload:
         bs = np.ascontiguousarray(batches, np.int32)
         thr, bw, d, mem = cm.camelot_profile_from_latency(self.costs(), bs, np.asarray(dur, np.float64))
         n, L = d.shape[1], d.shape[2]
-        pr = cm.Profile(n, L, len(bs), 8, bs.ctypes.data, thr.ctypes.data, bw.ctypes.data, d.ctypes.data,
+        unit = levels[0]                      # levels are unit, 2 unit, ...
+        assert list(levels) == [unit * (i + 1) for i in range(L)]
+        pr = cm.Profile(n, L, len(bs), unit, bs.ctypes.data, thr.ctypes.data, bw.ctypes.data, d.ctypes.data,
                         mem.ctypes.data)
         if handover is not None:
             cm.camelot_profile_add_handover(pr, handover, thr, bw, d)
@@ -684,7 +708,7 @@ class Workload:
         cm = self.cm
         n = len(self.stages)
         pr, keep = self.table(levels, [self.B], np.asarray(dur, np.float64)[None], handover)
-        cons = cm.Constraints(self.sms, self.sms // 8, _peaks().get("hbm_gbs", 6400.0), 200e9, qos_s,
+        cons = cm.Constraints(self.sms, self.sms // levels[0], _peaks().get("hbm_gbs", 6400.0), 200e9, qos_s,
                               0.0, cm.SOLVER_EXHAUSTIVE, 0, 0.0, 0.0, 0)
         a, obj = cm.camelot_allocate(pr, cm.POLICY_MAX_PEAK, cons)
         return [a.instances[i] for i in range(n)], [a.sm_quota[i] for i in range(n)], obj
@@ -905,7 +929,7 @@ def run_gpu(args, rank: int, world: int, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w["desc"], "queries_per_step": Q_STEP, "batch": w["batch"],
                    "alloc": {"instances": inst, "sm_quota": quota,
-                             "chosen_by": "camelot_allocate (Eq. 1 on the solo profile with measured hand-over times), "
+                             "chosen_by": "camelot_allocate (Eq. 1 on the solo profile in 4-SM quota units with measured hand-over times), "
                                           "then a hill climb by measured saturation over one-instance neighbours (from that "
                                           "allocation and from the same SMs split into 8-SM instances)"},
                    "handoff": "global", "qos_p99_ms": QOS_NS / 1e6, "peak_rate_qps": lam,

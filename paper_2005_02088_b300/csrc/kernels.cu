@@ -15,17 +15,20 @@ struct LeaderState {
     unsigned long long seen_h;   // oldest waiting ticket the trigger has seen ...
     uint64_t seen_t;             // ... and since when (device clock)
     uint64_t idle_since;
-    unsigned int polls;          // acquisition attempts (the host's stop flag is read on every 16th)
+    unsigned int polls;          // acquisition attempts (the host's stop flag is read on every 256th)
+    unsigned int backoff_ns;     // stage 0, host queue: sleep between polls while nothing is published
 };
 
 __device__ __forceinline__ bool stop_requested(const PipeParams& P) {
     return *P.host_stop != 0ull || has_error(P.ctl);
 }
-// The stop flag lives in host memory (a PCIe round trip per read): the
-// acquisition loops read it on every 16th attempt only, and the device error
-// word on every attempt.
+// The stop flag lives in host memory: the acquisition loops read it on every
+// 256th attempt only (well under a millisecond apart), and the device error
+// word on every attempt.  Reads of host memory by idle leaders travel over the
+// host link in the direction of the submits' copies: with dozens of instances
+// polling, they cost the end-to-end path a quarter of its rate.
 __device__ __forceinline__ bool stop_check(const PipeParams& P, LeaderState& ls) {
-    return (ls.polls++ & 15u) == 0 ? stop_requested(P) : has_error(P.ctl);
+    return (ls.polls++ & 255u) == 0 ? stop_requested(P) : has_error(P.ctl);
 }
 
 // Claim a free slot of `r` for a new ticket (producer side).  Returns false on
@@ -94,8 +97,13 @@ __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
             oldest = (long long)t0 + tr->off[h - tb];
             sid = tr->stream_id;
         } else {
+            // descriptors live in host memory: while the next one is not
+            // published, one lane polls it alone (a read per poll instead of
+            // B, which would take host-link bandwidth from the submits' copies)
             avail = P.B;
-            if (lane < avail) {
+            const int first_ready = __shfl_sync(
+                0xffffffffu, lane == 0 ? (int)(ld_acquire_sys(&P.qring[h & P.qmask].seq) == h + 1) : 0, 0);
+            if (first_ready && lane < avail) {
                 const QDesc& d = P.qring[(h + lane) & P.qmask];
                 ready = ld_acquire_sys(&d.seq) == h + lane + 1;
                 if (ready) { arr = d.t_arrival; sid = d.stream_id; }
@@ -108,12 +116,22 @@ __device__ unsigned int stage0_acquire(const PipeParams& P, LeaderState& ls,
             const int idle_out = __shfl_sync(
                 0xffffffffu, (!trace && now - ls.idle_since > (uint64_t)P.idle_ns) ? 1 : 0, 0);
             if (idle_out) return CMD_EXIT;
-            __nanosleep(trace ? 200 : 500);
+            if (trace) {
+                __nanosleep(200);
+            } else {
+                // host queue empty: poll less and less often (0.5 .. 8 us)
+                __nanosleep(ls.backoff_ns);
+                ls.backoff_ns = min(2u * ls.backoff_ns, 8000u);
+            }
             continue;
         }
+        ls.backoff_ns = 500u;
         if (!trace && ls.seen_h != h) { ls.seen_h = h; ls.seen_t = now; }
         const uint64_t waited = trace ? (now - (uint64_t)oldest) : (now - ls.seen_t);
-        if (kk < P.B && waited < (uint64_t)P.trig_wait_ns[kk - 1]) { __nanosleep(200); continue; }
+        if (kk < P.B && waited < (uint64_t)P.trig_wait_ns[kk - 1]) {
+            __nanosleep(trace ? 200 : 1000);   // (host descriptors: fewer re-reads over the link)
+            continue;
+        }
         unsigned long long got = 0;
         if (lane == 0) got = atomicCAS(&P.ctl->in_head.v, h, h + kk);
         got = __shfl_sync(0xffffffffu, got, 0);
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(const PipeParams*
     __shared__ unsigned long long sh_in, sh_first, sh_out;
     __shared__ long long sh_tb;
     __shared__ unsigned long long sh_t_work;   // leader: when this batch's work was held
-    LeaderState ls{~0ull, 0, gtime(), 0u};
+    LeaderState ls{~0ull, 0, gtime(), 0u, 500u};
     const bool tensor_stage = is_tensor_kind(SP.kind);
     if (tensor_stage) gemm_setup(reinterpret_cast<float*>(smem4));
     else if (SP.kind == KIND_NORM_POOL2_BF16) pool_setup(reinterpret_cast<float*>(smem4));

@@ -34,32 +34,39 @@ def _total(inst, quota):
 
 
 def test_refine_neighbours_within_sm_budget():
-    wl = _FakeWorkload(lambda i, q: 1.0 + i[1])
+    # the rate grows with stage 1's SMs
+    wl = _FakeWorkload(lambda i, q: 1.0 + i[1] * q[1])
     inst, quota, table = bench.Workload.refine(wl, [3, 12, 3], [8, 8, 8])
     allocs = {(tuple(r["instances"]), tuple(r["sm_quota"])) for r in table}
     assert len(allocs) == len(table)                     # each measured once
     assert ((3, 12, 3), (8, 8, 8)) in allocs             # the allocator's own choice
-    assert all(_total(a, q) <= 144 for a, q in allocs)   # 18 units of 8 SMs on 148 SMs
-    # the first round: moves of one instance between stages (the +1 moves
-    # exceed the budget)
-    assert {((3, 12, 3), (8, 8, 8)), ((2, 13, 3), (8, 8, 8)), ((2, 12, 4), (8, 8, 8)),
-            ((4, 11, 3), (8, 8, 8)), ((3, 11, 4), (8, 8, 8)), ((4, 12, 2), (8, 8, 8)),
-            ((3, 13, 2), (8, 8, 8))} <= allocs
-    # then the neighbours of each new best: the fake rate grows with stage 1's
-    # instances, so the climb ends with every other stage at one instance
-    assert (inst, quota) == ([1, 16, 1], [8, 8, 8])
+    assert all(_total(a, q) <= 148 for a, q in allocs)   # 37 units of 4 SMs on 148 SMs
+    # the first round: moves of one instance between stages, and the same SMs
+    # as 4-SM instances
+    assert {((2, 13, 3), (8, 8, 8)), ((4, 11, 3), (8, 8, 8)), ((3, 11, 4), (8, 8, 8)),
+            ((6, 24, 6), (4, 4, 4)), ((3, 24, 3), (8, 4, 8))} <= allocs
+    # then the neighbours of each new best: stage 1 ends with nearly all SMs
+    assert _total(inst, quota) <= 148 and inst[1] * quota[1] >= 128
 
 
 def test_refine_climbs_past_a_one_move_optimum():
-    # a 3-stage pipeline whose rate is its slowest stage: from 6 / 9 / 3 the
-    # best one-instance move is 5 / 10 / 3, and 4 / 11 / 3 (two moves away) is
-    # faster still
+    # a 3-stage pipeline whose rate is its slowest stage, on 8-SM instances
+    # only (4-SM ones run badly here): from 6 / 9 / 3 the best one-instance
+    # move is 5 / 10 / 3, and 4 / 11 / 3 (two moves away) is faster still
     rates = (0.75, 0.26, 1.2)
-    wl = _FakeWorkload(lambda i, q: min(a * r for a, r in zip(i, rates)))
+    wl = _FakeWorkload(lambda i, q: min(a * r for a, r in zip(i, rates)) if all(w == 8 for w in q) else 0.1)
     inst, quota, table = bench.Workload.refine(wl, [6, 9, 3], [8, 8, 8])
     allocs = {tuple(r["instances"]) for r in table}
     assert (5, 10, 3) in allocs
     assert (inst, quota) == ([4, 11, 3], [8, 8, 8])
+
+
+def test_refine_adds_to_two_stages_at_once():
+    # two stages limit the rate together: adding to either alone gains nothing
+    rates = (1.0, 0.5, 0.5)
+    wl = _FakeWorkload(lambda i, q: min(a * r for a, r in zip(i, rates)) if all(w == 8 for w in q) else 0.1)
+    inst, quota, table = bench.Workload.refine(wl, [3, 4, 4], [8, 8, 8])
+    assert quota == [8, 8, 8] and inst[1] > 4 and inst[2] > 4
 
 
 def test_refine_tries_the_8_sm_split_of_wide_instances():
@@ -68,9 +75,5 @@ def test_refine_tries_the_8_sm_split_of_wide_instances():
     inst, quota, table = bench.Workload.refine(wl, [1, 16], [16, 8])
     allocs = {(tuple(r["instances"]), tuple(r["sm_quota"])) for r in table}
     assert ((1, 16), (16, 8)) in allocs and ((2, 16), (8, 8)) in allocs
-    assert all(_total(a, q) <= 144 for a, q in allocs)
-    assert quota == [8, 8] and _total(inst, quota) <= 144
-    # nothing to split: only the one-instance neighbours
-    wl2 = _FakeWorkload(lambda i, q: 1.0)
-    _, _, t2 = bench.Workload.refine(wl2, [2, 16], [8, 8])
-    assert all(r["sm_quota"] == [8, 8] for r in t2)
+    assert all(_total(a, q) <= 148 for a, q in allocs)
+    assert quota == [8, 8] and _total(inst, quota) <= 148
