@@ -71,7 +71,7 @@ WORKLOADS = {
               "37632-1024-1024 GELU (bf16, tcgen05) -> GEMM 1024-1000 + top-5; batch 32; Poisson "
               "arrivals; p99 QoS 20 ms"),
         batch=32, row=224 * 224 * 3, even=([1, 1, 1], [48, 48, 48]),
-        profile_alloc=([4, 11, 3], [8, 8, 8]),
+        profile_alloc=([8, 24, 5], [4, 4, 4]),
         flop=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1000),
         bytes=150528 + 2 * 37632 * 2 + 2 * 1024 * 2,
         weight_bytes=2 * (37632 * 1024 + 1024 * 1024 + 1024 * 1024),
