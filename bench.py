@@ -591,12 +591,13 @@ class Workload:
                 dur[si, li] = ev0.elapsed_time(ev1) * 1e-3 / reps
         return levels, dur
 
-    def refine(self, inst, quota, max_rounds=16):
+    def refine(self, inst, quota, max_rounds=12, queries=8000):
         """Hill climb from the allocator's choice by measured saturation: the
         allocation and its one-instance neighbours (an instance moved from one
         stage to another, or one added where SMs are free), each measured by
         one saturated trace; then the neighbours of the best so far, until no
-        neighbour is faster (at most max_rounds rounds).  The solo profile
+        neighbour is faster (at most max_rounds rounds; each measurement a
+        saturated trace of `queries` queries).  The solo profile
         behind Eq. 1 does not see the per-batch hand-over cost inside the
         pipeline nor the co-location of the stages, and the bandwidth
         constraint counts every instance's weight reads as HBM traffic though
@@ -641,9 +642,9 @@ class Workload:
                 seen.add(key)
                 p = self.pipeline(0, c, q)
                 try:
-                    _, ms = self.trace(p, np.zeros(Q_STEP, np.int64))
+                    _, ms = self.trace(p, np.zeros(queries, np.int64))
                     table.append({"instances": list(c), "sm_quota": list(q),
-                                  "saturation_qps": Q_STEP / (ms * 1e-3)})
+                                  "saturation_qps": queries / (ms * 1e-3)})
                 finally:
                     self.cm.camelot_pipeline_destroy(p)
                 got.append(table[-1])
@@ -803,7 +804,10 @@ def measure_workload(name, args, local, headline: bool):
                             "solo_profile_only": {"instances": inst_s, "sm_quota": quota_s,
                                                   "predicted_min_thr_qps": obj_s, "measured_saturation_qps": sat_s,
                                                   "measured_over_predicted": sat_s / obj_s}}
+        t_ref = time.time()
         inst_r, quota_r, table = wl.refine(inst_c, quota_c)
+        print(f"[bench] {name}: hill climb measured {len(table)} allocations in {time.time() - t_ref:.1f} s",
+              file=sys.stderr, flush=True)
         out["refined"] = {"instances": inst_r, "sm_quota": quota_r, "measured_neighbours": table}
         main_alloc = (inst_r, quota_r) if name == "bf16-3stage" else wl.w["even"]
         other_alloc = wl.w["even"] if name == "bf16-3stage" else (inst_r, quota_r)
