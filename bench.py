@@ -421,7 +421,11 @@ class Workload:
         for s in self.stages:
             self.cm.camelot_stage_release(s)
 
-    def pipeline(self, mode, inst, quota, data_slots=0, device_data=0, batch=0, query_slots=65536):
+    def pipeline(self, mode, inst, quota, data_slots=64, device_data=0, batch=0, query_slots=65536):
+        """A pipeline for trace replays (device-resident queries): the buffer for
+        submitted query bytes keeps its minimum size unless data_slots asks
+        for more (0 = one row per query slot: ~10 GB of pinned host memory for
+        the 150 KB images)."""
         o = self.pl.options(exit_after_trace=1, query_slots=query_slots, idle_exit_ns=20_000_000,
                             data_slots=data_slots, device_data=device_data)
         p = self.cm.camelot_pipeline_create(self.stages, self.pl.alloc(inst, quota, batch or self.B), mode, o)
