@@ -595,7 +595,7 @@ class Workload:
                 dur[si, li] = ev0.elapsed_time(ev1) * 1e-3 / reps
         return levels, dur
 
-    def refine(self, inst, quota, max_rounds=12, queries=8000):
+    def refine(self, inst, quota, max_rounds=16, queries=Q_STEP):
         """Hill climb from the allocator's choice by measured saturation: the
         allocation and its one-instance neighbours (an instance moved from one
         stage to another, or one added where SMs are free), each measured by
