@@ -87,7 +87,7 @@ def bf16_full():
 
 def _bench_pipeline(cm, pl, st, mode, inst, quota, sink=0):
     o = pl.options(exit_after_trace=1, query_slots=65536, idle_exit_ns=20_000_000,
-                   logits_sink=sink)
+                   logits_sink=sink, data_slots=64)
     return cm.camelot_pipeline_create(st, pl.alloc(inst, quota, 32), mode, o)
 
 
@@ -115,20 +115,25 @@ def test_bf16_three_stage_full_size(orc, bf16_full):
     assert res["top5_fixed_on_gpu_input"] >= 0.9 * len(pick), res
     print("bf16 full-size sampled parity:", res)
 
-    # the benchmark's configurations (no sink) give bit-identical completions
-    runs = [(0, [4, 11, 3], np.zeros(N_FULL, np.int64)),
-            (0, [4, 11, 3], synth.poisson_arrivals_ns(101, N_FULL, 2.0e6)),
-            (0, [3, 12, 3], np.zeros(N_FULL, np.int64)),
-            (1, [4, 11, 3], np.zeros(N_FULL, np.int64))]
-    for mode, inst, offs in runs:
-        p = _bench_pipeline(cm, pl, st, mode, inst, [8, 8, 8])
+    # the benchmark's configurations (no sink) give bit-identical completions:
+    # 8-SM instances, and 4-SM ones (each GEMM CTA then runs two weight tiles
+    # and the final stage's leader merges two tiles' candidates per CTA)
+    runs = [(0, [4, 11, 3], [8, 8, 8], np.zeros(N_FULL, np.int64)),
+            (0, [4, 11, 3], [8, 8, 8], synth.poisson_arrivals_ns(101, N_FULL, 2.0e6)),
+            (0, [3, 12, 3], [8, 8, 8], np.zeros(N_FULL, np.int64)),
+            (1, [4, 11, 3], [8, 8, 8], np.zeros(N_FULL, np.int64)),
+            (0, [8, 24, 5], [4, 4, 4], np.zeros(N_FULL, np.int64)),
+            (0, [8, 24, 5], [4, 4, 4], synth.poisson_arrivals_ns(102, N_FULL, 2.5e6)),
+            (0, [8, 12, 5], [4, 8, 4], np.zeros(N_FULL, np.int64))]
+    for mode, inst, quota, offs in runs:
+        p = _bench_pipeline(cm, pl, st, mode, inst, quota)
         try:
             c = _trace(cm, p, xq, offs)
         finally:
             cm.camelot_pipeline_destroy(p)
         _check_invariants(c, N_FULL, 5)
-        assert np.array_equal(c["idx"], ref["idx"]), (mode, inst)
-        assert np.array_equal(c["val"].view(np.uint32), ref["val"].view(np.uint32)), (mode, inst)
+        assert np.array_equal(c["idx"], ref["idx"]), (mode, inst, quota)
+        assert np.array_equal(c["val"].view(np.uint32), ref["val"].view(np.uint32)), (mode, inst, quota)
         assert np.all((c["batch_size"] >= 1) & (c["batch_size"] <= 32))
 
 
@@ -147,7 +152,7 @@ def test_fp32_two_stage_full_size(orc):
         for mode, s in ((0, sink.data_ptr()), (0, 0), (1, 0)):
             torch.cuda.synchronize()
             o = pl.options(exit_after_trace=1, query_slots=65536, idle_exit_ns=20_000_000,
-                           logits_sink=s)
+                           logits_sink=s, data_slots=64)
             p = cm.camelot_pipeline_create(st, pl.alloc([1, 1], [72, 72], 16), mode, o)
             try:
                 out[(mode, s)] = _trace(cm, p, xq, np.zeros(N_FULL, np.int64))
