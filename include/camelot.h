@@ -412,7 +412,13 @@ typedef struct {
                                fully taken and drained (one launch per trace, which makes
                                the launch's CUDA-event time the trace's device time)  */
     uint32_t data_slots;    /* rows of the buffer that holds submitted query bytes
-                               (power of two <= query_slots; 0 = query_slots)          */
+                               (power of two in 64..query_slots; 0 = query_slots).  The
+                               buffer takes data_slots x the stage-0 row bytes, pinned or
+                               on the device, allocated at pipeline_create: 0 with 65536
+                               query slots and 150 KB rows is ~10 GB and seconds of
+                               allocation; a pipeline fed only by camelot_submit_trace
+                               needs the minimum, 64; one call of camelot_submit takes at
+                               most data_slots queries                                    */
     int32_t device_data;    /* 0: that buffer is pinned, mapped host memory which stage 0
                                reads over the host link; 1: it is device memory which
                                camelot_submit fills with DMA copies (cudaMemcpyAsync,
