@@ -77,3 +77,26 @@ def test_refine_tries_the_8_sm_split_of_wide_instances():
     assert ((1, 16), (16, 8)) in allocs and ((2, 16), (8, 8)) in allocs
     assert all(_total(a, q) <= 148 for a, q in allocs)
     assert quota == [8, 8] and _total(inst, quota) <= 148
+
+
+def test_studies_report_failures_instead_of_failing(monkeypatch):
+    # the compact study after the headline: its summary on success, its error
+    # (and no exception) on failure
+    def fake_ok(args, emit=True):
+        assert args.diurnal == 12.0 and emit is False
+        return {"value": 0.4, "unit": "fraction", "peak_qps": 1.0, "saturation_qps": 1.0, "static_alloc": {},
+                "allocator_measured_over_predicted": 1.0, "sm_seconds": {"eq3": 1, "static": 2},
+                "qos_violating_windows": {"eq3": 0, "static": 0}, "p99_ms_max": {"eq3": 0.1, "static": 0.1},
+                "queries": 10, "clocks": {}, "config": {"load": "day"}, "windows_eq3": [1, 2, 3]}
+
+    monkeypatch.setattr(bench, "run_diurnal", fake_ok)
+    out = bench.run_studies()
+    assert out["diurnal_fp8"]["value"] == 0.4 and out["diurnal_fp8"]["load"] == "day"
+    assert "windows_eq3" not in out["diurnal_fp8"] and out["diurnal_fp8"]["seconds"] >= 0
+
+    def fake_fail(args, emit=True):
+        raise TimeoutError("trace did not drain")
+
+    monkeypatch.setattr(bench, "run_diurnal", fake_fail)
+    out = bench.run_studies()
+    assert out["diurnal_fp8"]["error"] == "TimeoutError: trace did not drain"
